@@ -1,0 +1,205 @@
+/*
+ * msi.h -- exact k-nearest-neighbour similarity search over an in-memory collection
+ * of z-normalised data series summarised by iSAX, on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: MESSI (Peng, Fatourou, Palpanas, "MESSI: In-Memory Data Series Indexing").
+ * The calls follow the paper's problem statement (Section II-A, "Similarity Search"):
+ * given a collection of series of one length n and a query of that length, return
+ * the series at the smallest Euclidean distance; here generalised to the k smallest.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an msi_status; on failure msi_last_error() gives a detail
+ *    string for the calling thread. No exception crosses this boundary.
+ *  - Array arguments are plain pointers. Unless a call says otherwise a pointer may
+ *    address host memory or device memory of the index's GPU; the library detects
+ *    which (cudaPointerGetAttributes) and copies what it needs. The caller keeps
+ *    ownership of everything it passes.
+ *  - Layouts are row-major and densely packed: a collection is float[n][len].
+ *  - `stream` arguments are cudaStream_t values passed as void*. NULL means the
+ *    library's own stream, and the call returns only after its work is complete.
+ *    With a non-NULL stream, work is ordered on that stream; outputs in host memory
+ *    are complete when the call returns, outputs in device memory once the stream
+ *    reaches the call's work.
+ *  - Calls on one index must not overlap in time (they share the index's query
+ *    workspace); distinct indexes are independent.
+ */
+#ifndef MSI_H
+#define MSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every entry point is exported from the shared library. */
+#if defined(__GNUC__)
+#define MSI_API __attribute__((visibility("default")))
+#else
+#define MSI_API
+#endif
+
+#define MSI_ABI_VERSION 1
+#define MSI_MAX_SEGMENTS 16          /* one SAX word fits 16 bytes                    */
+#define MSI_MAX_CARDINALITY 256      /* 8-bit symbols (Section II-B)                  */
+#define MSI_MAX_LEN 4096             /* longest series                                */
+#define MSI_MAX_K 1024               /* most neighbours per query                     */
+#define MSI_DEFAULT_LEAF_CAPACITY 2000 /* leaf capacity used in Section IV            */
+
+typedef enum msi_status {
+  MSI_OK = 0,
+  MSI_EINVAL = 1,     /* an argument is out of range, NULL, or the input holds NaN/inf */
+  MSI_ENOMEM = 2,     /* device memory for the index or its workspace is short         */
+  MSI_ECUDA = 3,      /* a CUDA runtime call failed (no device, launch failure, ...)   */
+  MSI_ETIMEOUT = 4,   /* reserved: a bounded device-side wait ran out                  */
+  MSI_EINTERNAL = 5   /* an internal consistency check failed                          */
+} msi_status;
+
+typedef struct msi_index msi_index; /* opaque; owns all the device memory it uses */
+
+/* Build flags. */
+#define MSI_BUILD_BORROW 0x1u /* index a DEVICE collection in place, without a copy: the
+                                 caller keeps the buffer alive and unchanged until
+                                 msi_free; distances z-normalise its values on the fly */
+
+typedef struct msi_build_opts {
+  int32_t leaf_capacity; /* most series per leaf; 0 selects MSI_DEFAULT_LEAF_CAPACITY */
+  uint32_t flags;        /* MSI_BUILD_* bits                                          */
+  void* stream;          /* cudaStream_t or NULL                                       */
+} msi_build_opts;
+
+/*
+ * msi_build -- summarise a collection and build its index (Section III-A, Algorithms
+ * 1-4: CreateIndex, IndexWorker, CalculateiSAXSummaries, TreeConstruction).
+ *
+ * Each series is z-normalised (Section II-A: mean 0, standard deviation 1, population
+ * moments; a constant series becomes all zeros), cut into `segments` equal segments
+ * whose means form its PAA (Section II-B), and each mean is quantised to one of
+ * `cardinality` symbols against N(0,1) equiprobable breakpoints, giving the series'
+ * iSAX word. Series are grouped into leaves of at most leaf_capacity members by the
+ * bits of their words taken one bit of every segment at a time, most significant
+ * first, splitting a group in two on the next bit while it is over capacity; the
+ * first `segments` bits always split (the root fan-out of Section II-B). Each leaf
+ * keeps the per-segment minimum and maximum symbol of its members.
+ *
+ *   series       float[n][len], host or device. Copied unless MSI_BUILD_BORROW.
+ *   n            number of series, 1 .. 2^32-2.
+ *   len          points per series, 1 .. MSI_MAX_LEN, a multiple of `segments`.
+ *   segments     1 .. MSI_MAX_SEGMENTS.
+ *   cardinality  a power of two in [2, 256].
+ *   opts         NULL for the defaults.
+ *   out          receives the index; set to NULL on failure (no partial index).
+ * Errors: MSI_EINVAL (arguments; a series holding NaN or infinity), MSI_ENOMEM,
+ * MSI_ECUDA.
+ */
+MSI_API msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segments,
+                     int32_t cardinality, const msi_build_opts* opts, msi_index** out);
+
+/*
+ * msi_knn -- exact k-NN search, one query after another (Section III-B, Algorithms 5-9:
+ * ExactSearch, SearchWorker, TraverseRootSubtree, ProcessQueue, CalculateRealDistance).
+ *
+ * Every query is z-normalised like the collection. The answer is exactly the k
+ * series at the smallest Euclidean distance between z-normalised values, ordered by
+ * distance and then by lower id (ties go to the lower id). The distance itself is
+ * the square root of the FP64 sum of squared differences, rounded to float.
+ *
+ *   index    an index from msi_build.
+ *   queries  float[nq][len], host or device.
+ *   nq       number of queries, >= 0 (0 is a no-op).
+ *   k        neighbours per query, 1 .. min(n, MSI_MAX_K).
+ *   ids      int64[nq][k]: ids (row positions in the collection), host or device.
+ *   dists    float[nq][k]: Euclidean distances, host or device; may be NULL.
+ *   stream   see the conventions above.
+ * Errors: MSI_EINVAL, MSI_ENOMEM (query workspace), MSI_ECUDA.
+ */
+MSI_API msi_status msi_knn(msi_index* index, const float* queries, int64_t nq, int32_t k, int64_t* ids,
+                   float* dists, void* stream);
+
+/* Releases the index and all its device memory. NULL is a no-op. */
+MSI_API void msi_free(msi_index* index);
+
+/* Static name of a status code. */
+MSI_API const char* msi_status_str(msi_status status);
+
+/* Detail of the calling thread's last failure ("" if none). Valid until the thread's
+ * next msi_* call. */
+MSI_API const char* msi_last_error(void);
+
+/* ABI version of the loaded library (MSI_ABI_VERSION). */
+MSI_API int32_t msi_abi_version(void);
+
+typedef struct msi_index_info {
+  int64_t n;              /* series                                   */
+  int32_t len;            /* points per series                        */
+  int32_t segments;       /* PAA segments (word length in symbols)    */
+  int32_t cardinality;    /* symbols per segment                      */
+  int32_t leaf_capacity;  /* most series per leaf                     */
+  int64_t leaves;         /* leaves built                             */
+  int64_t device_bytes;   /* device memory the index holds            */
+  uint32_t flags;         /* MSI_BUILD_* flags it was built with      */
+  int32_t device;         /* CUDA device ordinal                      */
+} msi_index_info;
+
+/* Shape and size of an index. `info` is a host pointer. */
+MSI_API msi_status msi_index_info_get(const msi_index* index, msi_index_info* info);
+
+/*
+ * msi_index_export -- copy the index's summaries to HOST memory, for inspection and
+ * tests. Every pointer may be NULL to skip that array.
+ *   words       uint8[n][segments]: the iSAX word of each series, in collection order.
+ *   perm        uint32[n]: collection id of the series at each leaf-order position.
+ *   leaf_begin  uint32[leaves+1]: first leaf-order position of each leaf, then n.
+ *   env_lo/hi   uint8[leaves][segments]: per-leaf minimum / maximum symbol.
+ *   thresholds  float[cardinality-1]: the fp32 quantisation thresholds in use (the
+ *               smallest float at or above each N(0,1) breakpoint).
+ *   znorm       float[n][len]: z-normalised collection (collection order).
+ */
+typedef struct msi_export {
+  uint8_t* words;
+  uint32_t* perm;
+  uint32_t* leaf_begin;
+  uint8_t* env_lo;
+  uint8_t* env_hi;
+  float* thresholds;
+  float* znorm;
+} msi_export;
+MSI_API msi_status msi_index_export(const msi_index* index, const msi_export* out);
+
+/*
+ * msi_lower_bounds -- the iSAX lower bound (mindist between the query's PAA and an
+ * iSAX region, Section II-B; used by Algorithms 7 and 9) of one query against every
+ * series and every leaf, as the search computes it (fp32). HOST outputs.
+ *   query     float[len], host or device (raw; z-normalised here).
+ *   series_lb float[n] in collection order, or NULL.
+ *   leaf_lb   float[leaves], or NULL.
+ */
+MSI_API msi_status msi_lower_bounds(msi_index* index, const float* query, float* series_lb, float* leaf_lb,
+                            void* stream);
+
+/* Work counters of the msi_knn calls since the last reset (all queries summed). */
+typedef struct msi_query_stats {
+  int64_t queries;
+  int64_t leaves_total;          /* leaves examined by the leaf filter              */
+  int64_t leaves_survived;       /* leaves whose bound did not exceed the threshold */
+  int64_t leaves_processed;      /* leaves whose members were lower-bounded         */
+  int64_t series_lower_bounded;  /* per-series lower bounds computed                */
+  int64_t series_refined;        /* real distances computed (seed leaf included)    */
+  int64_t seed_series;           /* real distances of the approximate-search seed   */
+  int64_t candidates;            /* (distance, id) pairs kept for the final pick    */
+  int64_t rechecked;             /* FP64 re-computations at the k-th boundary       */
+  int64_t refine_launches;       /* launches of the refinement kernel               */
+  double refine_ms;              /* their summed device time (timing enabled only)  */
+} msi_query_stats;
+
+/* Reads the counters (host pointer), optionally resetting them. Reading synchronises
+ * with the index's last call. */
+MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats, int32_t reset);
+
+/* Enables (1) or disables (0) CUDA-event timing of the refinement kernel. */
+MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSI_H */

@@ -1,0 +1,234 @@
+"""Exact k-NN similarity search over iSAX-summarised data series on one GB300 GPU.
+
+A thin ctypes binding of the C ABI in include/msi.h: every function below has the
+name of the C entry point it calls and only marshals arguments (numpy arrays and
+host/device torch tensors to raw pointers, torch streams to cudaStream_t). All the
+computation runs in the CUDA library libmsi.so; importing this module fails loudly
+if that library has not been built (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "MsiError", "Index", "msi_build", "msi_knn", "msi_free", "msi_status_str", "msi_last_error",
+    "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
+    "msi_query_stats_get", "msi_set_timing", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
+]
+
+MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
+MSI_BUILD_BORROW = 0x1
+MSI_MAX_K = 1024
+MSI_MAX_LEN = 4096
+
+
+def library_path():
+    return _build.LIB
+
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(f"{_build.LIB} is missing: the CUDA library must be built first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(_build.LIB)
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("leaf_capacity", ctypes.c_int32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+
+
+class _IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("len", ctypes.c_int32), ("segments", ctypes.c_int32),
+                ("cardinality", ctypes.c_int32), ("leaf_capacity", ctypes.c_int32), ("leaves", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("flags", ctypes.c_uint32), ("device", ctypes.c_int32)]
+
+
+class _Export(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("words", "perm", "leaf_begin", "env_lo", "env_hi", "thresholds", "znorm")]
+
+
+class _QueryStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "queries", "leaves_total", "leaves_survived", "leaves_processed", "series_lower_bounded",
+        "series_refined", "seed_series", "candidates", "rechecked", "refine_launches")] + [("refine_ms", ctypes.c_double)]
+
+
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_lib.msi_build.argtypes = [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(_BuildOpts), ctypes.POINTER(_vp)]
+_lib.msi_build.restype = ctypes.c_int
+_lib.msi_knn.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
+_lib.msi_knn.restype = ctypes.c_int
+_lib.msi_free.argtypes = [_vp]
+_lib.msi_free.restype = None
+_lib.msi_status_str.argtypes = [ctypes.c_int]
+_lib.msi_status_str.restype = ctypes.c_char_p
+_lib.msi_last_error.argtypes = []
+_lib.msi_last_error.restype = ctypes.c_char_p
+_lib.msi_abi_version.argtypes = []
+_lib.msi_abi_version.restype = _i32
+_lib.msi_index_info_get.argtypes = [_vp, ctypes.POINTER(_IndexInfo)]
+_lib.msi_index_info_get.restype = ctypes.c_int
+_lib.msi_index_export.argtypes = [_vp, ctypes.POINTER(_Export)]
+_lib.msi_index_export.restype = ctypes.c_int
+_lib.msi_lower_bounds.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.msi_lower_bounds.restype = ctypes.c_int
+_lib.msi_query_stats_get.argtypes = [_vp, ctypes.POINTER(_QueryStats), _i32]
+_lib.msi_query_stats_get.restype = ctypes.c_int
+_lib.msi_set_timing.argtypes = [_vp, _i32]
+_lib.msi_set_timing.restype = ctypes.c_int
+
+
+class MsiError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__(f"{msi_status_str(status)}: {detail}")
+
+
+def _check(status):
+    if status != MSI_OK:
+        raise MsiError(status, msi_last_error())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """Raw pointer of a contiguous numpy array or torch tensor of `dtype`."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        want = {np.float32: torch.float32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy {np.dtype(dtype)} array")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Index:
+    """Owner of an msi_index handle; msi_free runs when it is released."""
+
+    def __init__(self, handle, keepalive=None):
+        self.handle = handle
+        self._keepalive = keepalive  # borrowed collection
+        info = msi_index_info_get(self)
+        self.n, self.len, self.segments = info["n"], info["len"], info["segments"]
+        self.cardinality, self.leaves = info["cardinality"], info["leaves"]
+
+    def close(self):
+        if self.handle:
+            msi_free(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+def msi_status_str(status):
+    return _lib.msi_status_str(int(status)).decode()
+
+
+def msi_last_error():
+    return _lib.msi_last_error().decode()
+
+
+def msi_abi_version():
+    return int(_lib.msi_abi_version())
+
+
+def msi_build(series, n=None, len=None, segments=16, cardinality=256, leaf_capacity=0, flags=0, stream=None):
+    """msi_build: `series` is float32 [n, len] (numpy host array or torch tensor, host
+    or device). Returns an Index."""
+    n = series.shape[0] if n is None else n
+    len_ = series.shape[1] if len is None else len
+    opts = _BuildOpts(leaf_capacity, flags, _stream(stream))
+    out = ctypes.c_void_p()
+    _check(_lib.msi_build(_ptr(series, np.float32), n, len_, segments, cardinality, ctypes.byref(opts),
+                          ctypes.byref(out)))
+    return Index(out.value, keepalive=series if flags & MSI_BUILD_BORROW else None)
+
+
+def msi_knn(index, queries, k, ids=None, dists=None, stream=None, nq=None):
+    """msi_knn: `queries` float32 [nq, len] host or device. Outputs are allocated
+    like the queries (numpy for host input, torch on the same device otherwise)
+    unless given. Returns (ids int64 [nq, k], dists float32 [nq, k])."""
+    nq = queries.shape[0] if nq is None else nq
+    if ids is None:
+        if _is_torch(queries):
+            import torch
+            ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device) if dists is None else dists
+        else:
+            ids = np.empty((nq, k), dtype=np.int64)
+            dists = np.empty((nq, k), dtype=np.float32) if dists is None else dists
+    _check(_lib.msi_knn(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, _ptr(ids, np.int64),
+                        _ptr(dists, np.float32), _stream(stream)))
+    return ids, dists
+
+
+def msi_free(index):
+    _lib.msi_free(ctypes.c_void_p(index.handle if isinstance(index, Index) else index))
+
+
+def msi_index_info_get(index):
+    info = _IndexInfo()
+    _check(_lib.msi_index_info_get(ctypes.c_void_p(index.handle), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
+
+
+def msi_index_export(index, words=True, perm=True, leaves=True, thresholds=True, znorm=False):
+    """msi_index_export into fresh numpy arrays (a dict)."""
+    n, w, L = index.n, index.segments, index.leaves
+    out = {}
+    if words:
+        out["words"] = np.empty((n, w), dtype=np.uint8)
+    if perm:
+        out["perm"] = np.empty(n, dtype=np.uint32)
+    if leaves:
+        out["leaf_begin"] = np.empty(L + 1, dtype=np.uint32)
+        out["env_lo"] = np.empty((L, w), dtype=np.uint8)
+        out["env_hi"] = np.empty((L, w), dtype=np.uint8)
+    if thresholds:
+        out["thresholds"] = np.empty(index.cardinality - 1, dtype=np.float32)
+    if znorm:
+        out["znorm"] = np.empty((n, index.len), dtype=np.float32)
+    ex = _Export(*[ctypes.c_void_p(out[f].ctypes.data) if f in out else None for f, _ in _Export._fields_])
+    _check(_lib.msi_index_export(ctypes.c_void_p(index.handle), ctypes.byref(ex)))
+    return out
+
+
+def msi_lower_bounds(index, query, stream=None):
+    """msi_lower_bounds: (series_lb float32 [n] in collection order, leaf_lb float32 [leaves])."""
+    s = np.empty(index.n, dtype=np.float32)
+    lf = np.empty(index.leaves, dtype=np.float32)
+    _check(_lib.msi_lower_bounds(ctypes.c_void_p(index.handle), _ptr(query, np.float32), _ptr(s, np.float32),
+                                 _ptr(lf, np.float32), _stream(stream)))
+    return s, lf
+
+
+def msi_query_stats_get(index, reset=False):
+    st = _QueryStats()
+    _check(_lib.msi_query_stats_get(ctypes.c_void_p(index.handle), ctypes.byref(st), 1 if reset else 0))
+    return {f: getattr(st, f) for f, _ in _QueryStats._fields_}
+
+
+def msi_set_timing(index, enable=True):
+    _check(_lib.msi_set_timing(ctypes.c_void_p(index.handle), 1 if enable else 0))

@@ -1,0 +1,456 @@
+// msi_api.cu -- the C ABI of include/msi.h: argument checks, device memory,
+// streams, the breakpoint tables, and the order in which the build and query
+// kernels run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "msi_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+msi_status fail(msi_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+msi_status fail(msi_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+msi_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error for the next call
+  if (e == cudaErrorMemoryAllocation) return fail(MSI_ENOMEM, "%s: out of device memory", what);
+  return fail(MSI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Is `p` device memory of `device`? Host memory (pinned or pageable) answers false.
+bool is_device_ptr(const void* p, int device, bool* other_device) {
+  *other_device = false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.device != device) *other_device = true;
+    return true;
+  }
+  return false;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------- breakpoints
+// beta = Phi^{-1}(p) by Newton's method on Phi(x) - p, with Phi(x) = erfc(-x/sqrt 2)/2
+// and Phi'(x) = exp(-x^2/2)/sqrt(2 pi), started from the logistic approximation
+// x0 = (sqrt 3 / pi) ln(p / (1 - p)).
+double normal_quantile(double p) {
+  const double kPi = 3.14159265358979323846;
+  double x = std::sqrt(3.0) / kPi * std::log(p / (1.0 - p));
+  for (int it = 0; it < 100; ++it) {
+    const double f = 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+    const double d = std::exp(-0.5 * x * x) / std::sqrt(2.0 * kPi);
+    const double step = f / d;
+    x -= step;
+    if (std::fabs(step) <= 1e-17 * std::fmax(1.0, std::fabs(x))) break;
+  }
+  return x;
+}
+
+// Region edges for cardinality c: up[v] = smallest float >= beta_v (the SAX decision
+// thresholds), lo[v] = largest float <= beta_v; v = 0 and v = c are -inf / +inf.
+void region_edges(int c, float* up, float* lo) {
+  up[0] = lo[0] = -INFINITY;
+  up[c] = lo[c] = INFINITY;
+  for (int v = 1; v < c; ++v) {
+    const double b = (2 * v == c) ? 0.0 : normal_quantile((double)v / (double)c);
+    float f = (float)b;
+    while ((double)f < b) f = std::nextafter(f, INFINITY);
+    while ((double)std::nextafter(f, -INFINITY) >= b) f = std::nextafter(f, -INFINITY);
+    up[v] = f;
+    float g = (float)b;
+    while ((double)g > b) g = std::nextafter(g, -INFINITY);
+    while ((double)std::nextafter(g, INFINITY) <= b) g = std::nextafter(g, INFINITY);
+    lo[v] = g;
+  }
+}
+
+void free_index(msi_index* ix) {
+  if (!ix) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != ix->device) cudaSetDevice(ix->device);
+  void* ptrs[] = {ix->data_owned, ix->words, ix->perm, ix->stats, ix->leaf_begin, ix->env, ix->leaf_key,
+                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2,
+                  ix->qv.cand, ix->qv.rc_d, ix->qv.rc_id, ix->qv.counters, ix->ws_qraw, ix->ws_ids, ix->ws_dists};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& ev : ix->events) {
+    if (ev.first) cudaEventDestroy(ev.first);
+    if (ev.second) cudaEventDestroy(ev.second);
+  }
+  if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
+  if (cur >= 0 && cur != ix->device) cudaSetDevice(cur);
+  delete ix;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t msi_abi_version(void) { return MSI_ABI_VERSION; }
+
+const char* msi_status_str(msi_status s) {
+  switch (s) {
+    case MSI_OK: return "MSI_OK";
+    case MSI_EINVAL: return "MSI_EINVAL";
+    case MSI_ENOMEM: return "MSI_ENOMEM";
+    case MSI_ECUDA: return "MSI_ECUDA";
+    case MSI_ETIMEOUT: return "MSI_ETIMEOUT";
+    case MSI_EINTERNAL: return "MSI_EINTERNAL";
+  }
+  return "MSI_UNKNOWN";
+}
+
+const char* msi_last_error(void) { return g_err.c_str(); }
+
+msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segments, int32_t cardinality,
+                     const msi_build_opts* opts, msi_index** out) {
+  g_err.clear();
+  if (!out) return fail(MSI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!series) return fail(MSI_EINVAL, "series is NULL");
+  if (n < 1 || n > 0xfffffffeLL) return fail(MSI_EINVAL, "n = %lld outside [1, 2^32-2]", (long long)n);
+  if (len < 1 || len > MSI_MAX_LEN) return fail(MSI_EINVAL, "len = %d outside [1, %d]", len, MSI_MAX_LEN);
+  if (segments < 1 || segments > MSI_MAX_SEGMENTS)
+    return fail(MSI_EINVAL, "segments = %d outside [1, %d]", segments, MSI_MAX_SEGMENTS);
+  if (len % segments != 0) return fail(MSI_EINVAL, "len = %d is not a multiple of segments = %d", len, segments);
+  if (cardinality < 2 || cardinality > MSI_MAX_CARDINALITY || (cardinality & (cardinality - 1)))
+    return fail(MSI_EINVAL, "cardinality = %d is not a power of two in [2, 256]", cardinality);
+  const int32_t cap = (opts && opts->leaf_capacity) ? opts->leaf_capacity : MSI_DEFAULT_LEAF_CAPACITY;
+  if (cap < 1 || cap > (1 << 24)) return fail(MSI_EINVAL, "leaf_capacity = %d outside [1, 2^24]", cap);
+  const uint32_t flags = opts ? opts->flags : 0u;
+  if (flags & ~MSI_BUILD_BORROW) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+  bool other = false;
+  const bool on_dev = is_device_ptr(series, dev, &other);
+  if (other) return fail(MSI_EINVAL, "series lives on another device than the current one (%d)", dev);
+  if ((flags & MSI_BUILD_BORROW) && !on_dev) return fail(MSI_EINVAL, "MSI_BUILD_BORROW needs device memory");
+  // kernels read rows with 16-byte vector loads
+  const bool aligned = ((uintptr_t)series & 15u) == 0;
+  if ((flags & MSI_BUILD_BORROW) && !aligned)
+    return fail(MSI_EINVAL, "a borrowed collection must start on a 16-byte boundary");
+
+  msi_index* ix = new msi_index();
+  ix->device = dev;
+  ix->n = n;
+  ix->len = len;
+  ix->w = segments;
+  ix->card = cardinality;
+  ix->bits = 0;
+  while ((1 << ix->bits) < cardinality) ++ix->bits;
+  ix->seglen = len / segments;
+  ix->cap = cap;
+  ix->flags = flags;
+  region_edges(cardinality, ix->h_thr_up, ix->h_thr_lo);
+
+  cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+  if ((e = cudaStreamCreateWithFlags(&ix->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    free_index(ix);
+    return cuda_fail(e, "creating the index stream");
+  }
+  if (!s) s = ix->own_stream;
+  const size_t tb = sizeof(float) * (size_t)(cardinality + 1);
+  if ((e = cudaMalloc(&ix->thr_up, tb)) != cudaSuccess || (e = cudaMalloc(&ix->thr_lo, tb)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ix->thr_up, ix->h_thr_up, tb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ix->thr_lo, ix->h_thr_lo, tb, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    free_index(ix);
+    return cuda_fail(e, "uploading breakpoint tables");
+  }
+  const size_t data_bytes = sizeof(float) * (size_t)n * len;
+  const float* src = series;
+  bool in_place = false;
+  if (flags & MSI_BUILD_BORROW) {
+    ix->data = series;
+    ix->data_is_z = false;
+  } else {
+    if ((e = cudaMalloc(&ix->data_owned, data_bytes)) != cudaSuccess) {
+      free_index(ix);
+      return cuda_fail(e, "allocating the collection copy");
+    }
+    ix->device_bytes += (int64_t)data_bytes;
+    ix->data = ix->data_owned;
+    ix->data_is_z = true;
+    if (!on_dev || !aligned) {
+      if ((e = cudaMemcpyAsync(ix->data_owned, series, data_bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               s)) != cudaSuccess) {
+        free_index(ix);
+        return cuda_fail(e, "copying the collection to the device");
+      }
+      src = ix->data_owned;
+      in_place = true;
+    }
+  }
+  int64_t first_bad = -1;
+  const char* stage = "build";
+  e = msi::build_index(ix, src, in_place, s, &first_bad, &stage);
+  if (e != cudaSuccess) {
+    free_index(ix);
+    return cuda_fail(e, stage);
+  }
+  if (first_bad >= 0) {
+    free_index(ix);
+    return fail(MSI_EINVAL, "series %lld holds NaN or infinity (or its moments overflow)", (long long)first_bad);
+  }
+  *out = ix;
+  return MSI_OK;
+}
+
+msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
+                   void* stream) {
+  g_err.clear();
+  if (!ix) return fail(MSI_EINVAL, "index is NULL");
+  if (nq < 0) return fail(MSI_EINVAL, "nq = %lld is negative", (long long)nq);
+  if (k < 1 || k > MSI_MAX_K || (int64_t)k > ix->n)
+    return fail(MSI_EINVAL, "k = %d outside [1, min(n = %lld, %d)]", k, (long long)ix->n, MSI_MAX_K);
+  if (nq == 0) return MSI_OK;
+  if (!queries || !ids) return fail(MSI_EINVAL, "queries or ids is NULL");
+  DeviceGuard guard(ix->device);
+  bool o1 = false, o2 = false, o3 = false;
+  const bool q_dev = is_device_ptr(queries, ix->device, &o1);
+  const bool ids_dev = is_device_ptr(ids, ix->device, &o2);
+  const bool d_dev = dists ? is_device_ptr(dists, ix->device, &o3) : true;
+  if (o1 || o2 || o3) return fail(MSI_EINVAL, "an argument lives on another device than the index");
+  cudaError_t e = msi::query_setup(ix);
+  if (e != cudaSuccess) return cuda_fail(e, "allocating the query workspace");
+  cudaStream_t s = stream ? (cudaStream_t)stream : ix->own_stream;
+  unsigned long long* bad_flag = ix->qv.counters + msi::ST_BAD_QUERY;
+  if ((e = cudaMemsetAsync(bad_flag, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+    return cuda_fail(e, "msi_knn");
+  const int64_t chunk = msi::kQueryChunk;
+  if (ix->timing && ix->events.size() < (size_t)chunk) {
+    while (ix->events.size() < (size_t)chunk) {
+      cudaEvent_t a, b;
+      if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess)
+        return cuda_fail(e, "creating timing events");
+      ix->events.emplace_back(a, b);
+    }
+  }
+  const bool host_out = !ids_dev || !d_dev;
+  for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
+    const int64_t cnt = std::min<int64_t>(chunk, nq - c0);
+    const float* qd = queries + c0 * ix->len;
+    if (!q_dev) {
+      if ((e = cudaMemcpyAsync(ix->ws_qraw, qd, sizeof(float) * cnt * ix->len, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e, "copying queries to the device");
+      qd = ix->ws_qraw;
+    }
+    int64_t* id_base = ids_dev ? ids + c0 * k : ix->ws_ids;
+    float* d_base = dists ? (d_dev ? dists + c0 * k : ix->ws_dists) : nullptr;
+    for (int64_t i = 0; i < cnt; ++i) {
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (ix->timing) {
+        ea = ix->events[i].first;
+        eb = ix->events[i].second;
+      }
+      e = msi::query_one(ix, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr, s, ea, eb);
+      if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
+    }
+    if (!ids_dev &&
+        (e = cudaMemcpyAsync(ids + c0 * k, ix->ws_ids, sizeof(int64_t) * cnt * k, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+      return cuda_fail(e, "copying ids to the host");
+    if (dists && !d_dev &&
+        (e = cudaMemcpyAsync(dists + c0 * k, ix->ws_dists, sizeof(float) * cnt * k, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+      return cuda_fail(e, "copying distances to the host");
+    if (host_out || ix->timing || c0 + chunk < nq) {
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "query execution");
+    }
+    if (ix->timing) {
+      for (int64_t i = 0; i < cnt; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ix->events[i].first, ix->events[i].second) == cudaSuccess) {
+          ix->refine_ms += ms;
+          ++ix->refine_launches;
+        }
+      }
+    }
+  }
+  if (!stream || host_out) {
+    unsigned long long bad = 0;
+    if ((e = cudaMemcpyAsync(&bad, bad_flag, sizeof bad, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "query execution");
+    if (bad) return fail(MSI_EINVAL, "%llu queries hold NaN or infinity", bad);
+  }
+  return MSI_OK;
+}
+
+void msi_free(msi_index* ix) { free_index(ix); }
+
+msi_status msi_index_info_get(const msi_index* ix, msi_index_info* info) {
+  g_err.clear();
+  if (!ix || !info) return fail(MSI_EINVAL, "index or info is NULL");
+  info->n = ix->n;
+  info->len = ix->len;
+  info->segments = ix->w;
+  info->cardinality = ix->card;
+  info->leaf_capacity = ix->cap;
+  info->leaves = ix->L;
+  info->device_bytes = ix->device_bytes;
+  info->flags = ix->flags;
+  info->device = ix->device;
+  return MSI_OK;
+}
+
+msi_status msi_index_export(const msi_index* cix, const msi_export* ex) {
+  g_err.clear();
+  if (!cix || !ex) return fail(MSI_EINVAL, "index or export is NULL");
+  msi_index* ix = const_cast<msi_index*>(cix);
+  DeviceGuard guard(ix->device);
+  cudaError_t e;
+  const int64_t n = ix->n, L = ix->L;
+  std::vector<uint32_t> perm;
+  if (ex->words || ex->perm) {
+    perm.resize(n);
+    if ((e = cudaMemcpy(perm.data(), ix->perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "export");
+    if (ex->perm) std::memcpy(ex->perm, perm.data(), sizeof(uint32_t) * n);
+  }
+  if (ex->words) {
+    std::vector<uint4> wl(n);
+    if ((e = cudaMemcpy(wl.data(), ix->words, sizeof(uint4) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "export");
+    for (int64_t p = 0; p < n; ++p)
+      std::memcpy(ex->words + (int64_t)perm[p] * ix->w, &wl[p], (size_t)ix->w);
+  }
+  if (ex->leaf_begin &&
+      (e = cudaMemcpy(ex->leaf_begin, ix->leaf_begin, sizeof(uint32_t) * (L + 1), cudaMemcpyDeviceToHost)) !=
+          cudaSuccess)
+    return cuda_fail(e, "export");
+  if (ex->env_lo || ex->env_hi) {
+    std::vector<uint4> env(2 * L);
+    if ((e = cudaMemcpy(env.data(), ix->env, sizeof(uint4) * 2 * L, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "export");
+    for (int64_t l = 0; l < L; ++l) {
+      if (ex->env_lo) std::memcpy(ex->env_lo + l * ix->w, &env[2 * l], (size_t)ix->w);
+      if (ex->env_hi) std::memcpy(ex->env_hi + l * ix->w, &env[2 * l + 1], (size_t)ix->w);
+    }
+  }
+  if (ex->thresholds) std::memcpy(ex->thresholds, ix->h_thr_up + 1, sizeof(float) * (ix->card - 1));
+  if (ex->znorm) {
+    const size_t bytes = sizeof(float) * (size_t)n * ix->len;
+    if (ix->data_is_z) {
+      if ((e = cudaMemcpy(ex->znorm, ix->data, bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "export");
+    } else {
+      float* tmp = nullptr;
+      if ((e = cudaMalloc(&tmp, bytes)) != cudaSuccess) return cuda_fail(e, "export");
+      e = msi::export_z(ix, tmp, ix->own_stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ix->own_stream);
+      if (e == cudaSuccess) e = cudaMemcpy(ex->znorm, tmp, bytes, cudaMemcpyDeviceToHost);
+      cudaFree(tmp);
+      if (e != cudaSuccess) return cuda_fail(e, "export");
+    }
+  }
+  return MSI_OK;
+}
+
+msi_status msi_lower_bounds(msi_index* ix, const float* query, float* series_lb, float* leaf_lb, void* stream) {
+  g_err.clear();
+  if (!ix || !query) return fail(MSI_EINVAL, "index or query is NULL");
+  DeviceGuard guard(ix->device);
+  cudaError_t e = msi::query_setup(ix);
+  if (e != cudaSuccess) return cuda_fail(e, "allocating the query workspace");
+  cudaStream_t s = stream ? (cudaStream_t)stream : ix->own_stream;
+  bool other = false;
+  const float* qd = query;
+  if (!is_device_ptr(query, ix->device, &other)) {
+    if ((e = cudaMemcpyAsync(ix->ws_qraw, query, sizeof(float) * ix->len, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_fail(e, "copying the query");
+    qd = ix->ws_qraw;
+  } else if (other) {
+    return fail(MSI_EINVAL, "query lives on another device");
+  }
+  float *sl = nullptr, *ll = nullptr;
+  if (series_lb && (e = cudaMalloc(&sl, sizeof(float) * ix->n)) != cudaSuccess) return cuda_fail(e, "lower bounds");
+  if (leaf_lb && (e = cudaMalloc(&ll, sizeof(float) * ix->L)) != cudaSuccess) {
+    cudaFree(sl);
+    return cuda_fail(e, "lower bounds");
+  }
+  e = msi::lower_bounds(ix, qd, sl, ll, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && sl) e = cudaMemcpy(series_lb, sl, sizeof(float) * ix->n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && ll) e = cudaMemcpy(leaf_lb, ll, sizeof(float) * ix->L, cudaMemcpyDeviceToHost);
+  cudaFree(sl);
+  cudaFree(ll);
+  if (e != cudaSuccess) return cuda_fail(e, "lower bounds");
+  return MSI_OK;
+}
+
+msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset) {
+  g_err.clear();
+  if (!ix || !st) return fail(MSI_EINVAL, "index or stats is NULL");
+  std::memset(st, 0, sizeof *st);
+  if (!ix->ws_ready) return MSI_OK;
+  DeviceGuard guard(ix->device);
+  unsigned long long c[msi::ST_COUNT];
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c, ix->qv.counters, sizeof(unsigned long long) * msi::ST_COUNT, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+  st->queries = (int64_t)c[msi::ST_QUERIES];
+  st->leaves_total = (int64_t)c[msi::ST_LEAVES_TOTAL];
+  st->leaves_survived = (int64_t)c[msi::ST_LEAVES_SURVIVED];
+  st->leaves_processed = (int64_t)c[msi::ST_LEAVES_PROCESSED];
+  st->series_lower_bounded = (int64_t)c[msi::ST_SERIES_LB];
+  st->series_refined = (int64_t)c[msi::ST_SERIES_REFINED];
+  st->seed_series = (int64_t)c[msi::ST_SEED];
+  st->candidates = (int64_t)c[msi::ST_CANDIDATES];
+  st->rechecked = (int64_t)c[msi::ST_RECHECKED];
+  st->refine_launches = ix->refine_launches;
+  st->refine_ms = ix->refine_ms;
+  if (reset) {
+    if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_BAD_QUERY)) != cudaSuccess)
+      return cuda_fail(e, "resetting counters");
+    ix->refine_ms = 0.0;
+    ix->refine_launches = 0;
+  }
+  return MSI_OK;
+}
+
+msi_status msi_set_timing(msi_index* ix, int32_t enable) {
+  g_err.clear();
+  if (!ix) return fail(MSI_EINVAL, "index is NULL");
+  ix->timing = enable != 0;
+  return MSI_OK;
+}
+
+}  // extern "C"

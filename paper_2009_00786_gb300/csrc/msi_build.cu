@@ -1,0 +1,581 @@
+// msi_build.cu -- index construction on the GPU (Section III-A, Algorithms 1-4).
+//
+// The paper's CPU pipeline (index workers computing iSAX summaries into per-root-
+// subtree buffers, then building subtrees with node splits) becomes four data-
+// parallel phases:
+//   1. summarise: one warp per series computes the canonical z-normalisation, the
+//      PAA, the SAX word and an interleaved 64-bit key (ConvertToiSAX, Algorithm 3);
+//   2. sort: stable LSD radix sort of (key, id), which groups series exactly as the
+//      iSAX tree does (the first `segments` key bits are the root subtree);
+//   3. split: a capacity-bounded binary split of key ranges, one bit per level, the
+//      flat equivalent of SplitNode (Algorithm 4), leaves as contiguous ranges;
+//   4. envelopes: per-leaf minimum / maximum symbol of every segment.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "msi_internal.cuh"
+
+namespace msi {
+namespace {
+
+#define MSI_TRY(x)                      \
+  do {                                  \
+    cudaError_t e_ = (x);               \
+    if (e_ != cudaSuccess) return e_;   \
+  } while (0)
+
+// ------------------------------------------------------------------ summarise
+constexpr int kSumWarps = 8;
+
+struct SumOut {
+  uint4* words;                 // [n] collection order
+  unsigned long long* keys;     // [n]
+  uint32_t* ids;                // [n] iota
+  float2* stats;                // [n] collection order (mu, 1/sigma)
+  float* z_out;                 // [n][len] or nullptr (borrowed data)
+  unsigned long long* first_bad;  // min id of a non-finite series
+};
+
+// Writes the word (symbols in a per-warp byte buffer) and the key.
+__device__ __forceinline__ void emit_word(uint8_t* sw, int sym_lane, int w, int bits, int64_t i,
+                                          const SumOut& o) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long key = interleave_key(sym_lane, w, bits);
+  if (lane == 0) {
+    const uint4 word = *reinterpret_cast<const uint4*>(sw);
+    o.words[i] = word;
+    o.keys[i] = key;
+    o.ids[i] = (uint32_t)i;
+  }
+}
+
+// Fast path: len = 128 * NC, segment length s = 4 * G with G a power of two <= 32
+// (every segment inside one 128-point chunk). Each lane holds its points in
+// registers as NC float4 values, so the series is read once with coalesced 512-byte
+// warp loads; sums follow the canonical order exactly.
+template <int NC>
+__global__ void __launch_bounds__(kSumWarps * 32)
+summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bits, int G,
+               const float* __restrict__ thr_up_g, SumOut o) {
+  __shared__ float thr_s[257];
+  __shared__ __align__(16) uint8_t sw_s[kSumWarps][16];
+  for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int len = NC * 128;
+  const int s = 4 * G;
+  const int segs_per_chunk = 128 / s;
+  uint8_t* sw = sw_s[warp];
+  for (int64_t i = (int64_t)blockIdx.x * kSumWarps + warp; i < n; i += (int64_t)gridDim.x * kSumWarps) {
+    const float4* row = reinterpret_cast<const float4*>(src + i * len);
+    float4 v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = __ldcs(row + c * 32 + lane);
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      acc = __fadd_rn(acc, v[c].x);
+      acc = __fadd_rn(acc, v[c].y);
+      acc = __fadd_rn(acc, v[c].z);
+      acc = __fadd_rn(acc, v[c].w);
+    }
+    const float mu = __fdiv_rn(tree32(acc), (float)len);
+    float acc2 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float d = __fsub_rn(v[c].x, mu);
+      acc2 = __fmaf_rn(d, d, acc2);
+      d = __fsub_rn(v[c].y, mu);
+      acc2 = __fmaf_rn(d, d, acc2);
+      d = __fsub_rn(v[c].z, mu);
+      acc2 = __fmaf_rn(d, d, acc2);
+      d = __fsub_rn(v[c].w, mu);
+      acc2 = __fmaf_rn(d, d, acc2);
+    }
+    const Moments m = finish_moments(mu, tree32(acc2), len);
+    if (m.flag < 0 && lane == 0) atomicMin(o.first_bad, (unsigned long long)i);
+    const bool cst = m.flag != 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float4 z;
+      z.x = cst ? 0.0f : znorm_value(v[c].x, m.mu, m.rsig);
+      z.y = cst ? 0.0f : znorm_value(v[c].y, m.mu, m.rsig);
+      z.z = cst ? 0.0f : znorm_value(v[c].z, m.mu, m.rsig);
+      z.w = cst ? 0.0f : znorm_value(v[c].w, m.mu, m.rsig);
+      if (o.z_out) __stcs(reinterpret_cast<float4*>(o.z_out + i * len) + c * 32 + lane, z);
+      float g = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
+      for (int off = 1; off < G; off <<= 1) g = __fadd_rn(g, __shfl_xor_sync(kFull, g, off));
+      if ((lane & (G - 1)) == 0) {
+        const int j = c * segs_per_chunk + lane / G;
+        if (j < 16) sw[j] = (uint8_t)sax_symbol(thr_s, card, __fdiv_rn(g, (float)s));
+      }
+    }
+    if (lane < 16 - w) sw[w + lane] = 0;
+    __syncwarp();
+    const int sym = lane < w ? sw[lane] : 0;
+    if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
+    emit_word(sw, sym, w, bits, i, o);
+    __syncwarp();
+  }
+}
+
+// Generic path: any length up to MSI_MAX_LEN and any segment length. The warp
+// stages the z values in shared memory and lanes j < w reduce their segment in the
+// canonical order.
+constexpr int kGenWarps = 4;
+__global__ void __launch_bounds__(kGenWarps * 32)
+summarise_generic(const float* __restrict__ src, int64_t n, int len, int w, int card, int bits,
+                  const float* __restrict__ thr_up_g, SumOut o) {
+  extern __shared__ float zs_all[];  // [kGenWarps][len]
+  __shared__ float thr_s[257];
+  __shared__ __align__(16) uint8_t sw_s[kGenWarps][16];
+  for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* zs = zs_all + warp * len;
+  uint8_t* sw = sw_s[warp];
+  const int s = len / w;
+  for (int64_t i = (int64_t)blockIdx.x * kGenWarps + warp; i < n; i += (int64_t)gridDim.x * kGenWarps) {
+    const float* x = src + i * len;
+    const Moments m = warp_moments_generic(x, len);
+    if (m.flag < 0 && lane == 0) atomicMin(o.first_bad, (unsigned long long)i);
+    const bool cst = m.flag != 0;
+    for (int t = lane; t < len; t += 32) {
+      const float z = cst ? 0.0f : znorm_value(x[t], m.mu, m.rsig);
+      zs[t] = z;
+    }
+    __syncwarp();
+    if (o.z_out)
+      for (int t = lane; t < len; t += 32) o.z_out[i * len + t] = zs[t];
+    int sym = 0;
+    if (lane < w) sym = sax_symbol(thr_s, card, paa_segment_generic(zs, lane, s));
+    if (lane < 16) sw[lane] = lane < w ? (uint8_t)sym : 0;
+    __syncwarp();
+    if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
+    emit_word(sw, sym, w, bits, i, o);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (u64 key, u32 value), 8-bit digits. Per pass: a tile
+// histogram (upsweep), an exclusive scan of the digit-major histogram, and a stable
+// scatter that ranks keys inside a tile with warp match + per-digit warp prefixes.
+constexpr int kRsThreads = 256;
+constexpr int kRsRounds = 16;
+constexpr int kRsTile = kRsThreads * kRsRounds;
+
+__global__ void __launch_bounds__(kRsThreads)
+rs_upsweep(const unsigned long long* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+           int64_t tiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+  for (int r = 0; r < kRsRounds; ++r) {
+    const int64_t idx = base + r * kRsThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+           unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+           const uint32_t* __restrict__ offs, int64_t tiles) {
+  constexpr int kW = kRsThreads / 32;
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wc[kW][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  run[threadIdx.x] = offs[(int64_t)threadIdx.x * tiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kRsRounds; ++r) {
+#pragma unroll
+    for (int q = 0; q < kW; ++q) wc[q][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t idx = base + r * kRsThreads + threadIdx.x;
+    const bool valid = idx < n;
+    const unsigned long long key = valid ? kin[idx] : 0ull;
+    const int d = valid ? (int)((key >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(kFull, d);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = run[threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < kW; ++q) {
+        const uint32_t c = wc[q][threadIdx.x];
+        wc[q][threadIdx.x] = acc;
+        acc += c;
+      }
+      run[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = wc[warp][d] + (uint32_t)rank;
+      kout[pos] = key;
+      vout[pos] = vin[idx];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ scan (u32)
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < kScanThreads / 32 ? ws[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, t, off);
+      if (lane >= off) t += y;
+    }
+    if (lane < kScanThreads / 32) ws[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t warp_off = warp ? ws[warp - 1] : 0;
+  *total = ws[kScanThreads / 32 - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += in[base + i];
+  uint32_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_sums_inplace(uint32_t* __restrict__ sums, int64_t m) {
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < m; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t v = i < m ? sums[i] : 0;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(v, &total);
+    if (i < m) sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_tiles(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ sums,
+           uint32_t* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0;
+    s += v[i];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+// Exclusive scan of n u32 values (in may equal out). `sums` holds ceil(n / tile).
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 0) return cudaSuccess;
+  scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+  scan_sums_inplace<<<1, kScanThreads, 0, s>>>(sums, tiles);
+  scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ leaf split
+struct Node {
+  uint32_t begin, end;
+};
+
+// One level of the binary split. A node at depth d (its keys share their first d
+// bits) becomes a leaf once d >= root_bits and it holds at most `cap` series;
+// otherwise it splits on key bit d into the members with that bit 0 and 1
+// (SplitNode, Algorithm 4: one more bit of one segment). Nodes whose keys are
+// identical in all 64 bits are cut into consecutive pieces of `cap`.
+// `out` holds node_cap entries; a level that would exceed it sets *overflow and
+// drops the node (the host then fails the build).
+__global__ void split_level(const unsigned long long* __restrict__ keys, const Node* __restrict__ in,
+                            const uint32_t* __restrict__ in_count, Node* __restrict__ out,
+                            uint32_t* __restrict__ out_count, uint8_t* __restrict__ leaf_flag, int depth,
+                            int root_bits, int total_bits, uint32_t cap, uint32_t node_cap,
+                            uint32_t* __restrict__ overflow) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *in_count) return;
+  const Node nd = in[i];
+  const uint32_t size = nd.end - nd.begin;
+  if (depth >= root_bits && size <= cap) {
+    leaf_flag[nd.begin] = 1;
+    return;
+  }
+  if (depth >= total_bits) {
+    for (uint32_t p = nd.begin; p < nd.end; p += cap) leaf_flag[p] = 1;
+    return;
+  }
+  const int bit = 63 - depth;
+  uint32_t lo = nd.begin, hi = nd.end;
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if ((keys[mid] >> bit) & 1ull) hi = mid; else lo = mid + 1;
+  }
+  if (lo > nd.begin) {
+    const uint32_t slot = atomicAdd(out_count, 1u);
+    if (slot < node_cap) out[slot] = Node{nd.begin, lo}; else *overflow = 1u;
+  }
+  if (lo < nd.end) {
+    const uint32_t slot = atomicAdd(out_count, 1u);
+    if (slot < node_cap) out[slot] = Node{lo, nd.end}; else *overflow = 1u;
+  }
+}
+
+__global__ void flags_to_u32(const uint8_t* __restrict__ f, int64_t n, uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = f[i];
+}
+
+__global__ void write_leaf_begin(const uint8_t* __restrict__ f, const uint32_t* __restrict__ rank, int64_t n,
+                                 uint32_t* __restrict__ leaf_begin) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && f[i]) leaf_begin[rank[i]] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ envelopes
+__global__ void envelopes(const uint4* __restrict__ words, const uint32_t* __restrict__ leaf_begin, int64_t L,
+                          const unsigned long long* __restrict__ keys_sorted, uint4* __restrict__ env,
+                          uint64_t* __restrict__ leaf_key) {
+  const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= L) return;
+  const uint32_t b = leaf_begin[l], e = leaf_begin[l + 1];
+  uint4 lo = make_uint4(~0u, ~0u, ~0u, ~0u), hi = make_uint4(0, 0, 0, 0);
+  for (uint32_t p = b + lane; p < e; p += 32) {
+    const uint4 w = words[p];
+    lo.x = __vminu4(lo.x, w.x); lo.y = __vminu4(lo.y, w.y); lo.z = __vminu4(lo.z, w.z); lo.w = __vminu4(lo.w, w.w);
+    hi.x = __vmaxu4(hi.x, w.x); hi.y = __vmaxu4(hi.y, w.y); hi.z = __vmaxu4(hi.z, w.z); hi.w = __vmaxu4(hi.w, w.w);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo.x = __vminu4(lo.x, __shfl_xor_sync(kFull, lo.x, off));
+    lo.y = __vminu4(lo.y, __shfl_xor_sync(kFull, lo.y, off));
+    lo.z = __vminu4(lo.z, __shfl_xor_sync(kFull, lo.z, off));
+    lo.w = __vminu4(lo.w, __shfl_xor_sync(kFull, lo.w, off));
+    hi.x = __vmaxu4(hi.x, __shfl_xor_sync(kFull, hi.x, off));
+    hi.y = __vmaxu4(hi.y, __shfl_xor_sync(kFull, hi.y, off));
+    hi.z = __vmaxu4(hi.z, __shfl_xor_sync(kFull, hi.z, off));
+    hi.w = __vmaxu4(hi.w, __shfl_xor_sync(kFull, hi.w, off));
+  }
+  if (lane == 0) {
+    env[2 * l] = lo;
+    env[2 * l + 1] = hi;
+    leaf_key[l] = keys_sorted[b];
+  }
+}
+
+__global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, const uint4* __restrict__ words_in,
+                                  const float2* __restrict__ stats_in, uint4* __restrict__ words_out,
+                                  float2* __restrict__ stats_out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const uint32_t id = perm[p];
+  words_out[p] = words_in[id];
+  stats_out[p] = stats_in[id];
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+struct Freer {
+  std::vector<void*> ptrs;
+  ~Freer() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T** p, size_t count) {
+    cudaError_t e = dalloc(p, count);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+// Builds every device structure of `ix` (shape fields, thresholds and data pointers
+// already set). `src_dev` holds the raw collection on the device; with `in_place`
+// it is ix->data_owned and is overwritten by its z-normalised values.
+cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cudaStream_t s,
+                        int64_t* first_bad, const char** stage) {
+  (void)in_place;
+  const int64_t n = ix->n;
+  const int len = ix->len, w = ix->w;
+  Freer tmp;
+  SumOut o;
+  unsigned long long* keys_alt;
+  uint32_t* ids_alt;
+  *stage = "allocating build scratch";
+  MSI_TRY(tmp.get(&o.words, n));
+  MSI_TRY(tmp.get(&o.keys, n));
+  MSI_TRY(tmp.get(&o.ids, n));
+  MSI_TRY(tmp.get(&o.stats, n));
+  MSI_TRY(tmp.get(&keys_alt, n));
+  MSI_TRY(tmp.get(&ids_alt, n));
+  MSI_TRY(tmp.get(&o.first_bad, 1));
+  o.z_out = ix->data_owned;  // nullptr when borrowed
+  MSI_TRY(cudaMemsetAsync(o.first_bad, 0xff, sizeof(unsigned long long), s));
+
+  // 1. summarise
+  *stage = "summarise";
+  int dev_sms = 0;
+  MSI_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ix->device));
+  const int s_len = ix->seglen;
+  const int G = s_len / 4;
+  const bool fast = (len % 128 == 0) && (len / 128) <= 16 && (s_len % 4 == 0) && G >= 1 && G <= 32 &&
+                    (G & (G - 1)) == 0 && ((len / 128) & (len / 128 - 1)) == 0;
+  if (fast) {
+    const int64_t blocks = std::min<int64_t>((n + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);
+    switch (len / 128) {
+      case 1: summarise_fast<1><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;
+      case 2: summarise_fast<2><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;
+      case 4: summarise_fast<4><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;
+      case 8: summarise_fast<8><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;
+      default: summarise_fast<16><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;
+    }
+  } else {
+    const size_t smem = sizeof(float) * (size_t)len * kGenWarps;
+    if (smem > 48 * 1024)
+      MSI_TRY(cudaFuncSetAttribute(summarise_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = std::min<int64_t>((n + kGenWarps - 1) / kGenWarps, (int64_t)dev_sms * 32);
+    summarise_generic<<<(unsigned)blocks, kGenWarps * 32, smem, s>>>(src_dev, n, len, w, ix->card, ix->bits,
+                                                                     ix->thr_up, o);
+  }
+  MSI_TRY(cudaGetLastError());
+  unsigned long long bad = 0;
+  MSI_TRY(cudaMemcpyAsync(&bad, o.first_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+  MSI_TRY(cudaStreamSynchronize(s));
+  if (bad != ~0ull) {
+    *first_bad = (int64_t)bad;
+    return cudaSuccess;
+  }
+  *first_bad = -1;
+
+  // 2. sort (key, id), stable, 8 passes of 8 bits
+  *stage = "sort";
+  const int64_t tiles = (n + kRsTile - 1) / kRsTile;
+  uint32_t *hist, *sums;
+  MSI_TRY(tmp.get(&hist, (size_t)tiles * 256));
+  MSI_TRY(tmp.get(&sums, (size_t)((tiles * 256 + kScanTile - 1) / kScanTile + 1)));
+  unsigned long long *ka = o.keys, *kb = keys_alt;
+  uint32_t *va = o.ids, *vb = ids_alt;
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 8 * pass;
+    rs_upsweep<<<(unsigned)tiles, kRsThreads, 0, s>>>(ka, n, shift, hist, tiles);
+    MSI_TRY(exclusive_scan(hist, hist, tiles * 256, sums, s));
+    rs_scatter<<<(unsigned)tiles, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, tiles);
+    MSI_TRY(cudaGetLastError());
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // after 8 passes the sorted keys / ids are back in (ka, va) == (o.keys, o.ids)
+
+  // 3. leaf split
+  *stage = "leaf split";
+  const int total_bits = std::min(64, w * ix->bits);
+  const int root_bits = std::min(w, total_bits);
+  // Nodes of one depth are disjoint non-empty ranges. Below depth root_bits there
+  // are at most 2^depth of them; from there on only nodes above capacity split, at
+  // most n / cap of them, two children each.
+  const int64_t node_cap = std::min<int64_t>(n, (1ll << root_bits) + 2 * (n / ix->cap) + 2);
+  Node *na, *nb;
+  uint32_t* counts;  // [2] in, out; [2] overflow
+  uint8_t* flags;
+  MSI_TRY(tmp.get(&na, node_cap));
+  MSI_TRY(tmp.get(&nb, node_cap));
+  MSI_TRY(tmp.get(&counts, 3));
+  MSI_TRY(tmp.get(&flags, n + 1));
+  MSI_TRY(cudaMemsetAsync(flags, 0, (size_t)n + 1, s));
+  MSI_TRY(cudaMemsetAsync(counts + 2, 0, sizeof(uint32_t), s));
+  const Node root{0u, (uint32_t)n};
+  const uint32_t one = 1;
+  MSI_TRY(cudaMemcpyAsync(na, &root, sizeof root, cudaMemcpyHostToDevice, s));
+  MSI_TRY(cudaMemcpyAsync(counts, &one, sizeof one, cudaMemcpyHostToDevice, s));
+  for (int depth = 0; depth <= total_bits; ++depth) {
+    MSI_TRY(cudaMemsetAsync(counts + 1, 0, sizeof(uint32_t), s));
+    split_level<<<grid_for(node_cap, 256), 256, 0, s>>>(ka, na, counts, nb, counts + 1, flags, depth, root_bits,
+                                                       total_bits, (uint32_t)ix->cap, (uint32_t)node_cap,
+                                                       counts + 2);
+    MSI_TRY(cudaGetLastError());
+    MSI_TRY(cudaMemcpyAsync(counts, counts + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    std::swap(na, nb);
+  }
+  // leaf begins: exclusive scan of the flags gives each leaf's rank
+  uint32_t* rank;
+  uint32_t* sums2;
+  MSI_TRY(tmp.get(&rank, n + 1));
+  MSI_TRY(tmp.get(&sums2, (size_t)((n + 1 + kScanTile - 1) / kScanTile + 1)));
+  flags_to_u32<<<grid_for(n + 1, 256), 256, 0, s>>>(flags, n + 1, rank);
+  MSI_TRY(exclusive_scan(rank, rank, n + 1, sums2, s));
+  uint32_t L32 = 0, node_overflow = 0;
+  MSI_TRY(cudaMemcpyAsync(&L32, rank + n, sizeof L32, cudaMemcpyDeviceToHost, s));
+  MSI_TRY(cudaMemcpyAsync(&node_overflow, counts + 2, sizeof node_overflow, cudaMemcpyDeviceToHost, s));
+  MSI_TRY(cudaStreamSynchronize(s));
+  ix->L = L32;
+  if (node_overflow || ix->L < 1) {
+    *stage = "leaf split: node list overflow";
+    return cudaErrorUnknown;
+  }
+
+  // 4. final structures
+  *stage = "allocating index";
+  MSI_TRY(dalloc(&ix->words, n));
+  MSI_TRY(dalloc(&ix->perm, n));
+  MSI_TRY(dalloc(&ix->stats, n));
+  MSI_TRY(dalloc(&ix->leaf_begin, ix->L + 1));
+  MSI_TRY(dalloc(&ix->env, 2 * ix->L));
+  MSI_TRY(dalloc(&ix->leaf_key, ix->L));
+  ix->device_bytes += (int64_t)n * (16 + 4 + 8) + (ix->L + 1) * 4 + ix->L * (32 + 8);
+  *stage = "envelopes";
+  write_leaf_begin<<<grid_for(n, 256), 256, 0, s>>>(flags, rank, n, ix->leaf_begin);
+  const uint32_t nn = (uint32_t)n;
+  MSI_TRY(cudaMemcpyAsync(ix->leaf_begin + ix->L, &nn, sizeof nn, cudaMemcpyHostToDevice, s));
+  MSI_TRY(cudaMemcpyAsync(ix->perm, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.words, o.stats, ix->words, ix->stats);
+  envelopes<<<grid_for(ix->L * 32, 256), 256, 0, s>>>(ix->words, ix->leaf_begin, ix->L, ka, ix->env, ix->leaf_key);
+  MSI_TRY(cudaGetLastError());
+  MSI_TRY(cudaStreamSynchronize(s));
+  return cudaSuccess;
+}
+
+}  // namespace msi

@@ -1,0 +1,293 @@
+// msi_internal.cuh -- index layout and device helpers shared by the library's
+// translation units (msi_api.cu, msi_build.cu, msi_query.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/msi.h"
+
+namespace msi {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ index
+// Device-side view of an index, passed to kernels by value.
+struct IndexView {
+  const float* data;        // [n][len] collection: z-normalised (owned) or raw (borrowed)
+  int data_is_z;            // 1: data holds z values; 0: z = (x - mu) * rsig on the fly
+  const float2* stats;      // [n] leaf order: (mu, 1/sigma), 1/sigma = 0 for constant series
+  const uint4* words;       // [n] leaf order: iSAX word, one byte per segment, zero padded
+  const uint32_t* perm;     // [n] leaf order -> collection id
+  const uint32_t* leaf_begin; // [L+1]
+  const uint4* env;         // [L][2]: per-segment min symbols, max symbols
+  const uint64_t* leaf_key; // [L]: interleaved key of each leaf's first member
+  const float* thr_up;      // [card+1]: region upper edges: thr_up[v] = smallest float >= beta_v,
+                            //   thr_up[0] = -inf, thr_up[card] = +inf (also the SAX thresholds)
+  const float* thr_lo;      // [card+1]: conservative lower edges: largest float <= beta_v
+  int64_t n;
+  int64_t L;
+  int len, w, card, bits, seglen;
+};
+
+// Per-query device state (one instance per in-flight query).
+struct QState {
+  float qpaa[16];
+  int32_t qsym[16];
+  unsigned long long qkey;
+  uint32_t seed_a, seed_b;      // leaf-order positions refined by the approximate search
+  unsigned int thr_bits;        // fp32 bits of the current k-th best squared distance
+  unsigned int leaf_count;      // leaves that passed the leaf filter
+  unsigned int next_leaf;       // work counter of the refinement kernel
+  unsigned int cand_count;      // candidates appended
+  unsigned int rc_count;        // FP64 re-checks appended
+  unsigned int final_bits;      // k-th smallest candidate squared distance (fp32 bits)
+  unsigned int leaves_processed;
+  unsigned int series_lb;
+  unsigned int series_refined;
+  int32_t flag;                 // 1 constant query, -1 non-finite query
+};
+
+// Device-wide work counters (u64), in msi_query_stats field order.
+enum StatSlot {
+  ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_SURVIVED, ST_LEAVES_PROCESSED, ST_SERIES_LB,
+  ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_COUNT
+};
+
+struct QueryView {
+  float* qz;                    // [len]
+  float* T;                     // [w][card] squared per-segment gap, query PAA to each symbol
+  QState* st;
+  uint32_t* leaf_list;          // [L]
+  float* leaf_lb2;              // [L]
+  unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
+  double* rc_d;                 // [n]
+  uint32_t* rc_id;              // [n]
+  unsigned long long* counters; // [ST_COUNT]
+  int k;
+  float eps;                    // relative margin on squared distances
+  float tau;                    // absolute margin on lower bounds (distance units)
+};
+
+// ----------------------------------------------------- canonical fp32 arithmetic
+// The z-normalisation and PAA are computed in one fixed order (the CPU oracle
+// follows the same order) because the SAX symbols are integers decided by them:
+//   lane of point t = (t / 4) mod 32; each lane sums its points in increasing t;
+//   the 32 lane partials are combined by a pairwise tree in lane order;
+//   mu = S1 / n; V likewise over fma(d, d, .) with d = x_t - mu;
+//   sigma = sqrt(V / n); constant if sigma < 1e-30 or sigma <= 1e-6 |mu| (z = 0);
+//   z_t = (x_t - mu) * (1 / sigma); every step a single IEEE rounding.
+__device__ __forceinline__ float tree32(float v) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, off));
+  return v;
+}
+
+struct Moments {
+  float mu;
+  float rsig;  // 1/sigma, 0 for a constant series
+  int flag;    // 0 normal, 1 constant, -1 non-finite
+};
+
+// mu = S1 / n already rounded; v = the combined sum of squared deviations.
+__device__ __forceinline__ Moments finish_moments(float mu, float v, int len) {
+  Moments m;
+  const float n = (float)len;
+  m.mu = mu;
+  const float sigma = __fsqrt_rn(__fdiv_rn(v, n));
+  if (!isfinite(m.mu) || !isfinite(sigma)) {
+    m.flag = -1;
+    m.rsig = 0.0f;
+  } else if (sigma < 1e-30f || sigma <= __fmul_rn(1e-6f, fabsf(m.mu))) {
+    m.flag = 1;
+    m.rsig = 0.0f;
+  } else {
+    m.flag = 0;
+    m.rsig = __fdiv_rn(1.0f, sigma);
+  }
+  return m;
+}
+
+// Canonical moments of one series in global or shared memory, any length (one warp).
+__device__ __forceinline__ Moments warp_moments_generic(const float* x, int len) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.0f;
+  for (int c = 0; c * 128 < len; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = c * 128 + 4 * lane + i;
+      if (t < len) acc = __fadd_rn(acc, x[t]);
+    }
+  const float mu = __fdiv_rn(tree32(acc), (float)len);
+  float acc2 = 0.0f;
+  for (int c = 0; c * 128 < len; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = c * 128 + 4 * lane + i;
+      if (t < len) {
+        const float d = __fsub_rn(x[t], mu);
+        acc2 = __fmaf_rn(d, d, acc2);
+      }
+    }
+  return finish_moments(mu, tree32(acc2), len);
+}
+
+__device__ __forceinline__ float znorm_value(float x, float mu, float rsig) {
+  return __fmul_rn(__fsub_rn(x, mu), rsig);
+}
+
+// Canonical PAA of segment j from z values in memory: groups of 4 consecutive points
+// summed in order, groups combined by a pairwise tree in group order when the
+// segment length is 4 * 2^m; a sequential sum otherwise; then divided by s.
+__device__ __forceinline__ float paa_segment_generic(const float* z, int j, int s) {
+  const float* seg = z + j * s;
+  float sum;
+  const int g = s >> 2;
+  if ((s & 3) == 0 && (g & (g - 1)) == 0) {
+    // pairwise tree over the group sums, as a binary-counter stack
+    float stack[16];
+    int level[16];
+    int top = 0;
+    for (int i = 0; i < g; ++i) {
+      float v = __fadd_rn(__fadd_rn(__fadd_rn(seg[4 * i], seg[4 * i + 1]), seg[4 * i + 2]), seg[4 * i + 3]);
+      int lv = 0;
+      while (top > 0 && level[top - 1] == lv) {
+        v = __fadd_rn(stack[top - 1], v);
+        --top;
+        ++lv;
+      }
+      stack[top] = v;
+      level[top] = lv;
+      ++top;
+    }
+    sum = stack[0];
+  } else {
+    sum = seg[0];
+    for (int t = 1; t < s; ++t) sum = __fadd_rn(sum, seg[t]);
+  }
+  return __fdiv_rn(sum, (float)s);
+}
+
+// SAX symbol: number of thresholds t_1..t_{card-1} at or below p (thr_up[1..card-1]).
+__device__ __forceinline__ int sax_symbol(const float* thr_up_s, int card, float p) {
+  int lo = 1, hi = card;  // answer sym = (first index v in [1, card) with thr_up[v] > p) - 1
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (thr_up_s[mid] <= p) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Interleaved key of a word from one symbol per lane (lanes j < w hold sym_j): bit
+// planes from the most significant, each plane listing segment 0 first; the first
+// 64 bits, left aligned.
+__device__ __forceinline__ unsigned long long interleave_key(int sym, int w, int bits) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long key = 0;
+  int used = 0;
+  for (int p = bits - 1; p >= 0 && used < 64; --p) {
+    const unsigned m = __ballot_sync(kFull, lane < w && ((sym >> p) & 1));
+    const unsigned rev = __brev(m) >> (32 - w);  // segment 0 in the top bit of w
+    const int take = (64 - used) < w ? (64 - used) : w;
+    key = (key << take) | (unsigned long long)(rev >> (w - take));
+    used += take;
+  }
+  return used < 64 ? key << (64 - used) : key;
+}
+
+// ------------------------------------------------------------------ margins
+// Lower-bound pruning threshold for a k-th best squared distance `thr`:
+// (sqrt(thr) (1 + eps) + tau)^2, rounded up; +inf while thr is unknown.
+__device__ __forceinline__ float lb_bound2(unsigned thr_bits, float eps, float tau) {
+  const float thr = __uint_as_float(thr_bits);
+  if (!(thr < INFINITY)) return INFINITY;
+  const float b = __fadd_ru(__fmul_ru(__fsqrt_ru(thr), 1.0f + eps), tau);
+  return __fmul_ru(b, b);
+}
+// Squared distances at or below thr (1 + eps) are kept as candidates.
+__device__ __forceinline__ float keep_bound2(unsigned thr_bits, float eps) {
+  const float thr = __uint_as_float(thr_bits);
+  if (!(thr < INFINITY)) return INFINITY;
+  return __fmul_ru(thr, 1.0f + eps);
+}
+
+}  // namespace msi
+
+// -------------------------------------------------------------- host index
+struct msi_index {
+  int device = 0;
+  int64_t n = 0;
+  int32_t len = 0, w = 0, card = 0, bits = 0, seglen = 0, cap = 0;
+  uint32_t flags = 0;
+  bool data_is_z = false;
+  float* data_owned = nullptr;
+  const float* data = nullptr;
+  uint4* words = nullptr;
+  uint32_t* perm = nullptr;
+  float2* stats = nullptr;
+  int64_t L = 0;
+  uint32_t* leaf_begin = nullptr;
+  uint4* env = nullptr;
+  uint64_t* leaf_key = nullptr;
+  float* thr_up = nullptr;
+  float* thr_lo = nullptr;
+  float h_thr_up[257];
+  float h_thr_lo[257];
+  int64_t device_bytes = 0;
+  cudaStream_t own_stream = nullptr;
+  // query workspace (allocated on first use)
+  bool ws_ready = false;
+  msi::QueryView qv{};
+  float* ws_qraw = nullptr;     // staging for host queries [kQueryChunk][len]
+  int64_t* ws_ids = nullptr;    // staging for host outputs [kQueryChunk][MSI_MAX_K]
+  float* ws_dists = nullptr;
+  int refine_grid = 0;
+  size_t refine_smem = 0;
+  int refine_smem_k = -1;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // refinement timing, one pair per query
+  double refine_ms = 0.0;
+  int64_t refine_launches = 0;
+
+  msi::IndexView view() const {
+    msi::IndexView v;
+    v.data = data;
+    v.data_is_z = data_is_z ? 1 : 0;
+    v.stats = stats;
+    v.words = words;
+    v.perm = perm;
+    v.leaf_begin = leaf_begin;
+    v.env = env;
+    v.leaf_key = leaf_key;
+    v.thr_up = thr_up;
+    v.thr_lo = thr_lo;
+    v.n = n;
+    v.L = L;
+    v.len = len;
+    v.w = w;
+    v.card = card;
+    v.bits = bits;
+    v.seglen = seglen;
+    return v;
+  }
+};
+
+namespace msi {
+constexpr int kQueryChunk = 1024;
+
+// Build pipeline (msi_build.cu). All device pointers; stream-ordered.
+cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cudaStream_t s,
+                        int64_t* first_bad, const char** stage);
+
+// Query pipeline (msi_query.cu).
+cudaError_t query_setup(msi_index* ix);
+cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
+                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b);
+cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
+cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
+                         cudaStream_t s);
+}  // namespace msi

@@ -1,0 +1,734 @@
+// msi_query.cu -- exact k-NN query answering on the GPU (Section III-B, Algorithms 5-9).
+//
+// The paper's search workers, priority queues and BSF lock become one short chain
+// of kernels per query, all on one stream:
+//   q_prep         query iSAX summary (Algorithm 5, first step) and the per-segment
+//                  squared-gap table; the approximate-search leaf found by the
+//                  query's key, as descending the tree would (Algorithm 5, approxSearch);
+//   q_seed         real distances of that leaf's members: the initial BSF;
+//   q_seed_select  (k > 1) the k-th smallest of them;
+//   q_leaf_filter  lower bound of every leaf against the BSF; survivors listed
+//                  (TraverseRootSubtree, Algorithm 7, flattened over the leaves);
+//   q_refine       persistent CTAs take listed leaves, re-test each leaf against the
+//                  current BSF (ProcessQueue, Algorithm 8), lower-bound every member
+//                  from its SAX word and compute the real distance of the survivors
+//                  (CalculateRealDistance, Algorithm 9); the BSF is an atomicMin on the
+//                  bits of a non-negative float;
+//   q_final_select the k-th smallest candidate squared distance;
+//   q_recheck      FP64 distances of every candidate within the fp32 error margin of it;
+//   q_final_topk   the k smallest by (FP64 distance, id): the answer.
+// Pruning is conservative: a bound prunes only when it exceeds the BSF by more than
+// the fp32 rounding of both sides can explain, so the answer is the exact one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "msi_internal.cuh"
+
+namespace msi {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 1024;  // leaf positions lower-bounded per refinement step
+
+// A candidate: (fp32 squared distance bits << 32) | leaf-order position.
+__device__ __forceinline__ unsigned long long pack(float d2, uint32_t pos) {
+  return ((unsigned long long)__float_as_uint(d2) << 32) | pos;
+}
+
+// Squared Euclidean distance between the z-normalised series `id` and the
+// z-normalised query in shared memory; one warp, result in every lane. fp32 with a
+// fused multiply-add per point.
+__device__ __forceinline__ float warp_sqdist(const IndexView& ix, uint32_t id, float2 ms, const float* qs) {
+  const int lane = threadIdx.x & 31;
+  const float* row = ix.data + (size_t)id * ix.len;
+  float acc = 0.0f;
+  if ((ix.len & 3) == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    const float4* q4 = reinterpret_cast<const float4*>(qs);
+    const int n4 = ix.len >> 2;
+    if (ix.data_is_z) {
+      for (int c = lane; c < n4; c += 32) {
+        const float4 x = __ldg(r4 + c), q = q4[c];
+        float d = __fsub_rn(x.x, q.x); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x.y, q.y); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x.z, q.z); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x.w, q.w); acc = __fmaf_rn(d, d, acc);
+      }
+    } else {
+      for (int c = lane; c < n4; c += 32) {
+        const float4 x = __ldg(r4 + c), q = q4[c];
+        float d = __fsub_rn(znorm_value(x.x, ms.x, ms.y), q.x); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(znorm_value(x.y, ms.x, ms.y), q.y); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(znorm_value(x.z, ms.x, ms.y), q.z); acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(znorm_value(x.w, ms.x, ms.y), q.w); acc = __fmaf_rn(d, d, acc);
+      }
+    }
+  } else {
+    for (int t = lane; t < ix.len; t += 32) {
+      const float x = __ldg(row + t);
+      const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
+      const float d = __fsub_rn(z, qs[t]);
+      acc = __fmaf_rn(d, d, acc);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+  return acc;
+}
+
+// Squared iSAX lower bound of one SAX word: s * sum_j T[j][sym_j].
+__device__ __forceinline__ float word_lb2(uint4 wd, const float* Ts, int w, int card, float s) {
+  const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j < w) acc = __fadd_rn(acc, Ts[j * card + ((parts[j >> 2] >> (8 * (j & 3))) & 255)]);
+  }
+  return __fmul_rn(acc, s);
+}
+
+// Squared iSAX lower bound of a leaf from its per-segment symbol envelope: the gap
+// between the query's PAA value and the region from the lower edge of the smallest
+// symbol to the upper edge of the largest (0 inside).
+__device__ __forceinline__ float leaf_lb2(const IndexView& ix, int64_t l, const float* paa_s,
+                                          const float* thr_lo_s, const float* thr_up_s) {
+  const uint4 lo = ix.env[2 * l], hi = ix.env[2 * l + 1];
+  const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j < ix.w) {
+      const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
+      const float p = paa_s[j], lower = thr_lo_s[sl], upper = thr_up_s[sh + 1];
+      float d = 0.0f;
+      if (p < lower) d = __fsub_rn(lower, p);
+      else if (p > upper) d = __fsub_rn(p, upper);
+      acc = __fadd_rn(acc, __fmul_rn(d, d));
+    }
+  }
+  return __fmul_rn(acc, (float)ix.seglen);
+}
+
+// k-th smallest (1-based) of `count` 32-bit keys read through get(i), by one block:
+// four 8-bit radix passes with a shared histogram.
+template <typename Get>
+__device__ uint32_t block_select_u32(Get get, uint32_t count, uint32_t k, uint32_t* hist, uint32_t* sel) {
+  uint32_t prefix = 0, mask = 0, kk = k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+      const uint32_t v = get(i);
+      if ((v & mask) == prefix) atomicAdd(&hist[(v >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t loc[8], tot = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; tot += loc[b]; }
+      uint32_t incl = tot;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const uint32_t excl = incl - tot;
+      if (excl < kk && kk <= incl) {
+        uint32_t cum = excl;
+        for (int b = 0; b < 8; ++b) {
+          if (cum + loc[b] >= kk) { sel[0] = (uint32_t)(lane * 8 + b); sel[1] = kk - cum; break; }
+          cum += loc[b];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= sel[0] << shift;
+    mask |= 255u << shift;
+    kk = sel[1];
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// ------------------------------------------------------------------ q_prep
+__global__ void __launch_bounds__(kThreads)
+q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
+  extern __shared__ float zs[];  // [len]
+  __shared__ float thr_up_s[257], thr_lo_s[257];
+  __shared__ float paa_s[16];
+  __shared__ int sym_s[16];
+  __shared__ unsigned long long key_s;
+  __shared__ int lo_s, hi_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int v = tid; v <= ix.card; v += blockDim.x) {
+    thr_up_s[v] = ix.thr_up[v];
+    thr_lo_s[v] = ix.thr_lo[v];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const Moments m = warp_moments_generic(q, ix.len);
+    for (int t = lane; t < ix.len; t += 32) zs[t] = m.flag != 0 ? 0.0f : znorm_value(q[t], m.mu, m.rsig);
+    __syncwarp();
+    int sym = 0;
+    if (lane < ix.w) {
+      const float p = paa_segment_generic(zs, lane, ix.seglen);
+      paa_s[lane] = p;
+      sym = sax_symbol(thr_up_s, ix.card, p);
+      sym_s[lane] = sym;
+    }
+    const unsigned long long key = interleave_key(sym, ix.w, ix.bits);
+    if (lane == 0) {
+      key_s = key;
+      qv.st->flag = m.flag;
+      if (m.flag < 0) atomicAdd(&qv.counters[ST_BAD_QUERY], 1ull);
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < ix.len; t += blockDim.x) qv.qz[t] = zs[t];
+  const int wc = ix.w * ix.card;
+  for (int e = tid; e < wc; e += blockDim.x) {
+    const int j = e / ix.card, v = e - j * ix.card;
+    const float p = paa_s[j];
+    const float lower = thr_lo_s[v], upper = thr_up_s[v + 1];
+    float d = 0.0f;
+    if (p < lower) d = __fsub_rn(lower, p);
+    else if (p > upper) d = __fsub_rn(p, upper);
+    qv.T[e] = __fmul_rn(d, d);
+  }
+  if (tid < ix.w) {
+    qv.st->qpaa[tid] = paa_s[tid];
+    qv.st->qsym[tid] = sym_s[tid];
+  }
+  // approximate search: the last leaf whose first key is <= the query key
+  const unsigned long long qkey = key_s;
+  if (tid == 0) { lo_s = 0; hi_s = (int)ix.L; }
+  __syncthreads();
+  while (true) {
+    const int lo = lo_s, hi = hi_s;
+    if (hi - lo <= 1) break;
+    const int step = (hi - lo + blockDim.x - 1) / blockDim.x;
+    const int idx = lo + tid * step;
+    const bool pred = idx < hi && ix.leaf_key[idx] <= qkey;
+    const int cnt = __syncthreads_count(pred);
+    if (tid == 0) {
+      if (cnt == 0) { hi_s = lo + 1; }  // query key below every probe: keep lo
+      else {
+        const int nlo = lo + (cnt - 1) * step;
+        lo_s = nlo;
+        hi_s = min(hi, nlo + step);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int64_t l = lo_s;
+    int64_t a = ix.leaf_begin[l], b = ix.leaf_begin[l + 1];
+    if (b - a < k) {
+      b = min(ix.n, max(b, a + (int64_t)k));
+      a = min(a, b - (int64_t)k);
+    }
+    QState* st = qv.st;
+    st->qkey = qkey;
+    st->seed_a = (uint32_t)a;
+    st->seed_b = (uint32_t)b;
+    st->thr_bits = 0x7f800000u;
+    st->leaf_count = 0;
+    st->next_leaf = 0;
+    st->cand_count = (uint32_t)(b - a);
+    st->rc_count = 0;
+    st->final_bits = 0;
+    st->leaves_processed = 0;
+    st->series_lb = 0;
+    st->series_refined = 0;
+  }
+}
+
+// ------------------------------------------------------------------ q_seed
+__global__ void __launch_bounds__(kThreads)
+q_seed(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float qs[];
+  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  __syncthreads();
+  const uint32_t a = qv.st->seed_a, b = qv.st->seed_b;
+  const uint32_t warps = gridDim.x * (kThreads / 32);
+  for (uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); gw < b - a; gw += warps) {
+    const uint32_t pos = a + gw;
+    const uint32_t id = ix.perm[pos];
+    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
+    const float d2 = warp_sqdist(ix, id, ms, qs);
+    if ((threadIdx.x & 31) == 0) {
+      qv.cand[gw] = pack(d2, pos);
+      if (qv.k == 1) atomicMin(&qv.st->thr_bits, __float_as_uint(d2));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+q_seed_select(QueryView qv) {
+  __shared__ uint32_t hist[256], sel[2];
+  const uint32_t count = qv.st->cand_count;
+  const unsigned long long* c = qv.cand;
+  const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
+                                        (uint32_t)qv.k, hist, sel);
+  if (threadIdx.x == 0) qv.st->thr_bits = kth;
+}
+
+// ------------------------------------------------------------------ q_leaf_filter
+__global__ void __launch_bounds__(kThreads)
+q_leaf_filter(IndexView ix, QueryView qv) {
+  __shared__ float thr_up_s[257], thr_lo_s[257], paa_s[16];
+  for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
+    thr_up_s[v] = ix.thr_up[v];
+    thr_lo_s[v] = ix.thr_lo[v];
+  }
+  if (threadIdx.x < ix.w) paa_s[threadIdx.x] = qv.st->qpaa[threadIdx.x];
+  __syncthreads();
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = false;
+  float lb2 = 0.0f;
+  if (l < ix.L) {
+    const uint32_t b = ix.leaf_begin[l], e = ix.leaf_begin[l + 1];
+    const uint32_t sa = qv.st->seed_a, sb = qv.st->seed_b;
+    if (!(b >= sa && e <= sb)) {
+      lb2 = leaf_lb2(ix, l, paa_s, thr_lo_s, thr_up_s);
+      keep = lb2 <= lb_bound2(qv.st->thr_bits, qv.eps, qv.tau);
+    }
+  }
+  const unsigned m = __ballot_sync(kFull, keep);
+  if (m) {
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(&qv.st->leaf_count, (uint32_t)__popc(m));
+    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+    if (keep) {
+      const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
+      qv.leaf_list[slot] = (uint32_t)l;
+      qv.leaf_lb2[slot] = lb2;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ q_refine
+struct RefineSmem {
+  static size_t bytes(int w, int card, int len, int k) {
+    size_t b = sizeof(float) * (size_t)w * card;  // T
+    b = (b + 15) & ~size_t(15);
+    b += sizeof(float) * (size_t)((len + 3) & ~3);  // query z
+    b += sizeof(uint32_t) * kChunk * 2;              // survivor positions, d2
+    if (k > 1) b += sizeof(uint32_t) * 2 * (size_t)(k + kChunk);  // top-k buffer + compaction
+    return b;
+  }
+};
+
+template <bool KONE>
+__global__ void __launch_bounds__(kThreads)
+q_refine(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Ts = reinterpret_cast<float*>(smem);
+  size_t off = ((sizeof(float) * (size_t)ix.w * ix.card) + 15) & ~size_t(15);
+  float* qs = reinterpret_cast<float*>(smem + off);
+  off += sizeof(float) * (size_t)((ix.len + 3) & ~3);
+  uint32_t* surv = reinterpret_cast<uint32_t*>(smem + off);
+  off += sizeof(uint32_t) * kChunk;
+  float* sd2 = reinterpret_cast<float*>(smem + off);
+  off += sizeof(uint32_t) * kChunk;
+  uint32_t* bufA = reinterpret_cast<uint32_t*>(smem + off);
+  uint32_t* bufB = bufA + (qv.k + kChunk);
+  __shared__ uint32_t s_li, s_ns, s_bc, s_thr, s_local, s_hist[256], s_sel[2];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wc = ix.w * ix.card;
+  for (int e = tid; e < wc; e += blockDim.x) Ts[e] = qv.T[e];
+  for (int t = tid; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  if (tid == 0) { s_bc = 0; s_local = 0x7f800000u; }
+  QState* st = qv.st;
+  const uint32_t leaf_count = st->leaf_count;
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const float seglen = (float)ix.seglen;
+  const uint32_t bcap = (uint32_t)qv.k + kChunk;
+  uint32_t n_lb = 0, n_ref = 0, n_leaf = 0;
+  volatile unsigned int* thr_v = &st->thr_bits;
+  __syncthreads();
+
+  while (true) {
+    if (tid == 0) {
+      s_li = atomicAdd(&st->next_leaf, 1u);
+      s_thr = *thr_v;
+    }
+    __syncthreads();
+    const uint32_t li = s_li;
+    if (li >= leaf_count) break;
+    const uint32_t l = qv.leaf_list[li];
+    if (qv.leaf_lb2[li] > lb_bound2(s_thr, qv.eps, qv.tau)) {
+      __syncthreads();
+      continue;
+    }
+    const uint32_t b = ix.leaf_begin[l], e = ix.leaf_begin[l + 1];
+    ++n_leaf;
+    for (uint32_t cb = b; cb < e; cb += kChunk) {
+      if (tid == 0) {
+        s_ns = 0;
+        s_thr = *thr_v;
+      }
+      __syncthreads();
+      const float bound2 = lb_bound2(s_thr, qv.eps, qv.tau);
+      const uint32_t ce = min(e, cb + kChunk);
+      for (uint32_t p = cb + tid; p < ce; p += blockDim.x) {
+        if (p >= sa && p < sb) continue;
+        ++n_lb;
+        if (word_lb2(ix.words[p], Ts, ix.w, ix.card, seglen) <= bound2) surv[atomicAdd(&s_ns, 1u)] = p;
+      }
+      __syncthreads();
+      const uint32_t ns = s_ns;
+      for (uint32_t i = warp; i < ns; i += kThreads / 32) {
+        const uint32_t p = surv[i];
+        const uint32_t id = ix.perm[p];
+        const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[p];
+        const float d2 = warp_sqdist(ix, id, ms, qs);
+        if (lane == 0) {
+          ++n_ref;
+          const unsigned thr = *thr_v;
+          if (d2 <= keep_bound2(thr, qv.eps)) qv.cand[atomicAdd(&st->cand_count, 1u)] = pack(d2, p);
+          if (KONE) atomicMin(&st->thr_bits, __float_as_uint(d2));
+          else sd2[i] = d2;
+        }
+      }
+      __syncthreads();
+      if (!KONE && ns > 0) {
+        // buffered local top-k: keep values at or below the local k-th best; when
+        // k or more are held, select the k-th, keep k of them, publish the bound
+        const float local = __uint_as_float(s_local);
+        for (uint32_t i = tid; i < ns; i += blockDim.x)
+          if (sd2[i] <= local) {
+            const uint32_t slot = atomicAdd(&s_bc, 1u);
+            if (slot < bcap) bufA[slot] = __float_as_uint(sd2[i]);
+          }
+        __syncthreads();
+        const uint32_t bc = min(s_bc, bcap);
+        if (bc >= (uint32_t)qv.k) {
+          const uint32_t kth = block_select_u32([&](uint32_t i) { return bufA[i]; }, bc, (uint32_t)qv.k,
+                                                s_hist, s_sel);
+          if (tid == 0) { s_ns = 0; s_local = kth; }
+          __syncthreads();
+          // compact: all values below kth, then values equal to kth up to k in total
+          for (uint32_t i = tid; i < bc; i += blockDim.x)
+            if (bufA[i] < kth) bufB[atomicAdd(&s_ns, 1u)] = bufA[i];
+          __syncthreads();
+          for (uint32_t i = tid; i < bc; i += blockDim.x)
+            if (bufA[i] == kth) {
+              const uint32_t slot = atomicAdd(&s_ns, 1u);
+              if (slot < (uint32_t)qv.k) bufB[slot] = kth;
+            }
+          __syncthreads();
+          const uint32_t kept = min(s_ns, (uint32_t)qv.k);
+          for (uint32_t i = tid; i < kept; i += blockDim.x) bufA[i] = bufB[i];
+          if (tid == 0) {
+            s_bc = kept;
+            atomicMin(&st->thr_bits, kth);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // reduce the work counters
+  for (int o = 16; o > 0; o >>= 1) {
+    n_lb += __shfl_xor_sync(kFull, n_lb, o);
+    n_ref += __shfl_xor_sync(kFull, n_ref, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&st->series_lb, n_lb);
+    atomicAdd(&st->series_refined, n_ref);
+  }
+  if (tid == 0) atomicAdd(&st->leaves_processed, n_leaf);
+}
+
+// ------------------------------------------------------------------ final pick
+__global__ void __launch_bounds__(1024)
+q_final_select(QueryView qv) {
+  __shared__ uint32_t hist[256], sel[2];
+  const uint32_t count = qv.st->cand_count;
+  const unsigned long long* c = qv.cand;
+  const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
+                                        (uint32_t)qv.k, hist, sel);
+  if (threadIdx.x == 0) qv.st->final_bits = __float_as_uint(__fmul_ru(__uint_as_float(kth), 1.0f + qv.eps));
+}
+
+// FP64 squared distance, summed in increasing t, no fused operations.
+__device__ __forceinline__ double sqdist64(const IndexView& ix, uint32_t id, float2 ms, const float* qz) {
+  const float* row = ix.data + (size_t)id * ix.len;
+  double acc = 0.0;
+  for (int t = 0; t < ix.len; ++t) {
+    const float x = row[t];
+    const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
+    const double d = __dsub_rn((double)z, (double)qz[t]);
+    acc = __dadd_rn(acc, __dmul_rn(d, d));
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kThreads)
+q_recheck(IndexView ix, QueryView qv) {
+  const uint32_t count = qv.st->cand_count;
+  const uint32_t bound = qv.st->final_bits;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const unsigned long long c = qv.cand[i];
+    if ((uint32_t)(c >> 32) > bound) continue;
+    const uint32_t pos = (uint32_t)c;
+    const uint32_t id = ix.perm[pos];
+    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
+    const double D = sqdist64(ix, id, ms, qv.qz);
+    const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
+    qv.rc_d[slot] = D;
+    qv.rc_id[slot] = id;
+  }
+}
+
+// (distance bits, id) lexicographic order; non-negative doubles order as their bits.
+__device__ __forceinline__ bool key_less(unsigned long long da, uint32_t ia, unsigned long long db, uint32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
+__device__ void block_bitonic(unsigned long long* sk, uint32_t* si, int n) {
+  for (int size = 2; size <= n; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+        const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+        const bool asc = (lo & size) == 0;
+        if (key_less(sk[hi], si[hi], sk[lo], si[lo]) == asc) {
+          const unsigned long long tk = sk[lo]; sk[lo] = sk[hi]; sk[hi] = tk;
+          const uint32_t ti = si[lo]; si[lo] = si[hi]; si[hi] = ti;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+constexpr int kSortCap = 2048;  // (distance, id) pairs sorted in shared memory
+
+__global__ void __launch_bounds__(1024)
+q_final_topk(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out) {
+  __shared__ unsigned long long sk[kSortCap];
+  __shared__ uint32_t si[kSortCap];
+  __shared__ uint32_t hist[256], sel[2], s_cnt;
+  const uint32_t R = qv.st->rc_count;
+  const int k = qv.k;
+  int nsort;
+  if (R <= (uint32_t)kSortCap) {
+    nsort = 1;
+    while (nsort < (int)R) nsort <<= 1;
+    for (int i = threadIdx.x; i < nsort; i += blockDim.x) {
+      const bool v = i < (int)R;
+      sk[i] = v ? (unsigned long long)__double_as_longlong(qv.rc_d[i]) : ~0ull;
+      si[i] = v ? qv.rc_id[i] : ~0u;
+    }
+    __syncthreads();
+  } else {
+    // exact k-th (distance, id) key by a 12-digit radix select, then the k keys at
+    // or below it
+    unsigned long long pre_hi = 0, mask_hi = 0;
+    uint32_t pre_lo = 0, mask_lo = 0, kk = (uint32_t)k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int dgt = 0; dgt < 12; ++dgt) {
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) {
+        const unsigned long long dk = (unsigned long long)__double_as_longlong(qv.rc_d[i]);
+        const uint32_t id = qv.rc_id[i];
+        if ((dk & mask_hi) != pre_hi || (id & mask_lo) != pre_lo) continue;
+        const uint32_t b = dgt < 8 ? (uint32_t)(dk >> (8 * (7 - dgt))) & 255u : (id >> (8 * (11 - dgt))) & 255u;
+        atomicAdd(&hist[b], 1u);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t loc[8], tot = 0;
+        for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; tot += loc[b]; }
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - tot;
+        if (excl < kk && kk <= incl) {
+          uint32_t cum = excl;
+          for (int b = 0; b < 8; ++b) {
+            if (cum + loc[b] >= kk) { sel[0] = (uint32_t)(lane * 8 + b); sel[1] = kk - cum; break; }
+            cum += loc[b];
+          }
+        }
+      }
+      __syncthreads();
+      if (dgt < 8) {
+        pre_hi |= (unsigned long long)sel[0] << (8 * (7 - dgt));
+        mask_hi |= 255ull << (8 * (7 - dgt));
+      } else {
+        pre_lo |= sel[0] << (8 * (11 - dgt));
+        mask_lo |= 255u << (8 * (11 - dgt));
+      }
+      kk = sel[1];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) {
+      const unsigned long long dk = (unsigned long long)__double_as_longlong(qv.rc_d[i]);
+      const uint32_t id = qv.rc_id[i];
+      if (dk < pre_hi || (dk == pre_hi && id <= pre_lo)) {
+        const uint32_t slot = atomicAdd(&s_cnt, 1u);
+        if (slot < (uint32_t)kSortCap) { sk[slot] = dk; si[slot] = id; }
+      }
+    }
+    __syncthreads();
+    const int got = (int)min(s_cnt, (uint32_t)kSortCap);
+    nsort = 1;
+    while (nsort < got) nsort <<= 1;
+    for (int i = got + threadIdx.x; i < nsort; i += blockDim.x) { sk[i] = ~0ull; si[i] = ~0u; }
+    __syncthreads();
+  }
+  block_bitonic(sk, si, nsort);
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    ids_out[r] = (int64_t)si[r];
+    if (dists_out) dists_out[r] = __double2float_rn(__dsqrt_rn(__longlong_as_double((long long)sk[r])));
+  }
+  if (threadIdx.x == 0) {
+    const QState* st = qv.st;
+    unsigned long long* c = qv.counters;
+    atomicAdd(&c[ST_QUERIES], 1ull);
+    atomicAdd(&c[ST_LEAVES_TOTAL], (unsigned long long)ix.L);
+    atomicAdd(&c[ST_LEAVES_SURVIVED], (unsigned long long)st->leaf_count);
+    atomicAdd(&c[ST_LEAVES_PROCESSED], (unsigned long long)st->leaves_processed);
+    atomicAdd(&c[ST_SERIES_LB], (unsigned long long)st->series_lb);
+    const unsigned long long seed = st->seed_b - st->seed_a;
+    atomicAdd(&c[ST_SERIES_REFINED], (unsigned long long)st->series_refined + seed);
+    atomicAdd(&c[ST_SEED], seed);
+    atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
+    atomicAdd(&c[ST_RECHECKED], (unsigned long long)R);
+  }
+}
+
+// ------------------------------------------------------------------ lower bounds
+__global__ void __launch_bounds__(kThreads)
+q_lb_all(IndexView ix, QueryView qv, float* __restrict__ series_lb, float* __restrict__ leaf_lb) {
+  __shared__ float thr_up_s[257], thr_lo_s[257], paa_s[16];
+  extern __shared__ float Ts[];
+  for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
+    thr_up_s[v] = ix.thr_up[v];
+    thr_lo_s[v] = ix.thr_lo[v];
+  }
+  if (threadIdx.x < ix.w) paa_s[threadIdx.x] = qv.st->qpaa[threadIdx.x];
+  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (series_lb)
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ix.n; p += stride)
+      series_lb[ix.perm[p]] = __fsqrt_rn(word_lb2(ix.words[p], Ts, ix.w, ix.card, (float)ix.seglen));
+  if (leaf_lb)
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L; l += stride)
+      leaf_lb[l] = __fsqrt_rn(leaf_lb2(ix, l, paa_s, thr_lo_s, thr_up_s));
+}
+
+// z-normalised collection in collection order, from the index's storage.
+__global__ void export_z_kernel(IndexView ix, float* __restrict__ out) {
+  for (int64_t p = blockIdx.x; p < ix.n; p += gridDim.x) {
+    const uint32_t id = ix.perm[p];
+    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[p];
+    for (int t = threadIdx.x; t < ix.len; t += blockDim.x) {
+      const float x = ix.data[(size_t)id * ix.len + t];
+      out[(size_t)id * ix.len + t] = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+}  // namespace
+
+// Allocates the query workspace of an index (once).
+cudaError_t query_setup(msi_index* ix) {
+  if (ix->ws_ready) return cudaSuccess;
+  QueryView& qv = ix->qv;
+  cudaError_t e;
+  if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.cand, (size_t)ix->n)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.rc_d, (size_t)ix->n)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.rc_id, (size_t)ix->n)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.counters, (size_t)ST_COUNT)) != cudaSuccess) return e;
+  if ((e = cudaMemset(qv.counters, 0, sizeof(unsigned long long) * ST_COUNT)) != cudaSuccess) return e;
+  if ((e = dalloc(&ix->ws_qraw, (size_t)kQueryChunk * ix->len)) != cudaSuccess) return e;
+  if ((e = dalloc(&ix->ws_ids, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
+  if ((e = dalloc(&ix->ws_dists, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
+  ix->device_bytes += (int64_t)ix->n * 20 + ix->L * 8 + (int64_t)kQueryChunk * (ix->len * 4 + MSI_MAX_K * 12);
+  const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
+  if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
+  qv.eps = 1.52587890625e-05f;  // 2^-16
+  qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
+  ix->ws_ready = true;
+  return cudaSuccess;
+}
+
+static cudaError_t refine_config(msi_index* ix, int k) {
+  if (ix->refine_smem_k == k) return cudaSuccess;
+  const size_t smem = RefineSmem::bytes(ix->w, ix->card, ix->len, k);
+  int per_sm = 0, sms = 0;
+  cudaError_t e = k == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<true>, kThreads, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device)) != cudaSuccess) return e;
+  ix->refine_grid = std::max(1, per_sm) * sms;
+  ix->refine_smem = smem;
+  ix->refine_smem_k = k;
+  return cudaSuccess;
+}
+
+// One query (device pointers), stream-ordered. ev_a / ev_b, when given, bracket the
+// refinement kernel.
+cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
+                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b) {
+  cudaError_t e = refine_config(ix, k);
+  if (e != cudaSuccess) return e;
+  QueryView qv = ix->qv;
+  qv.k = k;
+  const IndexView v = ix->view();
+  const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
+  const int64_t seed_max = std::max<int64_t>(ix->cap, k);
+  q_seed<<<(unsigned)((seed_max + 7) / 8), kThreads, qbytes, s>>>(v, qv);
+  if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
+  q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
+  if (ev_a) cudaEventRecord(ev_a, s);
+  if (k == 1) q_refine<true><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+  else q_refine<false><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+  if (ev_b) cudaEventRecord(ev_b, s);
+  q_final_select<<<1, 1024, 0, s>>>(qv);
+  q_recheck<<<(unsigned)ix->refine_grid, kThreads, 0, s>>>(v, qv);
+  q_final_topk<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s) {
+  export_z_kernel<<<4096, 128, 0, s>>>(ix->view(), z_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
+                         cudaStream_t s) {
+  QueryView qv = ix->qv;
+  qv.k = 1;
+  const IndexView v = ix->view();
+  const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, 1);
+  q_lb_all<<<1024, kThreads, sizeof(float) * (size_t)ix->w * ix->card, s>>>(v, qv, series_lb_dev, leaf_lb_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace msi

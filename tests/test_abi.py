@@ -1,0 +1,108 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every entry point
+include/msi.h declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def msi():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_00786_gb300 as m
+    return m
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "msi.h")).read()
+    return sorted(set(re.findall(r"MSI_API\s+[\w\s\*]+?\b(msi_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for want in ("msi_build", "msi_knn", "msi_free", "msi_status_str", "msi_last_error", "msi_index_info_get"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(msi):
+    lib = ctypes.CDLL(msi.library_path())
+    for name in declared_entry_points():
+        assert hasattr(lib, name), f"{name} is declared in include/msi.h but not exported"
+
+
+def test_status_strings_and_version(msi):
+    assert msi.msi_abi_version() == 1
+    names = [msi.msi_status_str(s) for s in range(6)]
+    assert names == ["MSI_OK", "MSI_EINVAL", "MSI_ENOMEM", "MSI_ECUDA", "MSI_ETIMEOUT", "MSI_EINTERNAL"]
+    assert msi.msi_status_str(99) == "MSI_UNKNOWN"
+
+
+def _raw_build(msi, series, n, length, segs, card, cap=0, flags=0):
+    lib = msi._lib
+    opts = msi._BuildOpts(cap, flags, None)
+    out = ctypes.c_void_p(123)
+    p = ctypes.c_void_p(series.ctypes.data) if series is not None else None
+    st = lib.msi_build(p, n, length, segs, card, ctypes.byref(opts), ctypes.byref(out))
+    return st, out.value
+
+
+@pytest.mark.parametrize("n,length,segs,card,cap,flags,needle", [
+    (0, 256, 16, 256, 0, 0, "n = 0"),
+    (-5, 256, 16, 256, 0, 0, "n = -5"),
+    (10, 0, 16, 256, 0, 0, "len = 0"),
+    (10, 5000, 16, 256, 0, 0, "len = 5000"),
+    (10, 250, 16, 256, 0, 0, "multiple"),
+    (10, 256, 0, 256, 0, 0, "segments = 0"),
+    (10, 256, 17, 256, 0, 0, "segments = 17"),
+    (10, 256, 16, 100, 0, 0, "power of two"),
+    (10, 256, 16, 512, 0, 0, "power of two"),
+    (10, 256, 16, 1, 0, 0, "power of two"),
+    (10, 256, 16, 256, -1, 0, "leaf_capacity"),
+    (10, 256, 16, 256, 0, 0x10, "flags"),
+])
+def test_build_rejects_bad_arguments_without_a_device(msi, n, length, segs, card, cap, flags, needle):
+    x = np.zeros((4, 256), np.float32)
+    st, out = _raw_build(msi, x, n, length, segs, card, cap, flags)
+    assert st == msi.MSI_EINVAL
+    assert out is None  # *out is cleared on failure
+    assert needle in msi.msi_last_error()
+
+
+def test_build_null_series(msi):
+    st, _ = _raw_build(msi, None, 10, 256, 16, 256)
+    assert st == msi.MSI_EINVAL and "NULL" in msi.msi_last_error()
+
+
+def test_knn_and_helpers_reject_null_index(msi):
+    lib = msi._lib
+    ids = np.zeros(4, np.int64)
+    q = np.zeros(256, np.float32)
+    assert lib.msi_knn(None, ctypes.c_void_p(q.ctypes.data), 1, 1, ctypes.c_void_p(ids.ctypes.data), None, None) == msi.MSI_EINVAL
+    assert "NULL" in msi.msi_last_error()
+    info = msi._IndexInfo()
+    assert lib.msi_index_info_get(None, ctypes.byref(info)) == msi.MSI_EINVAL
+    assert lib.msi_set_timing(None, 1) == msi.MSI_EINVAL
+    st = msi._QueryStats()
+    assert lib.msi_query_stats_get(None, ctypes.byref(st), 0) == msi.MSI_EINVAL
+    lib.msi_free(None)  # no-op
+
+
+def test_python_binding_raises_msierror(msi):
+    with pytest.raises(msi.MsiError) as e:
+        msi.msi_build(np.zeros((3, 250), np.float32), segments=16)
+    assert e.value.status == msi.MSI_EINVAL
+
+
+def test_product_package_does_not_load_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2009_00786_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
+                assert "liboracle" not in text and "oracle.c" not in text, f

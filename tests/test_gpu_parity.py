@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances: SAX words, z-normalised values, thresholds, leaf structure and neighbour
+ids bit-exact; distances within 1e-4 relative (they are FP64 results rounded to
+float on both sides, so in practice equal).
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def msi():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_00786_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+# (n, len, segments, cardinality, leaf capacity): several radix tiles and a ragged
+# tail, both summarise paths (len a power-of-two multiple of 128, and not), scalar
+# and vector distance paths, small words and alphabets.
+CASES = [
+    (20000, 256, 16, 256, 64),
+    (5003, 128, 16, 256, 2000),
+    (3001, 1024, 16, 256, 100),
+    (2500, 96, 16, 256, 50),
+    (4000, 256, 8, 16, 30),
+    (1500, 60, 4, 4, 20),
+    (777, 50, 5, 256, 10),
+]
+IDS = [f"n{c[0]}-len{c[1]}-w{c[2]}-c{c[3]}-cap{c[4]}" for c in CASES]
+
+_cache = {}
+
+
+def case_data(case):
+    if case not in _cache:
+        n, length, w, c, cap = case
+        X = datagen.walks(100 + n, 0, n, length)
+        Z, P, W, F = oracle.summarise(X, w, c)
+        _cache[case] = (X, Z, W)
+    return _cache[case]
+
+
+def build(msi, X, case, mode="host", torch=None):
+    n, length, w, c, cap = case
+    if mode == "host":
+        return msi.msi_build(X, segments=w, cardinality=c, leaf_capacity=cap)
+    t = torch.from_numpy(X).cuda()
+    if mode == "device":
+        return msi.msi_build(t, segments=w, cardinality=c, leaf_capacity=cap)
+    return msi.msi_build(t, segments=w, cardinality=c, leaf_capacity=cap, flags=msi.MSI_BUILD_BORROW)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_summaries_bit_exact(msi, case):
+    n, length, w, c, cap = case
+    X, Z, W = case_data(case)
+    ix = build(msi, X, case)
+    ex = msi.msi_index_export(ix, znorm=True)
+    assert np.array_equal(ex["thresholds"], oracle.thresholds(c))
+    assert np.array_equal(ex["znorm"].view(np.uint32), Z.view(np.uint32))
+    bad = np.nonzero((ex["words"] != W).any(axis=1))[0]
+    assert len(bad) == 0, f"{len(bad)} words differ, first ids {bad[:5]}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_leaf_structure(msi, case):
+    n, length, w, c, cap = case
+    X, Z, W = case_data(case)
+    ix = build(msi, X, case)
+    ex = msi.msi_index_export(ix)
+    lb, perm = ex["leaf_begin"].astype(np.int64), ex["perm"].astype(np.int64)
+    assert lb[0] == 0 and lb[-1] == n and np.all(np.diff(lb) > 0)
+    assert np.all(np.diff(lb) <= cap)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    bits = int(np.log2(c))
+    Wl = W[perm]
+    for l in range(len(lb) - 1):
+        m = Wl[lb[l]:lb[l + 1]]
+        assert np.array_equal(ex["env_lo"][l], m.min(axis=0))
+        assert np.array_equal(ex["env_hi"][l], m.max(axis=0))
+        # members of a leaf share their root subtree: the top bit of every symbol
+        assert np.all((m >> (bits - 1)) == (m[0] >> (bits - 1)))
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_knn_matches_oracle(msi, case):
+    n, length, w, c, cap = case
+    X, Z, W = case_data(case)
+    ix = build(msi, X, case)
+    Q = datagen.paper_queries(n, length, count=10, data_seed=100 + n, fresh_seed=7, pick_seed=8)
+    for k in [1, 10, 100]:
+        if k > n:
+            continue
+        ids, dists = msi.msi_knn(ix, Q, k)
+        for i, q in enumerate(Q):
+            oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
+            assert np.array_equal(ids[i], oid), f"k={k} query {i}: {ids[i][:8]} vs {oid[:8]}"
+            np.testing.assert_allclose(dists[i], np.sqrt(od2), rtol=RTOL, atol=1e-6)
+
+
+def test_input_modes_agree(msi, torch):
+    case = CASES[0]
+    X, Z, W = case_data(case)
+    Q = datagen.paper_queries(case[0], case[1], count=8, data_seed=100 + case[0])
+    Qd = torch.from_numpy(Q).cuda()
+    out = []
+    for mode in ("host", "device", "borrow"):
+        ix = build(msi, X, case, mode, torch)
+        ids, d = msi.msi_knn(ix, Qd, 10)
+        out.append((ids.cpu().numpy(), d.cpu().numpy()))
+        ids_h, d_h = msi.msi_knn(ix, Q, 10)  # host queries and outputs
+        assert np.array_equal(ids_h, out[-1][0]) and np.array_equal(d_h, out[-1][1])
+    for ids, d in out[1:]:
+        assert np.array_equal(ids, out[0][0]) and np.array_equal(d, out[0][1])
+
+
+def test_stream_ordered_call(msi, torch):
+    case = CASES[0]
+    X, Z, W = case_data(case)
+    Q = torch.from_numpy(datagen.paper_queries(case[0], case[1], count=5, data_seed=100 + case[0])).cuda()
+    ix = build(msi, X, case)
+    want = msi.msi_knn(ix, Q, 3)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ids = torch.empty((5, 3), dtype=torch.int64, device="cuda")
+        d = torch.empty((5, 3), dtype=torch.float32, device="cuda")
+        msi.msi_knn(ix, Q, 3, ids, d, stream=s)
+    s.synchronize()
+    assert torch.equal(ids, want[0]) and torch.equal(d, want[1])
+
+
+def test_edge_cases(msi):
+    length = 128
+    X = datagen.walks(3, 0, 300, length)
+    # a single series
+    ix = msi.msi_build(X[:1], segments=16)
+    ids, d = msi.msi_knn(ix, X[:2], 1)
+    assert list(ids[:, 0]) == [0, 0] and d[0, 0] == 0.0
+    # k = n: the full order
+    ix = msi.msi_build(X, segments=16, leaf_capacity=16)
+    Z = oracle.summarise(X, 16, 256)[0]
+    ids, d = msi.msi_knn(ix, X[5:6], 300)
+    oid, od2 = oracle.knn_scan(Z, oracle.znorm(X[5])[0], 300)
+    assert np.array_equal(ids[0], oid) and ids[0, 0] == 5
+    # duplicates and constant series: ties go to the lowest id
+    Xd = X.copy()
+    Xd[200] = Xd[40]
+    Xd[250] = Xd[40] * np.float32(3.0) + np.float32(1.0)  # same z-normalised shape
+    Xd[10] = 7.0
+    Xd[11] = -2.0
+    ix = msi.msi_build(Xd, segments=16, leaf_capacity=8)
+    ids, d = msi.msi_knn(ix, Xd[[200, 11]], 3)
+    Zd = oracle.summarise(Xd, 16, 256)[0]
+    for row, q in zip(ids, Xd[[200, 11]]):
+        assert np.array_equal(row, oracle.knn_scan(Zd, oracle.znorm(q)[0], 3)[0])
+    assert ids[0, 0] == 40 and ids[1, 0] == 10 and ids[1, 1] == 11  # constant query -> constant series
+    # invalid inputs
+    Xn = X.copy()
+    Xn[17, 3] = np.nan
+    with pytest.raises(msi.MsiError) as e:
+        msi.msi_build(Xn, segments=16)
+    assert e.value.status == msi.MSI_EINVAL and "series 17" in str(e.value)
+    Qn = X[:2].copy()
+    Qn[1, 0] = np.inf
+    with pytest.raises(msi.MsiError):
+        msi.msi_knn(ix, Qn, 1)
+    for k in (0, 301, 2000):
+        with pytest.raises(msi.MsiError):
+            msi.msi_knn(ix, X[:1], k)
+    ids, d = msi.msi_knn(ix, X[:0], 1)  # nq = 0
+    assert ids.shape == (0, 1)
+
+
+def test_lower_bounds_are_bounds(msi):
+    case = (6000, 256, 16, 256, 64)
+    X = datagen.walks(9, 0, case[0], 256)
+    Z, _, W, _ = oracle.summarise(X, 16, 256)
+    ix = msi.msi_build(X, segments=16, leaf_capacity=64)
+    ex = msi.msi_index_export(ix)
+    perm, lb = ex["perm"].astype(np.int64), ex["leaf_begin"].astype(np.int64)
+    for q in datagen.walks(10, 0, 3, 256):
+        zq = oracle.znorm(q)[0]
+        s_lb, l_lb = msi.msi_lower_bounds(ix, q)
+        true = np.sqrt(((Z.astype(np.float64) - zq.astype(np.float64)) ** 2).sum(axis=1))
+        assert np.all(s_lb <= true + 1e-3)
+        qp = oracle.paa64(zq, 16)
+        ref = np.array([oracle.mindist(qp, W[i], W[i], 256, 256) for i in range(0, case[0], 7)])
+        np.testing.assert_allclose(s_lb[::7], ref, rtol=0, atol=2e-4)
+        for l in range(0, len(lb) - 1, 5):
+            members = perm[lb[l]:lb[l + 1]]
+            assert l_lb[l] <= s_lb[members].min() + 1e-4
+
+
+def test_stats_counters(msi):
+    X = datagen.walks(11, 0, 8000, 256)
+    ix = msi.msi_build(X, segments=16, leaf_capacity=64)
+    msi.msi_query_stats_get(ix, reset=True)
+    msi.msi_set_timing(ix, True)
+    Q = datagen.paper_queries(8000, 256, count=6, data_seed=11)
+    msi.msi_knn(ix, Q, 5)
+    st = msi.msi_query_stats_get(ix)
+    assert st["queries"] == 6
+    assert st["leaves_total"] == 6 * ix.leaves
+    assert 0 < st["series_refined"] <= 6 * 8000
+    assert st["candidates"] >= 6 * 5 and st["rechecked"] >= 6 * 5
+    assert st["refine_launches"] == 6 and st["refine_ms"] > 0
+    assert st["series_lower_bounded"] < 6 * 8000  # leaves were pruned

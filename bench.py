@@ -1,0 +1,309 @@
+"""Benchmark: exact 1-NN queries/s and p50/p99 latency at 100M x 256 fp32.
+
+Workload (default): 100M random-walk series of 256 points (fp32, generated on the
+device from seed 0, ~102 GB resident in HBM), indexed with 16 segments and
+cardinality 256, leaf capacity 2000; 100 queries: 50 fresh random walks (seed 1) and
+50 collection members plus N(0, sigma^2) noise, sigma cycling 0.01 / 0.1 / 1 (ids and
+noise from seed 2). One step answers the 100 queries (k = 1) in one msi_knn call on
+a stream (the batched form); the plain form answers them one call and one wait at a
+time and gives the p50/p99 latency.
+
+Prints one JSON line. `--impl reference` times the CPU oracle (FP64 serial scan) on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+KERNELS_PER_QUERY = {1: 7}  # q_prep, q_seed, q_leaf_filter, q_refine, q_final_select, q_recheck, q_final_topk
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=100_000_000)
+    p.add_argument("--len", type=int, default=256)
+    p.add_argument("--queries", type=int, default=100)
+    p.add_argument("--k", type=int, default=1)
+    p.add_argument("--leaf", type=int, default=2000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=2_000_000, help="series in the oracle's timed sample")
+    p.add_argument("--cpu-queries", type=int, default=10)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index=0):
+        self.samples = []
+        self._stop = threading.Event()
+        self._index = index
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self._index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                vals = [v.strip() for v in out.stdout.strip().split(",")]
+                if len(vals) == 6:
+                    self.samples.append(vals)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(args, length, n_total, seconds_budget=None):
+    """The oracle's FP64 serial-scan 1-NN on a bounded sample of the workload: the
+    first `cpu_sample` series (regenerated on the host) and `cpu_queries` queries of
+    the same mix; time per query scaled to the full collection size."""
+    import datagen
+    import oracle
+    ns = min(args.cpu_sample, n_total)
+    X = datagen.walks(0, 0, ns, length)
+    t0 = time.perf_counter()
+    Z = oracle.summarise(X, 16, 256, want_paa=False)[0]
+    t_sum = time.perf_counter() - t0
+    Q = datagen.paper_queries(n_total, length, count=args.queries)[: args.cpu_queries]
+    t0 = time.perf_counter()
+    for q in Q:
+        oracle.knn_scan(Z, oracle.znorm(q)[0], args.k)
+    t_scan = (time.perf_counter() - t0) / len(Q)
+    per_query_full = t_scan * (n_total / ns)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"value": 1.0 / per_query_full, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 serial scan of {ns} of the {n_total} series (regenerated on the host, z-normalised by "
+                      f"the oracle in {t_sum:.2f} s) for {len(Q)} queries; {t_scan * 1e3:.1f} ms/query scaled "
+                      f"x{n_total / ns:g} to the full collection"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    length = args.len
+    times = []
+    base = None
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = cpu_baseline(args, length, args.n)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = base["value"]
+    line = {"impl": "reference", "metric": "exact 1-NN queries/s (100M x 256 fp32)", "value": value,
+            "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.n // 1_000_000}M x {length} random walks, {args.queries} queries, k={args.k}",
+                       "sample": base["sample"]},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import datagen
+    import paper_2009_00786_gb300 as msi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, length, nq, k = args.n, args.len, args.queries, args.k
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---- collection (this rank's shard of the weak-scaled job) and queries, in HBM
+    first_id = rank * n
+    X = torch.empty((n, length), dtype=torch.float32, device=dev)
+    datagen.walks_device(0, first_id, n, length, X.data_ptr(), stream.cuda_stream)
+    n_fresh, ids, sig = datagen.query_plan(n, nq)
+    Q = torch.empty((nq, length), dtype=torch.float32, device=dev)
+    datagen.walks_device(1, 0, n_fresh, length, Q.data_ptr(), stream.cuda_stream)
+    ids_d = torch.from_numpy(ids).to(dev)
+    sig_d = torch.from_numpy(sig).to(dev)
+    datagen.noisy_copies_device(0, 2, ids_d.data_ptr(), sig_d.data_ptr(), nq - n_fresh, length,
+                                Q[n_fresh:].data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+
+    # ---- build (timed once; the collection is borrowed in place)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        b0.record(stream)
+        index = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=args.leaf, flags=msi.MSI_BUILD_BORROW,
+                              stream=stream)
+        b1.record(stream)
+    stream.synchronize()
+    build_ms = b0.elapsed_time(b1)
+
+    out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    out_d = torch.empty((nq, k), dtype=torch.float32, device=dev)
+
+    def step():
+        msi.msi_knn(index, Q, k, out_ids, out_d, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    msi.msi_query_stats_get(index, reset=True)
+
+    # ---- timed region: K batched steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    qps = nq * args.steps * world / (elapsed_ms / 1e3)
+
+    # ---- plain form: one call and one wait per query, for p50 / p99
+    lat = []
+    qe0, qe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(nq):
+        qe0.record(stream)
+        msi.msi_knn(index, Q[i:i + 1], k, out_ids[i:i + 1], out_d[i:i + 1], stream=stream)
+        qe1.record(stream)
+        qe1.synchronize()
+        lat.append(qe0.elapsed_time(qe1))
+    plain_qps = nq / (sum(lat) / 1e3)
+
+    # ---- batched latency: every query of a step waits for the whole step
+    batch_lat = elapsed_ms / args.steps
+
+    # ---- end to end: host queries in, host results out, through the C ABI
+    Qh = torch.empty((nq, length), dtype=torch.float32, pin_memory=True)
+    Qh.copy_(Q.cpu())
+    ids_h = torch.empty((nq, k), dtype=torch.int64, pin_memory=True)
+    d_h = torch.empty((nq, k), dtype=torch.float32, pin_memory=True)
+    msi.msi_knn(index, Qh, k, ids_h, d_h, stream=stream)
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(args.steps):
+        msi.msi_knn(index, Qh, k, ids_h, d_h, stream=stream)
+    ee1.record(stream)
+    ee1.synchronize()
+    e2e_qps = nq * args.steps * world / (ee0.elapsed_time(ee1) / 1e3)
+
+    # ---- dominant kernel: refinement, timed with events on its own stream
+    msi.msi_query_stats_get(index, reset=True)
+    msi.msi_set_timing(index, True)
+    step()
+    stream.synchronize()
+    msi.msi_set_timing(index, False)
+    st = msi.msi_query_stats_get(index, reset=True)
+    launches = max(1, st["refine_launches"])
+    main_refined = st["series_refined"] - st["seed_series"]
+    alg_bytes = (16 * st["series_lower_bounded"] + (4 * length + 4 + 8) * main_refined
+                 + 16 * st["leaves_processed"] + 8 * st["leaves_survived"] + 8 * st["candidates"]) / launches
+    refine_s = st["refine_ms"] / launches / 1e3
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / refine_s / 1e9 if refine_s > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "q_refine_traffic.txt")
+    if os.path.exists(tpath):
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", "msi_query.cu"), "rb").read()
+        h = hashlib.sha256(src).hexdigest()[:16]
+        kv = dict(l.split(":", 1) for l in open(tpath).read().splitlines() if ":" in l and not l.startswith("#"))
+        if kv.get("source_sha256_16", "").strip() == h:
+            traffic = float(kv["dram_bytes_per_launch"])
+
+    line = {
+        "metric": "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs plain",
+        "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n * world // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries "
+                               f"(50% fresh walks, 50% noisy members), k={k}, 16 segments, cardinality 256, "
+                               f"leaf capacity {args.leaf}",
+                   "n_series": n * world, "len": length, "queries_per_step": nq, "k": k,
+                   "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)"},
+        "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+        "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq},
+        "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
+                "d2h_bytes_per_step": nq * k * 12},
+        "gpu_launches": KERNELS_PER_QUERY.get(k, 8) * nq * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "q_refine", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},
+        "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if kk not in ("refine_ms",)},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, length, n * world)
+    index.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

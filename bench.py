@@ -26,6 +26,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
+METRIC = "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs plain"
+
+
+def workload(n_total, length, nq, k, leaf):
+    return (f"{n_total // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries (50% fresh walks, "
+            f"50% noisy members), k={k}, 16 segments, cardinality 256, leaf capacity {leaf}")
 KERNELS_PER_QUERY = {1: 7}  # q_prep, q_seed, q_leaf_filter, q_refine, q_final_select, q_recheck, q_final_topk
 
 
@@ -136,11 +142,11 @@ def reference_arm(args):
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     value = base["value"]
-    line = {"impl": "reference", "metric": "exact 1-NN queries/s (100M x 256 fp32)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.n // 1_000_000}M x {length} random walks, {args.queries} queries, k={args.k}",
+            "config": {"workload": workload(args.n, length, args.queries, args.k, args.leaf),
                        "sample": base["sample"]},
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -275,13 +281,11 @@ def main():
             traffic = float(kv["dram_bytes_per_launch"])
 
     line = {
-        "metric": "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs plain",
+        "metric": METRIC,
         "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{n * world // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries "
-                               f"(50% fresh walks, 50% noisy members), k={k}, 16 segments, cardinality 256, "
-                               f"leaf capacity {args.leaf}",
+        "config": {"workload": workload(n * world, length, nq, k, args.leaf),
                    "n_series": n * world, "len": length, "queries_per_step": nq, "k": k,
                    "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)"},
         "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},

@@ -208,14 +208,26 @@ void orc_paa64(const float* z, int32_t n, int32_t w, double* paa) {
 }
 
 /* ------------------------------------------------------------ exact distance
- * Section II-A: Euclidean distance. D = sum_t (z_t - q_t)^2 in FP64, in increasing t. */
+ * Section II-A: Euclidean distance. D = sum_t (z_t - q_t)^2 in FP64. The paper
+ * fixes no summation order; this one is shared with the GPU re-check so both sides
+ * produce the same bits: 32 partial sums, partial l adding the terms with
+ * t mod 32 = l in increasing t, combined by a pairwise tree in partial order. */
+static double orc_lane_tree64(double a[32]) {
+  for (int off = 1; off < 32; off <<= 1) {
+    double b[32];
+    for (int l = 0; l < 32; ++l) b[l] = a[l] + a[l ^ off];
+    memcpy(a, b, sizeof b);
+  }
+  return a[0];
+}
+
 double orc_sqdist(const float* a, const float* b, int32_t n) {
-  double acc = 0.0;
+  double part[32] = {0};
   for (int32_t t = 0; t < n; ++t) {
     const double d = (double)a[t] - (double)b[t];
-    acc = acc + d * d;
+    part[t & 31] = part[t & 31] + d * d;
   }
-  return acc;
+  return orc_lane_tree64(part);
 }
 
 /* (D, id) order: smaller distance first, then lower id. */

@@ -13,6 +13,7 @@
 namespace msi {
 
 constexpr int kWarp = 32;
+constexpr int kItem = 256;  // leaf positions per refinement work item
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ index
@@ -42,6 +43,7 @@ struct QState {
   uint32_t seed_a, seed_b;      // leaf-order positions refined by the approximate search
   unsigned int thr_bits;        // fp32 bits of the current k-th best squared distance
   unsigned int leaf_count;      // leaves that passed the leaf filter
+  unsigned int item_count;      // refinement work items (<= kItem positions of one leaf)
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -64,6 +66,7 @@ struct QueryView {
   QState* st;
   uint32_t* leaf_list;          // [L]
   float* leaf_lb2;              // [L]
+  uint4* items;                 // [n / kItem + L]: {first pos, end pos, leaf bound^2 bits, leaf}
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
   double* rc_d;                 // [n]
   uint32_t* rc_id;              // [n]

@@ -235,6 +235,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->seed_b = (uint32_t)b;
     st->thr_bits = 0x7f800000u;
     st->leaf_count = 0;
+    st->item_count = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -251,18 +252,24 @@ q_seed(IndexView ix, QueryView qv) {
   extern __shared__ __align__(16) float qs[];
   for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
   __syncthreads();
+  __shared__ unsigned s_min;
+  if (threadIdx.x == 0) s_min = 0x7f800000u;
   const uint32_t a = qv.st->seed_a, b = qv.st->seed_b;
   const uint32_t warps = gridDim.x * (kThreads / 32);
+  unsigned best = 0x7f800000u;
   for (uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); gw < b - a; gw += warps) {
     const uint32_t pos = a + gw;
     const uint32_t id = ix.perm[pos];
     const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
     const float d2 = warp_sqdist(ix, id, ms, qs);
-    if ((threadIdx.x & 31) == 0) {
-      qv.cand[gw] = pack(d2, pos);
-      if (qv.k == 1) atomicMin(&qv.st->thr_bits, __float_as_uint(d2));
-    }
+    if ((threadIdx.x & 31) == 0) qv.cand[gw] = pack(d2, pos);
+    best = min(best, __float_as_uint(d2));
   }
+  // k = 1: one atomicMin per block, on the block's smallest distance
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && best < 0x7f800000u) atomicMin(&s_min, best);
+  __syncthreads();
+  if (threadIdx.x == 0 && qv.k == 1 && s_min < 0x7f800000u) atomicMin(&qv.st->thr_bits, s_min);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -299,13 +306,32 @@ q_leaf_filter(IndexView ix, QueryView qv) {
   const unsigned m = __ballot_sync(kFull, keep);
   if (m) {
     const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
     uint32_t base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&qv.st->leaf_count, (uint32_t)__popc(m));
-    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+    if (lane == leader) base = atomicAdd(&qv.st->leaf_count, (uint32_t)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    // work items of at most kItem positions, numbered by a warp prefix sum
+    uint32_t b = 0, e = 0, nit = 0;
+    if (keep) {
+      b = ix.leaf_begin[l];
+      e = ix.leaf_begin[l + 1];
+      nit = (e - b + kItem - 1) / kItem;
+    }
+    uint32_t incl = nit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t ibase = 0;
+    if (lane == 31) ibase = atomicAdd(&qv.st->item_count, incl);
+    ibase = __shfl_sync(kFull, ibase, 31) + incl - nit;
     if (keep) {
       const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
       qv.leaf_list[slot] = (uint32_t)l;
       qv.leaf_lb2[slot] = lb2;
+      for (uint32_t j = 0; j < nit; ++j)
+        qv.items[ibase + j] = make_uint4(b + j * kItem, min(e, b + (j + 1) * kItem), __float_as_uint(lb2), (uint32_t)l);
     }
   }
 }
@@ -445,6 +471,183 @@ q_refine(IndexView ix, QueryView qv) {
   if (tid == 0) atomicAdd(&st->leaves_processed, n_leaf);
 }
 
+// ------------------------------------------------------------------ q_refine_warp
+// Barrier-free refinement for k <= 32. Warps take work items (at most kItem
+// positions of one surviving leaf) in a fixed stride, re-test the item's leaf bound
+// against the current BSF (ProcessQueue, Algorithm 8), lower-bound every position
+// from its SAX word with all word loads in flight at once, queue the survivors in
+// shared memory, and compute their real distances four rows at a time
+// (CalculateRealDistance, Algorithm 9). k = 1: the BSF is an atomicMin taken only by
+// a distance below the current BSF. 1 < k <= 32: each warp keeps its k best in
+// registers (lane i holds the i-th) and publishes its k-th once it holds k.
+constexpr int kRefWarps = 8;
+constexpr int kRows = 4;
+
+struct WarpRefineSmem {
+  static size_t bytes(int w, int card, int len) {
+    size_t b = (sizeof(float) * (size_t)w * card + 15) & ~size_t(15);
+    b += sizeof(float) * (size_t)((len + 3) & ~3);
+    b += sizeof(uint32_t) * kItem * kRefWarps;
+    return b;
+  }
+};
+
+template <bool KONE>
+__global__ void __launch_bounds__(kRefWarps * 32)
+q_refine_warp(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Ts = reinterpret_cast<float*>(smem);
+  size_t off = ((sizeof(float) * (size_t)ix.w * ix.card) + 15) & ~size_t(15);
+  float* qs = reinterpret_cast<float*>(smem + off);
+  off += sizeof(float) * (size_t)((ix.len + 3) & ~3);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + off) + warp * kItem;
+  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  __syncthreads();
+
+  QState* st = qv.st;
+  volatile unsigned int* thr_v = &st->thr_bits;
+  const uint32_t nitems = st->item_count;
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const int k = qv.k;
+  const float seglen = (float)ix.seglen;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned mine = 0x7f800000u;  // k > 1: this lane's entry of the warp's sorted k best
+  uint32_t n_lb = 0, n_ref = 0, n_items = 0;
+  const uint32_t stride = gridDim.x * kRefWarps;
+  for (uint32_t it = blockIdx.x * kRefWarps + warp; it < nitems; it += stride) {
+    const uint4 item = qv.items[it];
+    const unsigned thr0 = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    const float bound2 = lb_bound2(thr0, qv.eps, qv.tau);
+    if (__uint_as_float(item.z) > bound2) continue;
+    ++n_items;
+    // lower bounds of up to kItem positions, all word loads issued first
+    uint4 wd[kItem / 32];
+#pragma unroll
+    for (int i = 0; i < kItem / 32; ++i) {
+      const uint32_t p = item.x + i * 32 + lane;
+      wd[i] = p < item.y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+    }
+    uint32_t nq = 0;
+#pragma unroll
+    for (int i = 0; i < kItem / 32; ++i) {
+      const uint32_t p = item.x + i * 32 + lane;
+      const bool valid = p < item.y && (p < sa || p >= sb);
+      n_lb += valid;
+      const bool pass = valid && word_lb2(wd[i], Ts, ix.w, ix.card, seglen) <= bound2;
+      const unsigned m = __ballot_sync(kFull, pass);
+      if (pass) queue[nq + __popc(m & lt)] = p;
+      nq += __popc(m);
+    }
+    __syncwarp();
+    // real distances, kRows rows at a time
+    for (uint32_t g = 0; g < nq; g += kRows) {
+      const uint32_t r = min((uint32_t)kRows, nq - g);
+      uint32_t myp = 0, myid = 0;
+      float2 myms = make_float2(0.f, 0.f);
+      if (lane < (int)r) {
+        myp = queue[g + lane];
+        myid = __ldg(ix.perm + myp);
+        if (!ix.data_is_z) myms = __ldg(ix.stats + myp);
+      }
+      uint32_t id[kRows];
+      float2 ms[kRows];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        id[j] = __shfl_sync(kFull, myid, j);
+        ms[j].x = __shfl_sync(kFull, myms.x, j);
+        ms[j].y = __shfl_sync(kFull, myms.y, j);
+      }
+      float acc[kRows];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) acc[j] = 0.0f;
+      if ((ix.len & 3) == 0) {
+        const int n4 = ix.len >> 2;
+        const float4* q4 = reinterpret_cast<const float4*>(qs);
+        for (int c = lane; c < n4; c += 32) {
+          float4 x[kRows];
+#pragma unroll
+          for (int j = 0; j < kRows; ++j)
+            x[j] = j < (int)r ? __ldg(reinterpret_cast<const float4*>(ix.data + (size_t)id[j] * ix.len) + c)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 q = q4[c];
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) {
+            float4 z = x[j];
+            if (!ix.data_is_z) {
+              z.x = znorm_value(z.x, ms[j].x, ms[j].y);
+              z.y = znorm_value(z.y, ms[j].x, ms[j].y);
+              z.z = znorm_value(z.z, ms[j].x, ms[j].y);
+              z.w = znorm_value(z.w, ms[j].x, ms[j].y);
+            }
+            float d = __fsub_rn(z.x, q.x); acc[j] = __fmaf_rn(d, d, acc[j]);
+            d = __fsub_rn(z.y, q.y); acc[j] = __fmaf_rn(d, d, acc[j]);
+            d = __fsub_rn(z.z, q.z); acc[j] = __fmaf_rn(d, d, acc[j]);
+            d = __fsub_rn(z.w, q.w); acc[j] = __fmaf_rn(d, d, acc[j]);
+          }
+        }
+      } else {
+        for (int t = lane; t < ix.len; t += 32) {
+#pragma unroll
+          for (int j = 0; j < kRows; ++j) {
+            if (j < (int)r) {
+              const float x = __ldg(ix.data + (size_t)id[j] * ix.len + t);
+              const float z = ix.data_is_z ? x : znorm_value(x, ms[j].x, ms[j].y);
+              const float d = __fsub_rn(z, qs[t]);
+              acc[j] = __fmaf_rn(d, d, acc[j]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kRows; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(kFull, acc[j], o);
+      n_ref += r;
+      // lane j < r owns row j
+      float d2 = acc[0];
+#pragma unroll
+      for (int j = 1; j < kRows; ++j)
+        if (lane == j) d2 = acc[j];
+      const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+      const bool keep = lane < (int)r && d2 <= keep_bound2(thr, qv.eps);
+      const unsigned km = __ballot_sync(kFull, keep);
+      if (km) {
+        const int leader = __ffs(km) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&st->cand_count, (uint32_t)__popc(km));
+        base = __shfl_sync(kFull, base, leader);
+        if (keep) qv.cand[base + __popc(km & lt)] = pack(d2, myp);
+      }
+      if (KONE) {
+        if (lane < (int)r && __float_as_uint(d2) < thr) atomicMin(&st->thr_bits, __float_as_uint(d2));
+      } else {
+        const unsigned kth_old = __shfl_sync(kFull, mine, k - 1);
+        for (uint32_t j = 0; j < r; ++j) {
+          const unsigned v = __float_as_uint(__shfl_sync(kFull, d2, j));
+          if (v >= __shfl_sync(kFull, mine, k - 1)) continue;
+          const int pos = __popc(__ballot_sync(kFull, lane < k && mine <= v));
+          const unsigned up = __shfl_up_sync(kFull, mine, 1);
+          if (lane >= pos && lane < k) mine = lane == pos ? v : up;
+        }
+        const unsigned kth = __shfl_sync(kFull, mine, k - 1);
+        if (lane == 0 && kth < kth_old && kth < thr) atomicMin(&st->thr_bits, kth);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_lb += __shfl_xor_sync(kFull, n_lb, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&st->series_lb, n_lb);
+    atomicAdd(&st->series_refined, n_ref);
+    atomicAdd(&st->leaves_processed, n_items);
+  }
+}
+
 // ------------------------------------------------------------------ final pick
 __global__ void __launch_bounds__(1024)
 q_final_select(QueryView qv) {
@@ -456,33 +659,37 @@ q_final_select(QueryView qv) {
   if (threadIdx.x == 0) qv.st->final_bits = __float_as_uint(__fmul_ru(__uint_as_float(kth), 1.0f + qv.eps));
 }
 
-// FP64 squared distance, summed in increasing t, no fused operations.
-__device__ __forceinline__ double sqdist64(const IndexView& ix, uint32_t id, float2 ms, const float* qz) {
-  const float* row = ix.data + (size_t)id * ix.len;
-  double acc = 0.0;
-  for (int t = 0; t < ix.len; ++t) {
-    const float x = row[t];
-    const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
-    const double d = __dsub_rn((double)z, (double)qz[t]);
-    acc = __dadd_rn(acc, __dmul_rn(d, d));
-  }
-  return acc;
-}
-
+// FP64 re-check of the candidates at or below the k-th candidate distance times
+// (1 + eps): one warp per candidate. Lane l adds the FP64 squared differences of the
+// points t = l, l + 32, ... in increasing t; the 32 partials are combined by a
+// pairwise tree in lane order. No fused operations: the same bits as the oracle.
 __global__ void __launch_bounds__(kThreads)
 q_recheck(IndexView ix, QueryView qv) {
   const uint32_t count = qv.st->cand_count;
   const uint32_t bound = qv.st->final_bits;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (kThreads / 32);
+  for (uint32_t i = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); i < count; i += warps) {
     const unsigned long long c = qv.cand[i];
     if ((uint32_t)(c >> 32) > bound) continue;
     const uint32_t pos = (uint32_t)c;
     const uint32_t id = ix.perm[pos];
     const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
-    const double D = sqdist64(ix, id, ms, qv.qz);
-    const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
-    qv.rc_d[slot] = D;
-    qv.rc_id[slot] = id;
+    const float* row = ix.data + (size_t)id * ix.len;
+    double acc = 0.0;
+    for (int t = lane; t < ix.len; t += 32) {
+      const float x = row[t];
+      const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
+      const double d = __dsub_rn((double)z, (double)qv.qz[t]);
+      acc = __dadd_rn(acc, __dmul_rn(d, d));
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) acc = __dadd_rn(acc, __shfl_xor_sync(kFull, acc, off));
+    if (lane == 0) {
+      const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
+      qv.rc_d[slot] = acc;
+      qv.rc_id[slot] = id;
+    }
   }
 }
 
@@ -658,6 +865,7 @@ cudaError_t query_setup(msi_index* ix) {
   if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.items, (size_t)(ix->n / kItem + ix->L + 1))) != cudaSuccess) return e;
   if ((e = dalloc(&qv.cand, (size_t)ix->n)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_d, (size_t)ix->n)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_id, (size_t)ix->n)) != cudaSuccess) return e;
@@ -670,23 +878,30 @@ cudaError_t query_setup(msi_index* ix) {
   const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
   if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
+  const size_t wsmem = WarpRefineSmem::bytes(ix->w, ix->card, ix->len);
+  if ((e = cudaFuncSetAttribute(q_refine_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(q_refine_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem)) != cudaSuccess) return e;
   qv.eps = 1.52587890625e-05f;  // 2^-16
   qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
   ix->ws_ready = true;
   return cudaSuccess;
 }
 
+// Refinement kernel for k: the warp-level kernel up to k = 32, the block kernel with a
+// shared-memory top-k buffer above.
 static cudaError_t refine_config(msi_index* ix, int k) {
-  if (ix->refine_smem_k == k) return cudaSuccess;
-  const size_t smem = RefineSmem::bytes(ix->w, ix->card, ix->len, k);
+  const int mode = k == 1 ? 1 : (k <= 32 ? 32 : 0);
+  if (ix->refine_smem_k == mode) return cudaSuccess;
+  const size_t smem = mode ? WarpRefineSmem::bytes(ix->w, ix->card, ix->len) : RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
   int per_sm = 0, sms = 0;
-  cudaError_t e = k == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<true>, kThreads, smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem);
+  cudaError_t e = mode == 1    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_warp<true>, kRefWarps * 32, smem)
+                  : mode == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_warp<false>, kRefWarps * 32, smem)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device)) != cudaSuccess) return e;
   ix->refine_grid = std::max(1, per_sm) * sms;
   ix->refine_smem = smem;
-  ix->refine_smem_k = k;
+  ix->refine_smem_k = mode;
   return cudaSuccess;
 }
 
@@ -706,7 +921,8 @@ cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
   q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
-  if (k == 1) q_refine<true><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+  if (k == 1) q_refine_warp<true><<<ix->refine_grid, kRefWarps * 32, ix->refine_smem, s>>>(v, qv);
+  else if (k <= 32) q_refine_warp<false><<<ix->refine_grid, kRefWarps * 32, ix->refine_smem, s>>>(v, qv);
   else q_refine<false><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
   if (ev_b) cudaEventRecord(ev_b, s);
   q_final_select<<<1, 1024, 0, s>>>(qv);

@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full size (100M x 256, borrowed collection, leaf capacity
+2000, 100 queries of the benchmark's mix answered in one batched msi_knn call),
+on outputs the oracle can compute one by one:
+  - the SAX words of sampled blocks of series, bit-exact;
+  - every returned distance equals the oracle's FP64 distance to the returned id;
+  - for noisy members, the answer is no farther than the member itself;
+  - for a few queries, the full answer of the oracle's serial scan over the whole
+    collection, regenerated on the host chunk by chunk.
+MSI_FULLSIZE_N overrides the collection size (default 100M)."""
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+N = int(os.environ.get("MSI_FULLSIZE_N", "100000000"))
+LEN, NQ, K = 256, 100, 1
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_00786_gb300 as msi
+    free, _ = torch.cuda.mem_get_info()
+    if free < N * LEN * 4 * 1.15:
+        pytest.skip(f"needs {N * LEN * 4 / 1e9:.0f} GB of free device memory")
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream()
+    X = torch.empty((N, LEN), dtype=torch.float32, device=dev)
+    datagen.walks_device(0, 0, N, LEN, X.data_ptr(), s.cuda_stream)
+    n_fresh, ids, sig = datagen.query_plan(N, NQ)
+    Q = torch.empty((NQ, LEN), dtype=torch.float32, device=dev)
+    datagen.walks_device(1, 0, n_fresh, LEN, Q.data_ptr(), s.cuda_stream)
+    ids_d, sig_d = torch.from_numpy(ids).to(dev), torch.from_numpy(sig).to(dev)
+    datagen.noisy_copies_device(0, 2, ids_d.data_ptr(), sig_d.data_ptr(), NQ - n_fresh, LEN,
+                                Q[n_fresh:].data_ptr(), s.cuda_stream)
+    s.synchronize()
+    index = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=2000, flags=msi.MSI_BUILD_BORROW, stream=s)
+    out_i = torch.empty((NQ, K), dtype=torch.int64, device=dev)
+    out_d = torch.empty((NQ, K), dtype=torch.float32, device=dev)
+    msi.msi_knn(index, Q, K, out_i, out_d, stream=s)
+    s.synchronize()
+    Qh = datagen.paper_queries(N, LEN, count=NQ)
+    assert np.array_equal(Q.cpu().numpy(), Qh), "device and host query generators disagree"
+    yield msi, index, out_i.cpu().numpy(), out_d.cpu().numpy(), Qh, n_fresh, ids
+    index.close()
+
+
+def test_sampled_words_bit_exact(setup):
+    msi, index, *_ = setup
+    ex = msi.msi_index_export(index, perm=False, leaves=False, thresholds=False)
+    rng = np.random.default_rng(5)
+    for start in rng.integers(0, N - 512, size=40):
+        X = datagen.walks(0, int(start), 512, LEN)
+        W = oracle.summarise(X, 16, 256, want_z=False, want_paa=False)[2]
+        assert np.array_equal(ex["words"][start:start + 512], W), f"block at {start}"
+
+
+def test_every_answer_distance_and_member_bound(setup):
+    msi, index, ids, dists, Q, n_fresh, members = setup
+    for i in range(NQ):
+        zq = oracle.znorm(Q[i])[0]
+        zi = oracle.znorm(datagen.walks(0, int(ids[i, 0]), 1, LEN)[0])[0]
+        d = np.sqrt(oracle.sqdist(zi, zq))
+        assert np.float32(d) == dists[i, 0] or abs(d - dists[i, 0]) <= 1e-4 * d
+        if i >= n_fresh:
+            zm = oracle.znorm(datagen.walks(0, int(members[i - n_fresh]), 1, LEN)[0])[0]
+            assert dists[i, 0] <= np.sqrt(oracle.sqdist(zm, zq)) * (1 + 1e-6)
+
+
+def test_full_scan_of_sampled_queries(setup):
+    msi, index, ids, dists, Q, n_fresh, members = setup
+    picks = [0, n_fresh + 2, n_fresh]  # a fresh walk, a sigma = 1 copy, a sigma = 0.01 copy
+    zqs = [oracle.znorm(Q[i])[0] for i in picks]
+    best = [(np.inf, -1)] * len(picks)
+    chunk = 4_000_000
+    for c0 in range(0, N, chunk):
+        cnt = min(chunk, N - c0)
+        Z = oracle.summarise(datagen.walks(0, c0, cnt, LEN), 16, 256, want_paa=False)[0]
+        for j, zq in enumerate(zqs):
+            oid, od2 = oracle.knn_scan(Z, zq, 1)
+            cand = (od2[0], int(oid[0]) + c0)
+            if cand < best[j]:
+                best[j] = cand
+    for j, i in enumerate(picks):
+        assert ids[i, 0] == best[j][1], f"query {i}: {ids[i, 0]} vs oracle {best[j][1]}"
+        np.testing.assert_allclose(dists[i, 0], np.sqrt(best[j][0]), rtol=1e-4)

@@ -32,7 +32,7 @@ METRIC = "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs pla
 def workload(n_total, length, nq, k, leaf):
     return (f"{n_total // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries (50% fresh walks, "
             f"50% noisy members), k={k}, 16 segments, cardinality 256, leaf capacity {leaf}")
-KERNELS_PER_QUERY = {1: 7}  # q_prep, q_seed, q_leaf_filter, q_refine, q_final_select, q_recheck, q_final_topk
+KERNELS_PER_QUERY = {1: 6}  # q_prep, q_seed, q_leaf_filter, q_filter_series, q_refine_rows, q_finalize
 
 
 def parse():
@@ -256,7 +256,7 @@ def main():
     ee1.synchronize()
     e2e_qps = nq * args.steps * world / (ee0.elapsed_time(ee1) / 1e3)
 
-    # ---- dominant kernel: refinement, timed with events on its own stream
+    # ---- refinement kernels, timed with CUDA events recorded on the query stream
     msi.msi_query_stats_get(index, reset=True)
     msi.msi_set_timing(index, True)
     step()
@@ -265,13 +265,26 @@ def main():
     st = msi.msi_query_stats_get(index, reset=True)
     launches = max(1, st["refine_launches"])
     main_refined = st["series_refined"] - st["seed_series"]
-    alg_bytes = (16 * st["series_lower_bounded"] + (4 * length + 4 + 8) * main_refined
-                 + 16 * st["leaves_processed"] + 8 * st["leaves_survived"] + 8 * st["candidates"]) / launches
-    refine_s = st["refine_ms"] / launches / 1e3
+    # algorithmic bytes per launch (kernel table):
+    # series filter: 16 per SAX word bounded + 32 per block envelope + 8 per survivor
+    # written; row refinement: 8 per survivor read + 4 len + 4 + 8 per refined series
+    # (row, perm, moments) + 8 per kept candidate
+    filt_bytes = (16 * st["series_lower_bounded"] + 32 * st["blocks_examined"] + 8 * main_refined) / launches
+    rows_bytes = ((8 + 4 * length + 4 + 8) * main_refined + 8 * st["candidates"]) / launches
+    filt_s = st["filter_ms"] / launches / 1e3
+    rows_s = (st["refine_ms"] - st["filter_ms"]) / launches / 1e3
     peak, peak_kind = peaks()
-    achieved = alg_bytes / refine_s / 1e9 if refine_s > 0 else 0.0
+    kernels = {
+        "q_filter_series": {"alg_bytes_per_launch": filt_bytes, "avg_launch_us": filt_s * 1e6,
+                            "achieved_gbs": filt_bytes / filt_s / 1e9 if filt_s > 0 else 0.0},
+        "q_refine_rows": {"alg_bytes_per_launch": rows_bytes, "avg_launch_us": rows_s * 1e6,
+                          "achieved_gbs": rows_bytes / rows_s / 1e9 if rows_s > 0 else 0.0},
+    }
+    dom = max(kernels, key=lambda kk: kernels[kk]["avg_launch_us"])
+    achieved = kernels[dom]["achieved_gbs"]
+    alg_bytes, refine_s = kernels[dom]["alg_bytes_per_launch"], kernels[dom]["avg_launch_us"] / 1e6
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "q_refine_traffic.txt")
+    tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.txt")
     if os.path.exists(tpath):
         import hashlib
         src = open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", "msi_query.cu"), "rb").read()
@@ -293,11 +306,12 @@ def main():
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
                 "d2h_bytes_per_step": nq * k * 12},
-        "gpu_launches": KERNELS_PER_QUERY.get(k, 8) * nq * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "q_refine", "achieved": achieved, "peak": peak,
+        "gpu_launches": KERNELS_PER_QUERY.get(k, 6) * nq * args.steps,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},
-        "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if kk not in ("refine_ms",)},
+        "refine_kernels": kernels,
+        "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if not kk.endswith("_ms")},
         "clocks": clocks.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

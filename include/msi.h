@@ -182,21 +182,24 @@ typedef struct msi_query_stats {
   int64_t queries;
   int64_t leaves_total;          /* leaves examined by the leaf filter              */
   int64_t leaves_survived;       /* leaves whose bound did not exceed the threshold */
-  int64_t leaves_processed;      /* leaves whose members were lower-bounded         */
+  int64_t blocks_examined;       /* leaf blocks (32 positions; k > 32: leaves) bounded */
   int64_t series_lower_bounded;  /* per-series lower bounds computed                */
   int64_t series_refined;        /* real distances computed (seed leaf included)    */
   int64_t seed_series;           /* real distances of the approximate-search seed   */
   int64_t candidates;            /* (distance, id) pairs kept for the final pick    */
   int64_t rechecked;             /* FP64 re-computations at the k-th boundary       */
-  int64_t refine_launches;       /* launches of the refinement kernel               */
-  double refine_ms;              /* their summed device time (timing enabled only)  */
+  int64_t refine_launches;       /* refinements timed (one per query)               */
+  double refine_ms;              /* summed device time of the refinement: series    */
+                                 /* filter + row refinement (timing enabled only)   */
+  double filter_ms;              /* the series-filter part of refine_ms             */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises
  * with the index's last call. */
 MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats, int32_t reset);
 
-/* Enables (1) or disables (0) CUDA-event timing of the refinement kernel. */
+/* Enables (1) or disables (0) CUDA-event timing of the refinement kernels (events
+ * recorded on the query stream around them; the call then waits for its work). */
 MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
 
 #ifdef __cplusplus

@@ -52,8 +52,9 @@ class _Export(ctypes.Structure):
 
 class _QueryStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
-        "queries", "leaves_total", "leaves_survived", "leaves_processed", "series_lower_bounded",
-        "series_refined", "seed_series", "candidates", "rechecked", "refine_launches")] + [("refine_ms", ctypes.c_double)]
+        "queries", "leaves_total", "leaves_survived", "blocks_examined", "series_lower_bounded",
+        "series_refined", "seed_series", "candidates", "rechecked", "refine_launches")] + [
+        ("refine_ms", ctypes.c_double), ("filter_ms", ctypes.c_double)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -232,3 +233,4 @@ def msi_query_stats_get(index, reset=False):
 
 def msi_set_timing(index, enable=True):
     _check(_lib.msi_set_timing(ctypes.c_void_p(index.handle), 1 if enable else 0))
+

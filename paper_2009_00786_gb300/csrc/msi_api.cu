@@ -102,15 +102,13 @@ void free_index(msi_index* ix) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != ix->device) cudaSetDevice(ix->device);
-  void* ptrs[] = {ix->data_owned, ix->words, ix->perm, ix->stats, ix->leaf_begin, ix->env, ix->leaf_key,
-                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2, ix->qv.items,
+  void* ptrs[] = {ix->data_owned, ix->words, ix->perm, ix->stats, ix->leaf_begin, ix->env, ix->benv, ix->leaf_key,
+                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.T5, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2, ix->qv.items, ix->qv.surv, ix->qv.partials,
                   ix->qv.cand, ix->qv.rc_d, ix->qv.rc_id, ix->qv.counters, ix->ws_qraw, ix->ws_ids, ix->ws_dists};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (auto& ev : ix->events) {
-    if (ev.first) cudaEventDestroy(ev.first);
-    if (ev.second) cudaEventDestroy(ev.second);
-  }
+  for (cudaEvent_t ev : ix->events)
+    if (ev) cudaEventDestroy(ev);
   if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
   if (cur >= 0 && cur != ix->device) cudaSetDevice(cur);
   delete ix;
@@ -252,12 +250,11 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
   if ((e = cudaMemsetAsync(bad_flag, 0, sizeof(unsigned long long), s)) != cudaSuccess)
     return cuda_fail(e, "msi_knn");
   const int64_t chunk = msi::kQueryChunk;
-  if (ix->timing && ix->events.size() < (size_t)chunk) {
-    while (ix->events.size() < (size_t)chunk) {
-      cudaEvent_t a, b;
-      if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess)
-        return cuda_fail(e, "creating timing events");
-      ix->events.emplace_back(a, b);
+  if (ix->timing && ix->events.size() < (size_t)(3 * chunk)) {
+    while (ix->events.size() < (size_t)(3 * chunk)) {
+      cudaEvent_t a;
+      if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "creating timing events");
+      ix->events.push_back(a);
     }
   }
   const bool host_out = !ids_dev || !d_dev;
@@ -273,12 +270,14 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
     int64_t* id_base = ids_dev ? ids + c0 * k : ix->ws_ids;
     float* d_base = dists ? (d_dev ? dists + c0 * k : ix->ws_dists) : nullptr;
     for (int64_t i = 0; i < cnt; ++i) {
-      cudaEvent_t ea = nullptr, eb = nullptr;
+      cudaEvent_t ea = nullptr, em = nullptr, eb = nullptr;
       if (ix->timing) {
-        ea = ix->events[i].first;
-        eb = ix->events[i].second;
+        ea = ix->events[3 * i];
+        em = ix->events[3 * i + 1];
+        eb = ix->events[3 * i + 2];
       }
-      e = msi::query_one(ix, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr, s, ea, eb);
+      e = msi::query_one(ix, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr, s, ea, em,
+                         eb);
       if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
     }
     if (!ids_dev &&
@@ -295,8 +294,11 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
     if (ix->timing) {
       for (int64_t i = 0; i < cnt; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ix->events[i].first, ix->events[i].second) == cudaSuccess) {
+        float fms = 0.f;
+        if (cudaEventElapsedTime(&ms, ix->events[3 * i], ix->events[3 * i + 2]) == cudaSuccess &&
+            cudaEventElapsedTime(&fms, ix->events[3 * i], ix->events[3 * i + 1]) == cudaSuccess) {
           ix->refine_ms += ms;
+          ix->filter_ms += fms;
           ++ix->refine_launches;
         }
       }
@@ -429,7 +431,7 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->queries = (int64_t)c[msi::ST_QUERIES];
   st->leaves_total = (int64_t)c[msi::ST_LEAVES_TOTAL];
   st->leaves_survived = (int64_t)c[msi::ST_LEAVES_SURVIVED];
-  st->leaves_processed = (int64_t)c[msi::ST_LEAVES_PROCESSED];
+  st->blocks_examined = (int64_t)c[msi::ST_LEAVES_PROCESSED];
   st->series_lower_bounded = (int64_t)c[msi::ST_SERIES_LB];
   st->series_refined = (int64_t)c[msi::ST_SERIES_REFINED];
   st->seed_series = (int64_t)c[msi::ST_SEED];
@@ -437,10 +439,12 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->rechecked = (int64_t)c[msi::ST_RECHECKED];
   st->refine_launches = ix->refine_launches;
   st->refine_ms = ix->refine_ms;
+  st->filter_ms = ix->filter_ms;
   if (reset) {
     if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_BAD_QUERY)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");
     ix->refine_ms = 0.0;
+    ix->filter_ms = 0.0;
     ix->refine_launches = 0;
   }
   return MSI_OK;

@@ -401,6 +401,31 @@ __global__ void envelopes(const uint4* __restrict__ words, const uint32_t* __res
   }
 }
 
+// Envelope of every aligned block of 32 leaf-order positions (one warp per block).
+__global__ void block_envelopes(const uint4* __restrict__ words, int64_t n, uint4* __restrict__ benv) {
+  const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (blk * 32 >= n) return;
+  const int64_t p = blk * 32 + lane;
+  uint4 lo = make_uint4(~0u, ~0u, ~0u, ~0u), hi = make_uint4(0, 0, 0, 0);
+  if (p < n) lo = hi = words[p];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo.x = __vminu4(lo.x, __shfl_xor_sync(kFull, lo.x, off));
+    lo.y = __vminu4(lo.y, __shfl_xor_sync(kFull, lo.y, off));
+    lo.z = __vminu4(lo.z, __shfl_xor_sync(kFull, lo.z, off));
+    lo.w = __vminu4(lo.w, __shfl_xor_sync(kFull, lo.w, off));
+    hi.x = __vmaxu4(hi.x, __shfl_xor_sync(kFull, hi.x, off));
+    hi.y = __vmaxu4(hi.y, __shfl_xor_sync(kFull, hi.y, off));
+    hi.z = __vmaxu4(hi.z, __shfl_xor_sync(kFull, hi.z, off));
+    hi.w = __vmaxu4(hi.w, __shfl_xor_sync(kFull, hi.w, off));
+  }
+  if (lane == 0) {
+    benv[2 * blk] = lo;
+    benv[2 * blk + 1] = hi;
+  }
+}
+
 __global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, const uint4* __restrict__ words_in,
                                   const float2* __restrict__ stats_in, uint4* __restrict__ words_out,
                                   float2* __restrict__ stats_out) {
@@ -565,7 +590,9 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(dalloc(&ix->leaf_begin, ix->L + 1));
   MSI_TRY(dalloc(&ix->env, 2 * ix->L));
   MSI_TRY(dalloc(&ix->leaf_key, ix->L));
-  ix->device_bytes += (int64_t)n * (16 + 4 + 8) + (ix->L + 1) * 4 + ix->L * (32 + 8);
+  const int64_t nblk = (n + 31) / 32;
+  MSI_TRY(dalloc(&ix->benv, 2 * nblk));
+  ix->device_bytes += (int64_t)n * (16 + 4 + 8) + (ix->L + 1) * 4 + ix->L * (32 + 8) + nblk * 32;
   *stage = "envelopes";
   write_leaf_begin<<<grid_for(n, 256), 256, 0, s>>>(flags, rank, n, ix->leaf_begin);
   const uint32_t nn = (uint32_t)n;
@@ -573,6 +600,7 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(cudaMemcpyAsync(ix->perm, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
   gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.words, o.stats, ix->words, ix->stats);
   envelopes<<<grid_for(ix->L * 32, 256), 256, 0, s>>>(ix->words, ix->leaf_begin, ix->L, ka, ix->env, ix->leaf_key);
+  block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, n, ix->benv);
   MSI_TRY(cudaGetLastError());
   MSI_TRY(cudaStreamSynchronize(s));
   return cudaSuccess;

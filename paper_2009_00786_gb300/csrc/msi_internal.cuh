@@ -14,6 +14,7 @@ namespace msi {
 
 constexpr int kWarp = 32;
 constexpr int kItem = 256;  // leaf positions per refinement work item
+constexpr int kMaxRefineWarps = 1 << 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ index
@@ -26,6 +27,7 @@ struct IndexView {
   const uint32_t* perm;     // [n] leaf order -> collection id
   const uint32_t* leaf_begin; // [L+1]
   const uint4* env;         // [L][2]: per-segment min symbols, max symbols
+  const uint4* benv;        // [ceil(n/32)][2]: the same over aligned blocks of 32 leaf positions
   const uint64_t* leaf_key; // [L]: interleaved key of each leaf's first member
   const float* thr_up;      // [card+1]: region upper edges: thr_up[v] = smallest float >= beta_v,
                             //   thr_up[0] = -inf, thr_up[card] = +inf (also the SAX thresholds)
@@ -44,6 +46,8 @@ struct QState {
   unsigned int thr_bits;        // fp32 bits of the current k-th best squared distance
   unsigned int leaf_count;      // leaves that passed the leaf filter
   unsigned int item_count;      // refinement work items (<= kItem positions of one leaf)
+  unsigned int next_item;       // (unused)
+  unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -63,14 +67,19 @@ enum StatSlot {
 struct QueryView {
   float* qz;                    // [len]
   float* T;                     // [w][card] squared per-segment gap, query PAA to each symbol
+  float* T5;                    // [w][32] the same to each 5-bit symbol prefix (coarse regions)
   QState* st;
   uint32_t* leaf_list;          // [L]
   float* leaf_lb2;              // [L]
-  uint4* items;                 // [n / kItem + L]: {first pos, end pos, leaf bound^2 bits, leaf}
+  uint4* items;                 // [n / kItem + 2L]: {first pos, end pos, leaf bound^2 bits, leaf}
+  uint2* surv;                  // [n]: {leaf-order position, bound^2 bits} of filter survivors
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
   double* rc_d;                 // [n]
   uint32_t* rc_id;              // [n]
   unsigned long long* counters; // [ST_COUNT]
+  uint32_t* partials;           // [kMaxRefineWarps][3]: per-warp work counters of the refinement
+  uint32_t npartials;           // warps of the series filter (or block refinement) launch
+  uint32_t npartials_rows;      // warps of the row refinement launch
   int k;
   float eps;                    // relative margin on squared distances
   float tau;                    // absolute margin on lower bounds (distance units)
@@ -235,6 +244,7 @@ struct msi_index {
   int64_t L = 0;
   uint32_t* leaf_begin = nullptr;
   uint4* env = nullptr;
+  uint4* benv = nullptr;
   uint64_t* leaf_key = nullptr;
   float* thr_up = nullptr;
   float* thr_lo = nullptr;
@@ -249,11 +259,13 @@ struct msi_index {
   int64_t* ws_ids = nullptr;    // staging for host outputs [kQueryChunk][MSI_MAX_K]
   float* ws_dists = nullptr;
   int refine_grid = 0;
+  int rows_grid = 0;
   size_t refine_smem = 0;
   int refine_smem_k = -1;
   bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // refinement timing, one pair per query
+  std::vector<cudaEvent_t> events;  // refinement timing: three per query (start, after filter, end)
   double refine_ms = 0.0;
+  double filter_ms = 0.0;
   int64_t refine_launches = 0;
 
   msi::IndexView view() const {
@@ -265,6 +277,7 @@ struct msi_index {
     v.perm = perm;
     v.leaf_begin = leaf_begin;
     v.env = env;
+    v.benv = benv;
     v.leaf_key = leaf_key;
     v.thr_up = thr_up;
     v.thr_lo = thr_lo;
@@ -289,7 +302,7 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
 cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
-                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b);
+                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b);
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);

@@ -14,9 +14,9 @@
 //                  from its SAX word and compute the real distance of the survivors
 //                  (CalculateRealDistance, Algorithm 9); the BSF is an atomicMin on the
 //                  bits of a non-negative float;
-//   q_final_select the k-th smallest candidate squared distance;
-//   q_recheck      FP64 distances of every candidate within the fp32 error margin of it;
-//   q_final_topk   the k smallest by (FP64 distance, id): the answer.
+//   q_finalize     the k-th smallest candidate squared distance, FP64 distances of
+//                  every candidate within the fp32 error margin of it, and the k
+//                  smallest by (FP64 distance, id): the answer.
 // Pruning is conservative: a bound prunes only when it exceeds the BSF by more than
 // the fp32 rounding of both sides can explain, so the answer is the exact one.
 #include <cuda_runtime.h>
@@ -197,6 +197,21 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     else if (p > upper) d = __fsub_rn(p, upper);
     qv.T[e] = __fmul_rn(d, d);
   }
+  // coarse table: gap to the union of the regions sharing a 5-bit symbol prefix
+  {
+    const int cb = ix.bits < 5 ? ix.bits : 5, cs = ix.bits - cb;
+    for (int e = tid; e < ix.w * 32; e += blockDim.x) {
+      const int j = e >> 5, c = e & 31;
+      float d = 0.0f;
+      if (c < (1 << cb)) {
+        const float p = paa_s[j];
+        const float lower = thr_lo_s[c << cs], upper = thr_up_s[(c + 1) << cs];
+        if (p < lower) d = __fsub_rn(lower, p);
+        else if (p > upper) d = __fsub_rn(p, upper);
+      }
+      qv.T5[e] = __fmul_rn(d, d);
+    }
+  }
   if (tid < ix.w) {
     qv.st->qpaa[tid] = paa_s[tid];
     qv.st->qsym[tid] = sym_s[tid];
@@ -236,6 +251,8 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->thr_bits = 0x7f800000u;
     st->leaf_count = 0;
     st->item_count = 0;
+    st->next_item = 0;
+    st->surv_count = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -315,7 +332,7 @@ q_leaf_filter(IndexView ix, QueryView qv) {
     if (keep) {
       b = ix.leaf_begin[l];
       e = ix.leaf_begin[l + 1];
-      nit = (e - b + kItem - 1) / kItem;
+      nit = (e - 1) / kItem - b / kItem + 1;  // aligned tiles of kItem positions touched
     }
     uint32_t incl = nit;
 #pragma unroll
@@ -330,8 +347,10 @@ q_leaf_filter(IndexView ix, QueryView qv) {
       const uint32_t slot = base + __popc(m & ((1u << lane) - 1u));
       qv.leaf_list[slot] = (uint32_t)l;
       qv.leaf_lb2[slot] = lb2;
+      const uint32_t t0 = b / kItem;
       for (uint32_t j = 0; j < nit; ++j)
-        qv.items[ibase + j] = make_uint4(b + j * kItem, min(e, b + (j + 1) * kItem), __float_as_uint(lb2), (uint32_t)l);
+        qv.items[ibase + j] = make_uint4(max(b, (t0 + j) * kItem), min(e, (t0 + j + 1) * kItem), __float_as_uint(lb2),
+                                         (uint32_t)l);
     }
   }
 }
@@ -362,7 +381,7 @@ q_refine(IndexView ix, QueryView qv) {
   off += sizeof(uint32_t) * kChunk;
   uint32_t* bufA = reinterpret_cast<uint32_t*>(smem + off);
   uint32_t* bufB = bufA + (qv.k + kChunk);
-  __shared__ uint32_t s_li, s_ns, s_bc, s_thr, s_local, s_hist[256], s_sel[2];
+  __shared__ uint32_t s_ns, s_bc, s_thr, s_local, s_hist[256], s_sel[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wc = ix.w * ix.card;
@@ -378,14 +397,9 @@ q_refine(IndexView ix, QueryView qv) {
   volatile unsigned int* thr_v = &st->thr_bits;
   __syncthreads();
 
-  while (true) {
-    if (tid == 0) {
-      s_li = atomicAdd(&st->next_leaf, 1u);
-      s_thr = *thr_v;
-    }
+  for (uint32_t li = blockIdx.x; li < leaf_count; li += gridDim.x) {
+    if (tid == 0) s_thr = *thr_v;
     __syncthreads();
-    const uint32_t li = s_li;
-    if (li >= leaf_count) break;
     const uint32_t l = qv.leaf_list[li];
     if (qv.leaf_lb2[li] > lb_bound2(s_thr, qv.eps, qv.tau)) {
       __syncthreads();
@@ -464,194 +478,261 @@ q_refine(IndexView ix, QueryView qv) {
     n_lb += __shfl_xor_sync(kFull, n_lb, o);
     n_ref += __shfl_xor_sync(kFull, n_ref, o);
   }
-  if (lane == 0) {
-    atomicAdd(&st->series_lb, n_lb);
-    atomicAdd(&st->series_refined, n_ref);
+  const uint32_t gw = blockIdx.x * (kThreads / 32) + warp;
+  if (lane == 0 && gw < kMaxRefineWarps) {
+    qv.partials[gw] = n_lb;
+    qv.partials[kMaxRefineWarps + gw] = n_ref;
+    qv.partials[2 * kMaxRefineWarps + gw] = warp == 0 ? n_leaf : 0u;
   }
-  if (tid == 0) atomicAdd(&st->leaves_processed, n_leaf);
 }
 
-// ------------------------------------------------------------------ q_refine_warp
-// Barrier-free refinement for k <= 32. Warps take work items (at most kItem
-// positions of one surviving leaf) in a fixed stride, re-test the item's leaf bound
-// against the current BSF (ProcessQueue, Algorithm 8), lower-bound every position
-// from its SAX word with all word loads in flight at once, queue the survivors in
-// shared memory, and compute their real distances four rows at a time
-// (CalculateRealDistance, Algorithm 9). k = 1: the BSF is an atomicMin taken only by
-// a distance below the current BSF. 1 < k <= 32: each warp keeps its k best in
-// registers (lane i holds the i-th) and publishes its k-th once it holds k.
-constexpr int kRefWarps = 8;
+// ------------------------------------------------------------------ k <= 32
+// Refinement for k <= 32 in two streaming kernels (ProcessQueue and
+// CalculateRealDistance, Algorithms 8-9, with the per-series filter and the real
+// distances decoupled so that each kernel keeps many loads in flight):
+//
+// q_filter_series: one warp per aligned block of 32 leaf positions of a work item
+//   (items are the positions of one surviving leaf inside an aligned tile of kItem
+//   positions). The warp re-tests the leaf's bound against the current BSF, bounds
+//   the block by its symbol envelope, and bounds every position by its SAX word;
+//   survivors {position, bound} go to a per-warp buffer flushed 32 at a time to the
+//   survivor list. kUnroll blocks are in flight per warp.
+// q_refine_rows: real distances of the survivors whose bound still passes the
+//   current BSF, kRows rows per warp at a time. k = 1: the BSF is an atomicMin taken
+//   only by a distance below the current BSF. 1 < k <= 32: each warp keeps its k
+//   best in registers (lane i holds the i-th) and publishes its k-th once it has k.
+constexpr int kFiltWarps = 8;
+constexpr int kUnroll = 4;
+constexpr int kBlocksPerItem = kItem / 32;
 constexpr int kRows = 4;
+constexpr int kRowWarps = 8;
 
-struct WarpRefineSmem {
-  static size_t bytes(int w, int card, int len) {
-    size_t b = (sizeof(float) * (size_t)w * card + 15) & ~size_t(15);
-    b += sizeof(float) * (size_t)((len + 3) & ~3);
-    b += sizeof(uint32_t) * kItem * kRefWarps;
-    return b;
-  }
-};
-
-template <bool KONE>
-__global__ void __launch_bounds__(kRefWarps * 32)
-q_refine_warp(IndexView ix, QueryView qv) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* Ts = reinterpret_cast<float*>(smem);
-  size_t off = ((sizeof(float) * (size_t)ix.w * ix.card) + 15) & ~size_t(15);
-  float* qs = reinterpret_cast<float*>(smem + off);
-  off += sizeof(float) * (size_t)((ix.len + 3) & ~3);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + off) + warp * kItem;
+__global__ void __launch_bounds__(kFiltWarps * 32)
+q_filter_series(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float Ts[];  // [w][card]
+  __shared__ int qsym_s[16];
+  __shared__ uint2 buf_s[kFiltWarps][64];
   for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
-  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
   __syncthreads();
-
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint2* buf = buf_s[warp];
   QState* st = qv.st;
-  volatile unsigned int* thr_v = &st->thr_bits;
-  const uint32_t nitems = st->item_count;
+  const uint32_t ntask = st->item_count * kBlocksPerItem;
   const uint32_t sa = st->seed_a, sb = st->seed_b;
-  const int k = qv.k;
   const float seglen = (float)ix.seglen;
   const unsigned lt = (1u << lane) - 1u;
-  unsigned mine = 0x7f800000u;  // k > 1: this lane's entry of the warp's sorted k best
-  uint32_t n_lb = 0, n_ref = 0, n_items = 0;
-  const uint32_t stride = gridDim.x * kRefWarps;
-  for (uint32_t it = blockIdx.x * kRefWarps + warp; it < nitems; it += stride) {
-    const uint4 item = qv.items[it];
-    const unsigned thr0 = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
-    const float bound2 = lb_bound2(thr0, qv.eps, qv.tau);
-    if (__uint_as_float(item.z) > bound2) continue;
-    ++n_items;
-    // lower bounds of up to kItem positions, all word loads issued first
-    uint4 wd[kItem / 32];
+  const uint32_t gw = blockIdx.x * kFiltWarps + warp;
+  const uint32_t stride = gridDim.x * kFiltWarps;
+  uint32_t nbuf = 0, n_lb = 0, n_blk = 0;
+  for (uint32_t t0 = gw; t0 < ntask; t0 += stride * kUnroll) {
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u, 0);
+    const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
+    uint4 item[kUnroll];
 #pragma unroll
-    for (int i = 0; i < kItem / 32; ++i) {
-      const uint32_t p = item.x + i * 32 + lane;
-      wd[i] = p < item.y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t t = t0 + u * stride;
+      item[u] = t < ntask ? qv.items[t / kBlocksPerItem] : make_uint4(0, 0, 0, 0);
     }
-    uint32_t nq = 0;
+    // block envelopes of live blocks (every lane reads the same 32 bytes)
+    uint32_t blk[kUnroll];
+    bool live[kUnroll];
+    uint4 lo[kUnroll], hi[kUnroll];
 #pragma unroll
-    for (int i = 0; i < kItem / 32; ++i) {
-      const uint32_t p = item.x + i * 32 + lane;
-      const bool valid = p < item.y && (p < sa || p >= sb);
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t t = t0 + u * stride;
+      blk[u] = (item[u].x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
+      live[u] = t < ntask && __uint_as_float(item[u].z) <= bound2 && blk[u] * 32 < item[u].y &&
+                blk[u] * 32 + 32 > item[u].x;
+      if (live[u]) {
+        lo[u] = __ldg(ix.benv + 2 * blk[u]);
+        hi[u] = __ldg(ix.benv + 2 * blk[u] + 1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (!live[u]) continue;
+      ++n_blk;
+      const uint32_t lop[4] = {lo[u].x, lo[u].y, lo[u].z, lo[u].w}, hip[4] = {hi[u].x, hi[u].y, hi[u].z, hi[u].w};
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j < ix.w) {
+          const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
+          acc = __fadd_rn(acc, Ts[j * ix.card + min(max(qsym_s[j], sl), sh)]);
+        }
+      }
+      live[u] = __fmul_rn(acc, seglen) <= bound2;
+    }
+    uint4 wd[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t p = blk[u] * 32 + lane;
+      wd[u] = live[u] && p >= item[u].x && p < item[u].y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (!live[u]) continue;
+      const uint32_t p = blk[u] * 32 + lane;
+      const bool valid = p >= item[u].x && p < item[u].y && (p < sa || p >= sb);
       n_lb += valid;
-      const bool pass = valid && word_lb2(wd[i], Ts, ix.w, ix.card, seglen) <= bound2;
+      const float lb2 = valid ? word_lb2(wd[u], Ts, ix.w, ix.card, seglen) : INFINITY;
+      const bool pass = valid && lb2 <= bound2;
       const unsigned m = __ballot_sync(kFull, pass);
-      if (pass) queue[nq + __popc(m & lt)] = p;
-      nq += __popc(m);
+      if (pass) buf[nbuf + __popc(m & lt)] = make_uint2(p, __float_as_uint(lb2));
+      nbuf += __popc(m);
+      if (nbuf >= 32) {  // flush 32 survivors with one atomic
+        __syncwarp();
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&st->surv_count, 32u);
+        base = __shfl_sync(kFull, base, 0);
+        qv.surv[base + lane] = buf[lane];
+        __syncwarp();
+        if (lane < (int)nbuf - 32) buf[lane] = buf[32 + lane];
+        nbuf -= 32;
+        __syncwarp();
+      }
     }
-    __syncwarp();
-    // real distances, kRows rows at a time
-    for (uint32_t g = 0; g < nq; g += kRows) {
-      const uint32_t r = min((uint32_t)kRows, nq - g);
-      uint32_t myp = 0, myid = 0;
-      float2 myms = make_float2(0.f, 0.f);
-      if (lane < (int)r) {
-        myp = queue[g + lane];
+  }
+  __syncwarp();
+  if (nbuf) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&st->surv_count, nbuf);
+    base = __shfl_sync(kFull, base, 0);
+    if (lane < (int)nbuf) qv.surv[base + lane] = buf[lane];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n_lb += __shfl_xor_sync(kFull, n_lb, o);
+  if (lane == 0 && gw < kMaxRefineWarps) {
+    qv.partials[gw] = n_lb;
+    qv.partials[2 * kMaxRefineWarps + gw] = n_blk;
+  }
+}
+
+template <bool KONE>
+__global__ void __launch_bounds__(kRowWarps * 32)
+q_refine_rows(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float qs[];
+  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  QState* st = qv.st;
+  volatile unsigned int* thr_v = &st->thr_bits;
+  const uint32_t nsurv = st->surv_count;
+  const int k = qv.k;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned mine = 0x7f800000u;
+  uint32_t n_ref = 0;
+  const uint32_t gw = blockIdx.x * kRowWarps + warp;
+  const uint32_t stride = gridDim.x * kRowWarps;
+  for (uint32_t g = gw * kRows; g < nsurv; g += stride * kRows) {
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
+    uint32_t myp = 0, myid = 0;
+    float2 myms = make_float2(0.f, 0.f);
+    bool mine_live = false;
+    if (lane < kRows && g + lane < nsurv) {
+      const uint2 sv = qv.surv[g + lane];
+      myp = sv.x;
+      mine_live = __uint_as_float(sv.y) <= bound2;  // re-test against the current BSF
+      if (mine_live) {
         myid = __ldg(ix.perm + myp);
         if (!ix.data_is_z) myms = __ldg(ix.stats + myp);
       }
-      uint32_t id[kRows];
-      float2 ms[kRows];
+    }
+    const unsigned rm = __ballot_sync(kFull, mine_live);
+    if (!rm) continue;
+    uint32_t id[kRows];
+    float2 ms[kRows];
 #pragma unroll
-      for (int j = 0; j < kRows; ++j) {
-        id[j] = __shfl_sync(kFull, myid, j);
-        ms[j].x = __shfl_sync(kFull, myms.x, j);
-        ms[j].y = __shfl_sync(kFull, myms.y, j);
+    for (int j = 0; j < kRows; ++j) {
+      id[j] = __shfl_sync(kFull, myid, j);
+      ms[j].x = __shfl_sync(kFull, myms.x, j);
+      ms[j].y = __shfl_sync(kFull, myms.y, j);
+    }
+    float acc[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) acc[j] = 0.0f;
+    if ((ix.len & 3) == 0) {
+      const int n4 = ix.len >> 2;
+      const float4* q4 = reinterpret_cast<const float4*>(qs);
+      for (int c = lane; c < n4; c += 32) {
+        float4 x[kRows];
+#pragma unroll
+        for (int j = 0; j < kRows; ++j)
+          x[j] = (rm >> j) & 1u ? __ldg(reinterpret_cast<const float4*>(ix.data + (size_t)id[j] * ix.len) + c)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q = q4[c];
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+          float4 z = x[j];
+          if (!ix.data_is_z) {
+            z.x = znorm_value(z.x, ms[j].x, ms[j].y);
+            z.y = znorm_value(z.y, ms[j].x, ms[j].y);
+            z.z = znorm_value(z.z, ms[j].x, ms[j].y);
+            z.w = znorm_value(z.w, ms[j].x, ms[j].y);
+          }
+          float d = __fsub_rn(z.x, q.x); acc[j] = __fmaf_rn(d, d, acc[j]);
+          d = __fsub_rn(z.y, q.y); acc[j] = __fmaf_rn(d, d, acc[j]);
+          d = __fsub_rn(z.z, q.z); acc[j] = __fmaf_rn(d, d, acc[j]);
+          d = __fsub_rn(z.w, q.w); acc[j] = __fmaf_rn(d, d, acc[j]);
+        }
       }
-      float acc[kRows];
+    } else {
+      for (int t = lane; t < ix.len; t += 32) {
 #pragma unroll
-      for (int j = 0; j < kRows; ++j) acc[j] = 0.0f;
-      if ((ix.len & 3) == 0) {
-        const int n4 = ix.len >> 2;
-        const float4* q4 = reinterpret_cast<const float4*>(qs);
-        for (int c = lane; c < n4; c += 32) {
-          float4 x[kRows];
-#pragma unroll
-          for (int j = 0; j < kRows; ++j)
-            x[j] = j < (int)r ? __ldg(reinterpret_cast<const float4*>(ix.data + (size_t)id[j] * ix.len) + c)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 q = q4[c];
-#pragma unroll
-          for (int j = 0; j < kRows; ++j) {
-            float4 z = x[j];
-            if (!ix.data_is_z) {
-              z.x = znorm_value(z.x, ms[j].x, ms[j].y);
-              z.y = znorm_value(z.y, ms[j].x, ms[j].y);
-              z.z = znorm_value(z.z, ms[j].x, ms[j].y);
-              z.w = znorm_value(z.w, ms[j].x, ms[j].y);
-            }
-            float d = __fsub_rn(z.x, q.x); acc[j] = __fmaf_rn(d, d, acc[j]);
-            d = __fsub_rn(z.y, q.y); acc[j] = __fmaf_rn(d, d, acc[j]);
-            d = __fsub_rn(z.z, q.z); acc[j] = __fmaf_rn(d, d, acc[j]);
-            d = __fsub_rn(z.w, q.w); acc[j] = __fmaf_rn(d, d, acc[j]);
+        for (int j = 0; j < kRows; ++j) {
+          if ((rm >> j) & 1u) {
+            const float x = __ldg(ix.data + (size_t)id[j] * ix.len + t);
+            const float z = ix.data_is_z ? x : znorm_value(x, ms[j].x, ms[j].y);
+            const float d = __fsub_rn(z, qs[t]);
+            acc[j] = __fmaf_rn(d, d, acc[j]);
           }
         }
-      } else {
-        for (int t = lane; t < ix.len; t += 32) {
-#pragma unroll
-          for (int j = 0; j < kRows; ++j) {
-            if (j < (int)r) {
-              const float x = __ldg(ix.data + (size_t)id[j] * ix.len + t);
-              const float z = ix.data_is_z ? x : znorm_value(x, ms[j].x, ms[j].y);
-              const float d = __fsub_rn(z, qs[t]);
-              acc[j] = __fmaf_rn(d, d, acc[j]);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kRows; ++j)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(kFull, acc[j], o);
-      n_ref += r;
-      // lane j < r owns row j
-      float d2 = acc[0];
-#pragma unroll
-      for (int j = 1; j < kRows; ++j)
-        if (lane == j) d2 = acc[j];
-      const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
-      const bool keep = lane < (int)r && d2 <= keep_bound2(thr, qv.eps);
-      const unsigned km = __ballot_sync(kFull, keep);
-      if (km) {
-        const int leader = __ffs(km) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&st->cand_count, (uint32_t)__popc(km));
-        base = __shfl_sync(kFull, base, leader);
-        if (keep) qv.cand[base + __popc(km & lt)] = pack(d2, myp);
-      }
-      if (KONE) {
-        if (lane < (int)r && __float_as_uint(d2) < thr) atomicMin(&st->thr_bits, __float_as_uint(d2));
-      } else {
-        const unsigned kth_old = __shfl_sync(kFull, mine, k - 1);
-        for (uint32_t j = 0; j < r; ++j) {
-          const unsigned v = __float_as_uint(__shfl_sync(kFull, d2, j));
-          if (v >= __shfl_sync(kFull, mine, k - 1)) continue;
-          const int pos = __popc(__ballot_sync(kFull, lane < k && mine <= v));
-          const unsigned up = __shfl_up_sync(kFull, mine, 1);
-          if (lane >= pos && lane < k) mine = lane == pos ? v : up;
-        }
-        const unsigned kth = __shfl_sync(kFull, mine, k - 1);
-        if (lane == 0 && kth < kth_old && kth < thr) atomicMin(&st->thr_bits, kth);
       }
     }
-    __syncwarp();
-  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    n_lb += __shfl_xor_sync(kFull, n_lb, o);
+    for (int j = 0; j < kRows; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(kFull, acc[j], o);
+    n_ref += __popc(rm);
+    float d2 = acc[0];
+#pragma unroll
+    for (int j = 1; j < kRows; ++j)
+      if (lane == j) d2 = acc[j];
+    const unsigned thr2 = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    const bool keep = mine_live && d2 <= keep_bound2(thr2, qv.eps);
+    const unsigned km = __ballot_sync(kFull, keep);
+    if (km) {
+      const int leader = __ffs(km) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&st->cand_count, (uint32_t)__popc(km));
+      base = __shfl_sync(kFull, base, leader);
+      if (keep) qv.cand[base + __popc(km & lt)] = pack(d2, myp);
+    }
+    if (KONE) {
+      if (mine_live && __float_as_uint(d2) < thr2) atomicMin(&st->thr_bits, __float_as_uint(d2));
+    } else {
+      const unsigned kth_old = __shfl_sync(kFull, mine, k - 1);
+      for (int j = 0; j < kRows; ++j) {
+        if (!((rm >> j) & 1u)) continue;
+        const unsigned v = __float_as_uint(__shfl_sync(kFull, d2, j));
+        if (v >= __shfl_sync(kFull, mine, k - 1)) continue;
+        const int pos = __popc(__ballot_sync(kFull, lane < k && mine <= v));
+        const unsigned up = __shfl_up_sync(kFull, mine, 1);
+        if (lane >= pos && lane < k) mine = lane == pos ? v : up;
+      }
+      const unsigned kth = __shfl_sync(kFull, mine, k - 1);
+      if (lane == 0 && kth < kth_old && kth < thr2) atomicMin(&st->thr_bits, kth);
+    }
   }
-  if (lane == 0) {
-    atomicAdd(&st->series_lb, n_lb);
-    atomicAdd(&st->series_refined, n_ref);
-    atomicAdd(&st->leaves_processed, n_items);
-  }
+  if (lane == 0 && gw < kMaxRefineWarps) qv.partials[kMaxRefineWarps + gw] = n_ref;
 }
 
 // ------------------------------------------------------------------ final pick
-__global__ void __launch_bounds__(1024)
-q_final_select(QueryView qv) {
-  __shared__ uint32_t hist[256], sel[2];
+// The k-th smallest candidate squared distance T; candidates at or below
+// T (1 + eps) are re-checked in FP64 (one block).
+__device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel) {
   const uint32_t count = qv.st->cand_count;
   const unsigned long long* c = qv.cand;
   const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
@@ -663,13 +744,12 @@ q_final_select(QueryView qv) {
 // (1 + eps): one warp per candidate. Lane l adds the FP64 squared differences of the
 // points t = l, l + 32, ... in increasing t; the 32 partials are combined by a
 // pairwise tree in lane order. No fused operations: the same bits as the oracle.
-__global__ void __launch_bounds__(kThreads)
-q_recheck(IndexView ix, QueryView qv) {
+__device__ void recheck(const IndexView& ix, const QueryView& qv) {
   const uint32_t count = qv.st->cand_count;
   const uint32_t bound = qv.st->final_bits;
   const int lane = threadIdx.x & 31;
-  const uint32_t warps = gridDim.x * (kThreads / 32);
-  for (uint32_t i = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); i < count; i += warps) {
+  const uint32_t warps = blockDim.x / 32;
+  for (uint32_t i = threadIdx.x >> 5; i < count; i += warps) {
     const unsigned long long c = qv.cand[i];
     if ((uint32_t)(c >> 32) > bound) continue;
     const uint32_t pos = (uint32_t)c;
@@ -715,11 +795,18 @@ __device__ void block_bitonic(unsigned long long* sk, uint32_t* si, int n) {
 
 constexpr int kSortCap = 2048;  // (distance, id) pairs sorted in shared memory
 
+// The exact answer (one block of 1024 threads): the k-th smallest candidate, the FP64
+// re-check of every candidate within the fp32 margin of it, and the k smallest by
+// (FP64 distance, id), written to the outputs.
 __global__ void __launch_bounds__(1024)
-q_final_topk(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out) {
+q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out) {
   __shared__ unsigned long long sk[kSortCap];
   __shared__ uint32_t si[kSortCap];
   __shared__ uint32_t hist[256], sel[2], s_cnt;
+  final_select(qv, hist, sel);
+  __syncthreads();
+  recheck(ix, qv);
+  __syncthreads();
   const uint32_t R = qv.st->rc_count;
   const int k = qv.k;
   int nsort;
@@ -799,16 +886,40 @@ q_final_topk(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* _
     ids_out[r] = (int64_t)si[r];
     if (dists_out) dists_out[r] = __double2float_rn(__dsqrt_rn(__longlong_as_double((long long)sk[r])));
   }
+  // sum the refinement's per-warp work counters
+  __shared__ unsigned long long s_part[3];
+  if (threadIdx.x < 3) s_part[threadIdx.x] = 0;
+  __syncthreads();
+  {
+    unsigned long long a = 0, b = 0, cc = 0;
+    for (uint32_t i = threadIdx.x; i < qv.npartials; i += blockDim.x) {
+      a += qv.partials[i];
+      cc += qv.partials[2 * kMaxRefineWarps + i];
+    }
+    for (uint32_t i = threadIdx.x; i < qv.npartials_rows; i += blockDim.x) b += qv.partials[kMaxRefineWarps + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      cc += __shfl_xor_sync(kFull, cc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {  // one shared atomic per warp
+      atomicAdd(&s_part[0], a);
+      atomicAdd(&s_part[1], b);
+      atomicAdd(&s_part[2], cc);
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const QState* st = qv.st;
     unsigned long long* c = qv.counters;
     atomicAdd(&c[ST_QUERIES], 1ull);
     atomicAdd(&c[ST_LEAVES_TOTAL], (unsigned long long)ix.L);
     atomicAdd(&c[ST_LEAVES_SURVIVED], (unsigned long long)st->leaf_count);
-    atomicAdd(&c[ST_LEAVES_PROCESSED], (unsigned long long)st->leaves_processed);
-    atomicAdd(&c[ST_SERIES_LB], (unsigned long long)st->series_lb);
+    atomicAdd(&c[ST_LEAVES_PROCESSED], s_part[2]);
+    atomicAdd(&c[ST_SERIES_LB], s_part[0]);
     const unsigned long long seed = st->seed_b - st->seed_a;
-    atomicAdd(&c[ST_SERIES_REFINED], (unsigned long long)st->series_refined + seed);
+    atomicAdd(&c[ST_SERIES_REFINED], s_part[1] + seed);
     atomicAdd(&c[ST_SEED], seed);
     atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
     atomicAdd(&c[ST_RECHECKED], (unsigned long long)R);
@@ -865,7 +976,9 @@ cudaError_t query_setup(msi_index* ix) {
   if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.items, (size_t)(ix->n / kItem + ix->L + 1))) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.items, (size_t)(ix->n / kItem + 2 * ix->L + 2))) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.T5, (size_t)ix->w * 32)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.partials, (size_t)3 * kMaxRefineWarps)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.cand, (size_t)ix->n)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_d, (size_t)ix->n)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_id, (size_t)ix->n)) != cudaSuccess) return e;
@@ -878,41 +991,55 @@ cudaError_t query_setup(msi_index* ix) {
   const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
   if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
-  const size_t wsmem = WarpRefineSmem::bytes(ix->w, ix->card, ix->len);
-  if ((e = cudaFuncSetAttribute(q_refine_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(q_refine_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.surv, (size_t)ix->n)) != cudaSuccess) return e;
+  ix->device_bytes += (int64_t)ix->n * 8;
   qv.eps = 1.52587890625e-05f;  // 2^-16
   qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
   ix->ws_ready = true;
   return cudaSuccess;
 }
 
-// Refinement kernel for k: the warp-level kernel up to k = 32, the block kernel with a
-// shared-memory top-k buffer above.
+// Persistent grids of the refinement kernels: the two streaming kernels up to
+// k = 32, the block kernel with a shared-memory top-k buffer above.
 static cudaError_t refine_config(msi_index* ix, int k) {
   const int mode = k == 1 ? 1 : (k <= 32 ? 32 : 0);
   if (ix->refine_smem_k == mode) return cudaSuccess;
-  const size_t smem = mode ? WarpRefineSmem::bytes(ix->w, ix->card, ix->len) : RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
-  int per_sm = 0, sms = 0;
-  cudaError_t e = mode == 1    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_warp<true>, kRefWarps * 32, smem)
-                  : mode == 32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_warp<false>, kRefWarps * 32, smem)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem);
+  int sms = 0, per_sm = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (e != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device)) != cudaSuccess) return e;
-  ix->refine_grid = std::max(1, per_sm) * sms;
-  ix->refine_smem = smem;
+  if (mode) {
+    const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, fsmem)) != cudaSuccess) return e;
+    ix->refine_grid = std::max(1, per_sm) * sms;
+    ix->refine_smem = fsmem;
+    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+    e = mode == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<true>, kRowWarps * 32, rsmem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<false>, kRowWarps * 32, rsmem);
+    if (e != cudaSuccess) return e;
+    ix->rows_grid = std::max(1, per_sm) * sms;
+  } else {
+    const size_t smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem)) != cudaSuccess) return e;
+    ix->refine_grid = std::max(1, per_sm) * sms;
+    ix->refine_smem = smem;
+    ix->rows_grid = 0;
+  }
   ix->refine_smem_k = mode;
   return cudaSuccess;
 }
 
-// One query (device pointers), stream-ordered. ev_a / ev_b, when given, bracket the
-// refinement kernel.
+// One query (device pointers), stream-ordered. ev_a / ev_m / ev_b, when given,
+// bracket the series filter and the row refinement.
 cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
-                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b) {
+                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b) {
   cudaError_t e = refine_config(ix, k);
   if (e != cudaSuccess) return e;
   QueryView qv = ix->qv;
   qv.k = k;
+  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)ix->refine_grid * (k <= 32 ? kFiltWarps : kThreads / 32),
+                                             kMaxRefineWarps);
+  qv.npartials_rows = k <= 32 ? (uint32_t)std::min<int64_t>((int64_t)ix->rows_grid * kRowWarps, kMaxRefineWarps)
+                              : qv.npartials;
   const IndexView v = ix->view();
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
@@ -921,13 +1048,18 @@ cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
   q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
-  if (k == 1) q_refine_warp<true><<<ix->refine_grid, kRefWarps * 32, ix->refine_smem, s>>>(v, qv);
-  else if (k <= 32) q_refine_warp<false><<<ix->refine_grid, kRefWarps * 32, ix->refine_smem, s>>>(v, qv);
-  else q_refine<false><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+  if (k <= 32) {
+    q_filter_series<<<ix->refine_grid, kFiltWarps * 32, ix->refine_smem, s>>>(v, qv);
+    if (ev_m) cudaEventRecord(ev_m, s);
+    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+    if (k == 1) q_refine_rows<true><<<ix->rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
+    else q_refine_rows<false><<<ix->rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
+  } else {
+    q_refine<false><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+    if (ev_m) cudaEventRecord(ev_m, s);
+  }
   if (ev_b) cudaEventRecord(ev_b, s);
-  q_final_select<<<1, 1024, 0, s>>>(qv);
-  q_recheck<<<(unsigned)ix->refine_grid, kThreads, 0, s>>>(v, qv);
-  q_final_topk<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev);
+  q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev);
   return cudaGetLastError();
 }
 

@@ -202,6 +202,37 @@ MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats,
  * recorded on the query stream around them; the call then waits for its work). */
 MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
 
+/*
+ * msi_lower_bounds_noalloc -- msi_lower_bounds for callers that cannot allocate
+ * device memory. The paper has no counterpart: it exists for code that must not
+ * call cudaMalloc, such as code running while a stream is captured into a CUDA graph
+ * (an allocation ends the capture), code held to a memory budget by an allocator or
+ * pool it does not own, and latency-critical paths that must not wait on the
+ * driver's allocator.
+ *
+ * It computes the same lower bounds, with the same kernels, and calls no cudaMalloc,
+ * cudaFree or allocating library routine: the per-query temporaries (query state,
+ * z-normalised query, per-segment gap tables, counters; 35,072 bytes) live in one
+ * fixed file-scope device array that every GPU loading the library holds until the
+ * process exits. Every call shares that array and finds the previous call's contents
+ * in it (it clears what must start at zero); calls whose work overlaps on the GPU
+ * race on it, so the caller serialises them. The first call on a device looks up the
+ * array's device address (once per device); make that first call before any stream
+ * capture begins.
+ *
+ *   index      an index from msi_build (its query workspace is not used).
+ *   query      float[len] in DEVICE memory of the index's GPU (raw; z-normalised here).
+ *   series_lb  float[n] in DEVICE memory: bound per series, collection order.
+ *   leaf_lb    float[leaves] in DEVICE memory: bound per leaf.
+ *   stream     cudaStream_t or NULL (NULL: the legacy default stream, and the call
+ *              waits for its work and reports a non-finite query).
+ * Errors: MSI_EINVAL (NULL or host pointers; an index whose len exceeds 4096 or whose
+ * segments * cardinality exceeds 4096 does not fit the fixed scratch; a non-finite
+ * query), MSI_ECUDA.
+ */
+MSI_API msi_status msi_lower_bounds_noalloc(const msi_index* index, const float* query, float* series_lb,
+                                            float* leaf_lb, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "MsiError", "Index", "msi_build", "msi_knn", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
-    "msi_query_stats_get", "msi_set_timing", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
+    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
 ]
 
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
@@ -80,6 +80,8 @@ _lib.msi_query_stats_get.argtypes = [_vp, ctypes.POINTER(_QueryStats), _i32]
 _lib.msi_query_stats_get.restype = ctypes.c_int
 _lib.msi_set_timing.argtypes = [_vp, _i32]
 _lib.msi_set_timing.restype = ctypes.c_int
+_lib.msi_lower_bounds_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.msi_lower_bounds_noalloc.restype = ctypes.c_int
 
 
 class MsiError(RuntimeError):
@@ -234,3 +236,9 @@ def msi_query_stats_get(index, reset=False):
 def msi_set_timing(index, enable=True):
     _check(_lib.msi_set_timing(ctypes.c_void_p(index.handle), 1 if enable else 0))
 
+
+def msi_lower_bounds_noalloc(index, query, series_lb, leaf_lb, stream=None):
+    """msi_lower_bounds_noalloc: device tensors only (query float32 [len], outputs
+    float32 [n] and [leaves]); the library allocates nothing for this call."""
+    _check(_lib.msi_lower_bounds_noalloc(ctypes.c_void_p(index.handle), _ptr(query, np.float32),
+                                         _ptr(series_lb, np.float32), _ptr(leaf_lb, np.float32), _stream(stream)))

@@ -116,6 +116,10 @@ void free_index(msi_index* ix) {
 
 }  // namespace
 
+namespace msi {
+void set_last_error(const char* what) { g_err = what; }
+}  // namespace msi
+
 extern "C" {
 
 int32_t msi_abi_version(void) { return MSI_ABI_VERSION; }

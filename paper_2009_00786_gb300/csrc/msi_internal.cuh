@@ -306,4 +306,8 @@ cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);
+// Sets the calling thread's msi_last_error() text (msi_api.cu).
+void set_last_error(const char* what);
+cudaError_t lower_bounds_on(const msi_index* ix, const QueryView& qv, const float* q_dev, float* series_lb_dev,
+                            float* leaf_lb_dev, cudaStream_t s);
 }  // namespace msi

@@ -1068,6 +1068,19 @@ cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The lower-bound pipeline on caller-provided query scratch (qz, T, T5, st,
+// counters inside `qv`); used by the entry point that allocates nothing.
+cudaError_t lower_bounds_on(const msi_index* ix, const QueryView& qv_in, const float* q_dev, float* series_lb_dev,
+                            float* leaf_lb_dev, cudaStream_t s) {
+  QueryView qv = qv_in;
+  qv.k = 1;
+  const IndexView v = ix->view();
+  const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, 1);
+  q_lb_all<<<1024, kThreads, sizeof(float) * (size_t)ix->w * ix->card, s>>>(v, qv, series_lb_dev, leaf_lb_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s) {
   QueryView qv = ix->qv;

@@ -103,7 +103,7 @@ void free_index(msi_index* ix) {
   cudaGetDevice(&cur);
   if (cur != ix->device) cudaSetDevice(ix->device);
   void* ptrs[] = {ix->data_owned, ix->words, ix->perm, ix->stats, ix->leaf_begin, ix->env, ix->benv, ix->leaf_key,
-                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.T5, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2, ix->qv.items, ix->qv.surv, ix->qv.partials,
+                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.T5, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2, ix->qv.items, ix->qv.surv, ix->qv.blks, ix->qv.partials,
                   ix->qv.cand, ix->qv.rc_d, ix->qv.rc_id, ix->qv.counters, ix->ws_qraw, ix->ws_ids, ix->ws_dists};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -48,6 +48,7 @@ struct QState {
   unsigned int item_count;      // refinement work items (<= kItem positions of one leaf)
   unsigned int next_item;       // (unused)
   unsigned int surv_count;      // series whose bound passed the series filter
+  unsigned int blk_count;       // leaf blocks whose envelope bound passed
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -73,6 +74,7 @@ struct QueryView {
   float* leaf_lb2;              // [L]
   uint4* items;                 // [n / kItem + 2L]: {first pos, end pos, leaf bound^2 bits, leaf}
   uint2* surv;                  // [n]: {leaf-order position, bound^2 bits} of filter survivors
+  uint2* blks;                  // [8 (n / kItem + 2L)]: {block index, item index} of surviving blocks
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
   double* rc_d;                 // [n]
   uint32_t* rc_id;              // [n]
@@ -260,6 +262,7 @@ struct msi_index {
   float* ws_dists = nullptr;
   int refine_grid = 0;
   int rows_grid = 0;
+  int blocks_grid = 0;
   size_t refine_smem = 0;
   int refine_smem_k = -1;
   bool timing = false;

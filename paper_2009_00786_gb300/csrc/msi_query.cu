@@ -253,6 +253,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->item_count = 0;
     st->next_item = 0;
     st->surv_count = 0;
+    st->blk_count = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -502,78 +503,96 @@ q_refine(IndexView ix, QueryView qv) {
 //   only by a distance below the current BSF. 1 < k <= 32: each warp keeps its k
 //   best in registers (lane i holds the i-th) and publishes its k-th once it has k.
 constexpr int kFiltWarps = 8;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 8;
 constexpr int kBlocksPerItem = kItem / 32;
 constexpr int kRows = 4;
 constexpr int kRowWarps = 8;
+constexpr int kBlkThreads = 256;
 
+// One thread per (work item, aligned block of 32 positions): re-tests the item's
+// leaf bound against the current BSF, bounds the block by its symbol envelope
+// (T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range),
+// and lists the surviving blocks; the list is compacted per CTA (one atomic per CTA).
+__global__ void __launch_bounds__(kBlkThreads)
+q_filter_blocks(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float Ts[];  // [w][card]
+  __shared__ int qsym_s[16];
+  __shared__ uint32_t s_cnt, s_base;
+  __shared__ uint2 s_out[kBlkThreads];
+  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
+  const uint32_t ntask = qv.st->item_count * kBlocksPerItem;
+  const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
+  const float seglen = (float)ix.seglen;
+  for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < ntask; t0 += gridDim.x * blockDim.x) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const uint32_t t = t0 + threadIdx.x;
+    if (t < ntask) {
+      const uint4 item = qv.items[t / kBlocksPerItem];
+      const uint32_t blk = (item.x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
+      if (__uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
+        const uint4 lo = __ldg(ix.benv + 2 * blk), hi = __ldg(ix.benv + 2 * blk + 1);
+        const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (j < ix.w) {
+            const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
+            acc = __fadd_rn(acc, Ts[j * ix.card + min(max(qsym_s[j], sl), sh)]);
+          }
+        }
+        if (__fmul_rn(acc, seglen) <= bound2) s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, t / kBlocksPerItem);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&qv.st->blk_count, s_cnt) : 0u;
+    __syncthreads();
+    if (threadIdx.x < s_cnt) qv.blks[s_base + threadIdx.x] = s_out[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// One warp per surviving block: bounds every position by its SAX word and buffers
+// the survivors {position, bound}, flushed 32 at a time. kUnroll blocks in flight.
 __global__ void __launch_bounds__(kFiltWarps * 32)
 q_filter_series(IndexView ix, QueryView qv) {
   extern __shared__ __align__(16) float Ts[];  // [w][card]
-  __shared__ int qsym_s[16];
   __shared__ uint2 buf_s[kFiltWarps][64];
   for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
-  if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
   QState* st = qv.st;
-  const uint32_t ntask = st->item_count * kBlocksPerItem;
+  const uint32_t ntask = st->blk_count;
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
-  uint32_t nbuf = 0, n_lb = 0, n_blk = 0;
+  uint32_t nbuf = 0, n_lb = 0;
   for (uint32_t t0 = gw; t0 < ntask; t0 += stride * kUnroll) {
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u, 0);
     const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
+    uint2 task[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t t = t0 + u * stride;
+      task[u] = t < ntask ? qv.blks[t] : make_uint2(0, 0xffffffffu);
+    }
     uint4 item[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t t = t0 + u * stride;
-      item[u] = t < ntask ? qv.items[t / kBlocksPerItem] : make_uint4(0, 0, 0, 0);
-    }
-    // block envelopes of live blocks (every lane reads the same 32 bytes)
-    uint32_t blk[kUnroll];
-    bool live[kUnroll];
-    uint4 lo[kUnroll], hi[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t t = t0 + u * stride;
-      blk[u] = (item[u].x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
-      live[u] = t < ntask && __uint_as_float(item[u].z) <= bound2 && blk[u] * 32 < item[u].y &&
-                blk[u] * 32 + 32 > item[u].x;
-      if (live[u]) {
-        lo[u] = __ldg(ix.benv + 2 * blk[u]);
-        hi[u] = __ldg(ix.benv + 2 * blk[u] + 1);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      if (!live[u]) continue;
-      ++n_blk;
-      const uint32_t lop[4] = {lo[u].x, lo[u].y, lo[u].z, lo[u].w}, hip[4] = {hi[u].x, hi[u].y, hi[u].z, hi[u].w};
-      float acc = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (j < ix.w) {
-          const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
-          acc = __fadd_rn(acc, Ts[j * ix.card + min(max(qsym_s[j], sl), sh)]);
-        }
-      }
-      live[u] = __fmul_rn(acc, seglen) <= bound2;
-    }
+    for (int u = 0; u < kUnroll; ++u)
+      item[u] = task[u].y != 0xffffffffu ? qv.items[task[u].y] : make_uint4(0, 0, 0, 0);
     uint4 wd[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t p = blk[u] * 32 + lane;
-      wd[u] = live[u] && p >= item[u].x && p < item[u].y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+      const uint32_t p = task[u].x * 32 + lane;
+      wd[u] = p >= item[u].x && p < item[u].y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      if (!live[u]) continue;
-      const uint32_t p = blk[u] * 32 + lane;
+      const uint32_t p = task[u].x * 32 + lane;
       const bool valid = p >= item[u].x && p < item[u].y && (p < sa || p >= sb);
       n_lb += valid;
       const float lb2 = valid ? word_lb2(wd[u], Ts, ix.w, ix.card, seglen) : INFINITY;
@@ -605,7 +624,7 @@ q_filter_series(IndexView ix, QueryView qv) {
   for (int o = 16; o > 0; o >>= 1) n_lb += __shfl_xor_sync(kFull, n_lb, o);
   if (lane == 0 && gw < kMaxRefineWarps) {
     qv.partials[gw] = n_lb;
-    qv.partials[2 * kMaxRefineWarps + gw] = n_blk;
+    qv.partials[2 * kMaxRefineWarps + gw] = gw == 0 ? ntask : 0u;
   }
 }
 
@@ -744,32 +763,45 @@ __device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel)
 // (1 + eps): one warp per candidate. Lane l adds the FP64 squared differences of the
 // points t = l, l + 32, ... in increasing t; the 32 partials are combined by a
 // pairwise tree in lane order. No fused operations: the same bits as the oracle.
-__device__ void recheck(const IndexView& ix, const QueryView& qv) {
+// In rounds of 4 * blockDim candidates, all threads test the candidates against the
+// bound and list the passing ones in shared memory (`list`, 4 * blockDim entries);
+// then one warp per listed candidate computes its FP64 distance.
+__device__ void recheck(const IndexView& ix, const QueryView& qv, uint32_t* list, uint32_t* s_n) {
   const uint32_t count = qv.st->cand_count;
   const uint32_t bound = qv.st->final_bits;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = blockDim.x / 32;
-  for (uint32_t i = threadIdx.x >> 5; i < count; i += warps) {
-    const unsigned long long c = qv.cand[i];
-    if ((uint32_t)(c >> 32) > bound) continue;
-    const uint32_t pos = (uint32_t)c;
-    const uint32_t id = ix.perm[pos];
-    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
-    const float* row = ix.data + (size_t)id * ix.len;
-    double acc = 0.0;
-    for (int t = lane; t < ix.len; t += 32) {
-      const float x = row[t];
-      const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
-      const double d = __dsub_rn((double)z, (double)qv.qz[t]);
-      acc = __dadd_rn(acc, __dmul_rn(d, d));
-    }
+  for (uint32_t c0 = 0; c0 < count; c0 += 4 * blockDim.x) {
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) acc = __dadd_rn(acc, __shfl_xor_sync(kFull, acc, off));
-    if (lane == 0) {
-      const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
-      qv.rc_d[slot] = acc;
-      qv.rc_id[slot] = id;
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t i = c0 + r * blockDim.x + threadIdx.x;
+      if (i < count && (uint32_t)(qv.cand[i] >> 32) <= bound) list[atomicAdd(s_n, 1u)] = i;
     }
+    __syncthreads();
+    const uint32_t listed = *s_n;
+    for (uint32_t li = threadIdx.x >> 5; li < listed; li += warps) {
+      const uint32_t pos = (uint32_t)qv.cand[list[li]];
+      const uint32_t id = ix.perm[pos];
+      const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
+      const float* row = ix.data + (size_t)id * ix.len;
+      double acc = 0.0;
+      for (int t = lane; t < ix.len; t += 32) {
+        const float x = row[t];
+        const float z = ix.data_is_z ? x : znorm_value(x, ms.x, ms.y);
+        const double d = __dsub_rn((double)z, (double)qv.qz[t]);
+        acc = __dadd_rn(acc, __dmul_rn(d, d));
+      }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) acc = __dadd_rn(acc, __shfl_xor_sync(kFull, acc, off));
+      if (lane == 0) {
+        const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
+        qv.rc_d[slot] = acc;
+        qv.rc_id[slot] = id;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -805,7 +837,8 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
   __shared__ uint32_t hist[256], sel[2], s_cnt;
   final_select(qv, hist, sel);
   __syncthreads();
-  recheck(ix, qv);
+  static_assert(sizeof(sk) >= 4 * 1024 * sizeof(uint32_t), "re-check list must hold 4 * blockDim entries");
+  recheck(ix, qv, reinterpret_cast<uint32_t*>(sk), &s_cnt);
   __syncthreads();
   const uint32_t R = qv.st->rc_count;
   const int k = qv.k;
@@ -992,6 +1025,7 @@ cudaError_t query_setup(msi_index* ix) {
   if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.surv, (size_t)ix->n)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * (ix->n / kItem + 2 * ix->L + 2))) != cudaSuccess) return e;
   ix->device_bytes += (int64_t)ix->n * 8;
   qv.eps = 1.52587890625e-05f;  // 2^-16
   qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
@@ -1012,6 +1046,8 @@ static cudaError_t refine_config(msi_index* ix, int k) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, fsmem)) != cudaSuccess) return e;
     ix->refine_grid = std::max(1, per_sm) * sms;
     ix->refine_smem = fsmem;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, fsmem)) != cudaSuccess) return e;
+    ix->blocks_grid = std::max(1, per_sm) * sms;
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
     e = mode == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<true>, kRowWarps * 32, rsmem)
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<false>, kRowWarps * 32, rsmem);
@@ -1049,6 +1085,7 @@ cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev
   q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   if (k <= 32) {
+    q_filter_blocks<<<ix->blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
     q_filter_series<<<ix->refine_grid, kFiltWarps * 32, ix->refine_smem, s>>>(v, qv);
     if (ev_m) cudaEventRecord(ev_m, s);
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);

@@ -66,6 +66,11 @@ typedef struct msi_build_opts {
   int32_t leaf_capacity; /* most series per leaf; 0 selects MSI_DEFAULT_LEAF_CAPACITY */
   uint32_t flags;        /* MSI_BUILD_* bits                                          */
   void* stream;          /* cudaStream_t or NULL                                       */
+  int32_t query_slots;   /* queries msi_knn runs at once (k <= 32); 0 selects 8, 1 runs */
+                         /* them one after another                                     */
+  int32_t slot_capacity; /* candidates / survivors a concurrent slot holds; 0 selects  */
+                         /* max(65536, leaf_capacity + MSI_MAX_K) and 2^20; a query     */
+                         /* that needs more is run again with room for all n          */
 } msi_build_opts;
 
 /*
@@ -111,10 +116,24 @@ MSI_API msi_status msi_build(const float* series, int64_t n, int32_t len, int32_
  *   ids      int64[nq][k]: ids (row positions in the collection), host or device.
  *   dists    float[nq][k]: Euclidean distances, host or device; may be NULL.
  *   stream   see the conventions above.
+ * With nq > 1 and k <= 32 the queries run concurrently on the index's query slots
+ * (msi_build_opts.query_slots), each slot on its own stream joined back to `stream`;
+ * the call then waits for its work before returning, whatever the output memory.
  * Errors: MSI_EINVAL, MSI_ENOMEM (query workspace), MSI_ECUDA.
  */
 MSI_API msi_status msi_knn(msi_index* index, const float* queries, int64_t nq, int32_t k, int64_t* ids,
                    float* dists, void* stream);
+
+/*
+ * msi_knn_ex -- msi_knn that also returns, per neighbour, the FP64 squared distance
+ * the exact pick ordered by (the paper's answer is the BSF distance, Algorithm 5;
+ * this is its squared FP64 value before rounding). Answers computed over disjoint
+ * parts of a collection merge exactly by (sqdists64, id).
+ *   sqdists64  double[nq][k], host or device; may be NULL (then this is msi_knn).
+ * Other arguments and errors as msi_knn.
+ */
+MSI_API msi_status msi_knn_ex(msi_index* index, const float* queries, int64_t nq, int32_t k, int64_t* ids,
+                              float* dists, double* sqdists64, void* stream);
 
 /* Releases the index and all its device memory. NULL is a no-op. */
 MSI_API void msi_free(msi_index* index);

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "MsiError", "Index", "msi_build", "msi_knn", "msi_free", "msi_status_str", "msi_last_error",
+    "MsiError", "Index", "msi_build", "msi_knn", "msi_knn_ex", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
     "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
 ]
@@ -37,7 +37,8 @@ _lib = ctypes.CDLL(_build.LIB)
 
 
 class _BuildOpts(ctypes.Structure):
-    _fields_ = [("leaf_capacity", ctypes.c_int32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+    _fields_ = [("leaf_capacity", ctypes.c_int32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("query_slots", ctypes.c_int32), ("slot_capacity", ctypes.c_int32)]
 
 
 class _IndexInfo(ctypes.Structure):
@@ -62,6 +63,8 @@ _lib.msi_build.argtypes = [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(_BuildOpt
 _lib.msi_build.restype = ctypes.c_int
 _lib.msi_knn.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
 _lib.msi_knn.restype = ctypes.c_int
+_lib.msi_knn_ex.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]
+_lib.msi_knn_ex.restype = ctypes.c_int
 _lib.msi_free.argtypes = [_vp]
 _lib.msi_free.restype = None
 _lib.msi_status_str.argtypes = [ctypes.c_int]
@@ -157,12 +160,13 @@ def msi_abi_version():
     return int(_lib.msi_abi_version())
 
 
-def msi_build(series, n=None, len=None, segments=16, cardinality=256, leaf_capacity=0, flags=0, stream=None):
+def msi_build(series, n=None, len=None, segments=16, cardinality=256, leaf_capacity=0, flags=0, stream=None,
+              query_slots=0, slot_capacity=0):
     """msi_build: `series` is float32 [n, len] (numpy host array or torch tensor, host
     or device). Returns an Index."""
     n = series.shape[0] if n is None else n
     len_ = series.shape[1] if len is None else len
-    opts = _BuildOpts(leaf_capacity, flags, _stream(stream))
+    opts = _BuildOpts(leaf_capacity, flags, _stream(stream), query_slots, slot_capacity)
     out = ctypes.c_void_p()
     _check(_lib.msi_build(_ptr(series, np.float32), n, len_, segments, cardinality, ctypes.byref(opts),
                           ctypes.byref(out)))
@@ -185,6 +189,26 @@ def msi_knn(index, queries, k, ids=None, dists=None, stream=None, nq=None):
     _check(_lib.msi_knn(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, _ptr(ids, np.int64),
                         _ptr(dists, np.float32), _stream(stream)))
     return ids, dists
+
+
+def msi_knn_ex(index, queries, k, stream=None):
+    """msi_knn_ex: (ids int64 [nq, k], dists float32 [nq, k], sqdists64 float64 [nq, k]),
+    outputs allocated like the queries (numpy for host input, torch on its device)."""
+    nq = queries.shape[0]
+    if _is_torch(queries):
+        import torch
+        ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        d64 = torch.empty((nq, k), dtype=torch.float64, device=queries.device)
+        d64p = ctypes.c_void_p(d64.data_ptr())
+    else:
+        ids = np.empty((nq, k), dtype=np.int64)
+        dists = np.empty((nq, k), dtype=np.float32)
+        d64 = np.empty((nq, k), dtype=np.float64)
+        d64p = ctypes.c_void_p(d64.ctypes.data)
+    _check(_lib.msi_knn_ex(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, _ptr(ids, np.int64),
+                           _ptr(dists, np.float32), d64p, _stream(stream)))
+    return ids, dists, d64
 
 
 def msi_free(index):

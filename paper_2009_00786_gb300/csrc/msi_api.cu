@@ -102,11 +102,16 @@ void free_index(msi_index* ix) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != ix->device) cudaSetDevice(ix->device);
-  void* ptrs[] = {ix->data_owned, ix->words, ix->perm, ix->stats, ix->leaf_begin, ix->env, ix->benv, ix->leaf_key,
-                  ix->thr_up, ix->thr_lo, ix->qv.qz, ix->qv.T, ix->qv.T5, ix->qv.st, ix->qv.leaf_list, ix->qv.leaf_lb2, ix->qv.items, ix->qv.surv, ix->qv.blks, ix->qv.partials,
-                  ix->qv.cand, ix->qv.rc_d, ix->qv.rc_id, ix->qv.counters, ix->ws_qraw, ix->ws_ids, ix->ws_dists};
+  void* ptrs[] = {ix->data_owned, ix->words,     ix->perm,         ix->stats,   ix->leaf_begin, ix->env,
+                  ix->benv,       ix->leaf_key,  ix->thr_up,       ix->thr_lo,  ix->qv.counters, ix->ws_qraw,
+                  ix->ws_ids,     ix->ws_dists,  ix->ws_ovf,       ix->ws_d64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  msi::free_workspace(ix->qv);
+  for (auto& qv : ix->slots) msi::free_workspace(qv);
+  for (cudaStream_t st : ix->slot_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : ix->slot_events) cudaEventDestroy(ev);
+  if (ix->fork_event) cudaEventDestroy(ix->fork_event);
   for (cudaEvent_t ev : ix->events)
     if (ev) cudaEventDestroy(ev);
   if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
@@ -155,6 +160,10 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
   if (cap < 1 || cap > (1 << 24)) return fail(MSI_EINVAL, "leaf_capacity = %d outside [1, 2^24]", cap);
   const uint32_t flags = opts ? opts->flags : 0u;
   if (flags & ~MSI_BUILD_BORROW) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
+  const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : 8;
+  if (slots < 1 || slots > 64) return fail(MSI_EINVAL, "query_slots = %d outside [1, 64]", slots);
+  const int32_t slot_cap = opts ? opts->slot_capacity : 0;
+  if (slot_cap < 0) return fail(MSI_EINVAL, "slot_capacity = %d is negative", slot_cap);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
@@ -178,6 +187,8 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
   ix->seglen = len / segments;
   ix->cap = cap;
   ix->flags = flags;
+  ix->nslots = slots;
+  ix->slot_cap = slot_cap;
   region_edges(cardinality, ix->h_thr_up, ix->h_thr_lo);
 
   cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -234,6 +245,11 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
 
 msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
                    void* stream) {
+  return msi_knn_ex(ix, queries, nq, k, ids, dists, nullptr, stream);
+}
+
+msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
+                      double* sqdists64, void* stream) {
   g_err.clear();
   if (!ix) return fail(MSI_EINVAL, "index is NULL");
   if (nq < 0) return fail(MSI_EINVAL, "nq = %lld is negative", (long long)nq);
@@ -242,11 +258,12 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
   if (nq == 0) return MSI_OK;
   if (!queries || !ids) return fail(MSI_EINVAL, "queries or ids is NULL");
   DeviceGuard guard(ix->device);
-  bool o1 = false, o2 = false, o3 = false;
+  bool o1 = false, o2 = false, o3 = false, o4 = false;
   const bool q_dev = is_device_ptr(queries, ix->device, &o1);
   const bool ids_dev = is_device_ptr(ids, ix->device, &o2);
   const bool d_dev = dists ? is_device_ptr(dists, ix->device, &o3) : true;
-  if (o1 || o2 || o3) return fail(MSI_EINVAL, "an argument lives on another device than the index");
+  const bool d64_dev = sqdists64 ? is_device_ptr(sqdists64, ix->device, &o4) : true;
+  if (o1 || o2 || o3 || o4) return fail(MSI_EINVAL, "an argument lives on another device than the index");
   cudaError_t e = msi::query_setup(ix);
   if (e != cudaSuccess) return cuda_fail(e, "allocating the query workspace");
   cudaStream_t s = stream ? (cudaStream_t)stream : ix->own_stream;
@@ -261,7 +278,10 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
       ix->events.push_back(a);
     }
   }
-  const bool host_out = !ids_dev || !d_dev;
+  const bool host_out = !ids_dev || !d_dev || !d64_dev;
+  // several queries of at most 32 neighbours run concurrently on the query slots
+  const bool batched = nq > 1 && k <= 32 && ix->nslots > 1 && !ix->timing;
+  if (batched && (e = msi::slots_setup(ix)) != cudaSuccess) return cuda_fail(e, "allocating query slots");
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t cnt = std::min<int64_t>(chunk, nq - c0);
     const float* qd = queries + c0 * ix->len;
@@ -273,6 +293,13 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
     }
     int64_t* id_base = ids_dev ? ids + c0 * k : ix->ws_ids;
     float* d_base = dists ? (d_dev ? dists + c0 * k : ix->ws_dists) : nullptr;
+    double* d64_base = sqdists64 ? (d64_dev ? sqdists64 + c0 * k : ix->ws_d64) : nullptr;
+    if (batched) {
+      if ((e = cudaEventRecord(ix->fork_event, s)) != cudaSuccess) return cuda_fail(e, "forking query streams");
+      for (int sl = 0; sl < ix->nslots; ++sl)
+        if ((e = cudaStreamWaitEvent(ix->slot_streams[sl], ix->fork_event, 0)) != cudaSuccess)
+          return cuda_fail(e, "forking query streams");
+    }
     for (int64_t i = 0; i < cnt; ++i) {
       cudaEvent_t ea = nullptr, em = nullptr, eb = nullptr;
       if (ix->timing) {
@@ -280,9 +307,37 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
         em = ix->events[3 * i + 1];
         eb = ix->events[3 * i + 2];
       }
-      e = msi::query_one(ix, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr, s, ea, em,
-                         eb);
+      if (batched) {
+        const int sl = (int)(i % ix->nslots);
+        e = msi::query_one(ix, ix->slots[sl], ix->nslots, qd + i * ix->len, k, id_base + i * k,
+                           d_base ? d_base + i * k : nullptr, d64_base ? d64_base + i * k : nullptr, ix->ws_ovf + i,
+                           ix->slot_streams[sl], ea, em, eb);
+      } else {
+        e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
+                           d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
+    }
+    if (batched) {
+      // join the slot streams back into the caller's stream, then run any query
+      // that overflowed a slot's bounded lists again on slot 0
+      for (int sl = 0; sl < ix->nslots; ++sl) {
+        if ((e = cudaEventRecord(ix->slot_events[sl], ix->slot_streams[sl])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ix->slot_events[sl], 0)) != cudaSuccess)
+          return cuda_fail(e, "joining query streams");
+      }
+      std::vector<uint32_t> ovf(cnt);
+      if ((e = cudaMemcpyAsync(ovf.data(), ix->ws_ovf, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost, s)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "query execution");
+      for (int64_t i = 0; i < cnt; ++i) {
+        if (!ovf[i]) continue;
+        e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
+                           d64_base ? d64_base + i * k : nullptr, nullptr, s, nullptr, nullptr, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
+        ++ix->overflow_reruns;
+      }
     }
     if (!ids_dev &&
         (e = cudaMemcpyAsync(ids + c0 * k, ix->ws_ids, sizeof(int64_t) * cnt * k, cudaMemcpyDeviceToHost, s)) !=
@@ -290,6 +345,10 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
       return cuda_fail(e, "copying ids to the host");
     if (dists && !d_dev &&
         (e = cudaMemcpyAsync(dists + c0 * k, ix->ws_dists, sizeof(float) * cnt * k, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+      return cuda_fail(e, "copying distances to the host");
+    if (sqdists64 && !d64_dev &&
+        (e = cudaMemcpyAsync(sqdists64 + c0 * k, ix->ws_d64, sizeof(double) * cnt * k, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)
       return cuda_fail(e, "copying distances to the host");
     if (host_out || ix->timing || c0 + chunk < nq) {

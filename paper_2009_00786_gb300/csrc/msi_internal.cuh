@@ -49,6 +49,7 @@ struct QState {
   unsigned int next_item;       // (unused)
   unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int blk_count;       // leaf blocks whose envelope bound passed
+  unsigned int overflow;        // a candidate or survivor list ran out of room
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -82,6 +83,9 @@ struct QueryView {
   uint32_t* partials;           // [kMaxRefineWarps][3]: per-warp work counters of the refinement
   uint32_t npartials;           // warps of the series filter (or block refinement) launch
   uint32_t npartials_rows;      // warps of the row refinement launch
+  uint32_t cand_cap;            // entries of cand / rc_d / rc_id
+  uint32_t surv_cap;            // entries of surv
+  uint32_t* ovf;                // per-query overflow flag written by q_finalize (or nullptr)
   int k;
   float eps;                    // relative margin on squared distances
   float tau;                    // absolute margin on lower bounds (distance units)
@@ -254,12 +258,23 @@ struct msi_index {
   float h_thr_lo[257];
   int64_t device_bytes = 0;
   cudaStream_t own_stream = nullptr;
-  // query workspace (allocated on first use)
+  // query workspace (allocated on first use): slot 0 has room for any query; the
+  // slots used to run several queries at once have bounded candidate / survivor
+  // lists, and a query that overflows them is run again on slot 0
   bool ws_ready = false;
   msi::QueryView qv{};
+  std::vector<msi::QueryView> slots;
+  std::vector<cudaStream_t> slot_streams;
+  std::vector<cudaEvent_t> slot_events;
+  cudaEvent_t fork_event = nullptr;
+  uint32_t* ws_ovf = nullptr;   // [kQueryChunk]
+  int nslots = 8;
+  int slot_cap = 0;
+  int64_t overflow_reruns = 0;
   float* ws_qraw = nullptr;     // staging for host queries [kQueryChunk][len]
   int64_t* ws_ids = nullptr;    // staging for host outputs [kQueryChunk][MSI_MAX_K]
   float* ws_dists = nullptr;
+  double* ws_d64 = nullptr;
   int refine_grid = 0;
   int rows_grid = 0;
   int blocks_grid = 0;
@@ -304,8 +319,11 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
 
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
-cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
-                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b);
+cudaError_t slots_setup(msi_index* ix);
+void free_workspace(QueryView& qv);
+cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
+                      float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
+                      cudaEvent_t ev_m, cudaEvent_t ev_b);
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);

@@ -254,6 +254,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->next_item = 0;
     st->surv_count = 0;
     st->blk_count = 0;
+    st->overflow = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -280,7 +281,10 @@ q_seed(IndexView ix, QueryView qv) {
     const uint32_t id = ix.perm[pos];
     const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
     const float d2 = warp_sqdist(ix, id, ms, qs);
-    if ((threadIdx.x & 31) == 0) qv.cand[gw] = pack(d2, pos);
+    if ((threadIdx.x & 31) == 0) {
+      if (gw < qv.cand_cap) qv.cand[gw] = pack(d2, pos);
+      else qv.st->overflow = 1u;
+    }
     best = min(best, __float_as_uint(d2));
   }
   // k = 1: one atomicMin per block, on the block's smallest distance
@@ -293,7 +297,7 @@ q_seed(IndexView ix, QueryView qv) {
 __global__ void __launch_bounds__(1024)
 q_seed_select(QueryView qv) {
   __shared__ uint32_t hist[256], sel[2];
-  const uint32_t count = qv.st->cand_count;
+  const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
   const unsigned long long* c = qv.cand;
   const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
                                         (uint32_t)qv.k, hist, sel);
@@ -431,7 +435,11 @@ q_refine(IndexView ix, QueryView qv) {
         if (lane == 0) {
           ++n_ref;
           const unsigned thr = *thr_v;
-          if (d2 <= keep_bound2(thr, qv.eps)) qv.cand[atomicAdd(&st->cand_count, 1u)] = pack(d2, p);
+          if (d2 <= keep_bound2(thr, qv.eps)) {
+            const uint32_t slot = atomicAdd(&st->cand_count, 1u);
+            if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, p);
+            else st->overflow = 1u;
+          }
           if (KONE) atomicMin(&st->thr_bits, __float_as_uint(d2));
           else sd2[i] = d2;
         }
@@ -605,7 +613,9 @@ q_filter_series(IndexView ix, QueryView qv) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&st->surv_count, 32u);
         base = __shfl_sync(kFull, base, 0);
-        qv.surv[base + lane] = buf[lane];
+        // entry by entry, so every entry below the capacity is written
+        if (base + lane < qv.surv_cap) qv.surv[base + lane] = buf[lane];
+        else st->overflow = 1u;
         __syncwarp();
         if (lane < (int)nbuf - 32) buf[lane] = buf[32 + lane];
         nbuf -= 32;
@@ -618,7 +628,10 @@ q_filter_series(IndexView ix, QueryView qv) {
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&st->surv_count, nbuf);
     base = __shfl_sync(kFull, base, 0);
-    if (lane < (int)nbuf) qv.surv[base + lane] = buf[lane];
+    if (lane < (int)nbuf) {
+      if (base + lane < qv.surv_cap) qv.surv[base + lane] = buf[lane];
+      else st->overflow = 1u;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_lb += __shfl_xor_sync(kFull, n_lb, o);
@@ -637,7 +650,8 @@ q_refine_rows(IndexView ix, QueryView qv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   QState* st = qv.st;
   volatile unsigned int* thr_v = &st->thr_bits;
-  const uint32_t nsurv = st->surv_count;
+  // a query whose lists overflowed is run again with room for all n: skip it here
+  const uint32_t nsurv = st->overflow ? 0u : min(st->surv_count, qv.surv_cap);
   const int k = qv.k;
   const unsigned lt = (1u << lane) - 1u;
   unsigned mine = 0x7f800000u;
@@ -727,7 +741,11 @@ q_refine_rows(IndexView ix, QueryView qv) {
       uint32_t base = 0;
       if (lane == leader) base = atomicAdd(&st->cand_count, (uint32_t)__popc(km));
       base = __shfl_sync(kFull, base, leader);
-      if (keep) qv.cand[base + __popc(km & lt)] = pack(d2, myp);
+      const uint32_t slot = base + __popc(km & lt);
+      if (keep) {
+        if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, myp);
+        else st->overflow = 1u;
+      }
     }
     if (KONE) {
       if (mine_live && __float_as_uint(d2) < thr2) atomicMin(&st->thr_bits, __float_as_uint(d2));
@@ -752,7 +770,7 @@ q_refine_rows(IndexView ix, QueryView qv) {
 // The k-th smallest candidate squared distance T; candidates at or below
 // T (1 + eps) are re-checked in FP64 (one block).
 __device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel) {
-  const uint32_t count = qv.st->cand_count;
+  const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
   const unsigned long long* c = qv.cand;
   const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
                                         (uint32_t)qv.k, hist, sel);
@@ -767,7 +785,7 @@ __device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel)
 // bound and list the passing ones in shared memory (`list`, 4 * blockDim entries);
 // then one warp per listed candidate computes its FP64 distance.
 __device__ void recheck(const IndexView& ix, const QueryView& qv, uint32_t* list, uint32_t* s_n) {
-  const uint32_t count = qv.st->cand_count;
+  const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
   const uint32_t bound = qv.st->final_bits;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = blockDim.x / 32;
@@ -831,10 +849,13 @@ constexpr int kSortCap = 2048;  // (distance, id) pairs sorted in shared memory
 // re-check of every candidate within the fp32 margin of it, and the k smallest by
 // (FP64 distance, id), written to the outputs.
 __global__ void __launch_bounds__(1024)
-q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out) {
+q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out,
+           double* __restrict__ d64_out) {
   __shared__ unsigned long long sk[kSortCap];
   __shared__ uint32_t si[kSortCap];
   __shared__ uint32_t hist[256], sel[2], s_cnt;
+  if (threadIdx.x == 0 && qv.ovf) *qv.ovf = qv.st->overflow;
+  if (qv.st->overflow) return;  // the query is run again with room for all n
   final_select(qv, hist, sel);
   __syncthreads();
   static_assert(sizeof(sk) >= 4 * 1024 * sizeof(uint32_t), "re-check list must hold 4 * blockDim entries");
@@ -918,6 +939,7 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
   for (int r = threadIdx.x; r < k; r += blockDim.x) {
     ids_out[r] = (int64_t)si[r];
     if (dists_out) dists_out[r] = __double2float_rn(__dsqrt_rn(__longlong_as_double((long long)sk[r])));
+    if (d64_out) d64_out[r] = __longlong_as_double((long long)sk[r]);
   }
   // sum the refinement's per-warp work counters
   __shared__ unsigned long long s_part[3];
@@ -999,37 +1021,98 @@ cudaError_t dalloc(T** p, size_t count) {
 
 }  // namespace
 
-// Allocates the query workspace of an index (once).
+// One query workspace with room for cand_cap candidates and surv_cap survivors
+// (work items, block lists and leaf lists always have room for any query).
+static cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
+                                   int64_t* bytes) {
+  cudaError_t e;
+  const size_t items = (size_t)(ix->n / kItem + 2 * ix->L + 2);
+  if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.T5, (size_t)ix->w * 32)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.items, items)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * items)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.partials, (size_t)3 * kMaxRefineWarps)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.cand, (size_t)cand_cap)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.rc_d, (size_t)cand_cap)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.rc_id, (size_t)cand_cap)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.surv, (size_t)surv_cap)) != cudaSuccess) return e;
+  qv.cand_cap = cand_cap;
+  qv.surv_cap = surv_cap;
+  qv.ovf = nullptr;
+  qv.eps = 1.52587890625e-05f;  // 2^-16
+  qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
+  *bytes += (int64_t)(ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
+            (int64_t)items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 +
+            (int64_t)surv_cap * 8;
+  return cudaSuccess;
+}
+
+void free_workspace(QueryView& qv) {
+  void* ptrs[] = {qv.qz, qv.T, qv.T5, qv.st, qv.leaf_list, qv.leaf_lb2, qv.items, qv.blks, qv.partials,
+                  qv.cand, qv.rc_d, qv.rc_id, qv.surv};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  qv = QueryView{};
+}
+
+// Allocates slot 0 of the query workspace (room for any query) once.
 cudaError_t query_setup(msi_index* ix) {
   if (ix->ws_ready) return cudaSuccess;
   QueryView& qv = ix->qv;
   cudaError_t e;
-  if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.items, (size_t)(ix->n / kItem + 2 * ix->L + 2))) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.T5, (size_t)ix->w * 32)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.partials, (size_t)3 * kMaxRefineWarps)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.cand, (size_t)ix->n)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.rc_d, (size_t)ix->n)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.rc_id, (size_t)ix->n)) != cudaSuccess) return e;
+  const uint32_t nn = (uint32_t)ix->n;
+  if ((e = alloc_workspace(ix, qv, nn, nn, &ix->device_bytes)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.counters, (size_t)ST_COUNT)) != cudaSuccess) return e;
   if ((e = cudaMemset(qv.counters, 0, sizeof(unsigned long long) * ST_COUNT)) != cudaSuccess) return e;
   if ((e = dalloc(&ix->ws_qraw, (size_t)kQueryChunk * ix->len)) != cudaSuccess) return e;
   if ((e = dalloc(&ix->ws_ids, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
   if ((e = dalloc(&ix->ws_dists, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
-  ix->device_bytes += (int64_t)ix->n * 20 + ix->L * 8 + (int64_t)kQueryChunk * (ix->len * 4 + MSI_MAX_K * 12);
+  if ((e = dalloc(&ix->ws_d64, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
+  if ((e = dalloc(&ix->ws_ovf, (size_t)kQueryChunk)) != cudaSuccess) return e;
+  ix->device_bytes += (int64_t)kQueryChunk * (ix->len * 4 + MSI_MAX_K * 20 + 4);
   const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
   if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.surv, (size_t)ix->n)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * (ix->n / kItem + 2 * ix->L + 2))) != cudaSuccess) return e;
-  ix->device_bytes += (int64_t)ix->n * 8;
-  qv.eps = 1.52587890625e-05f;  // 2^-16
-  qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
   ix->ws_ready = true;
+  return cudaSuccess;
+}
+
+// Allocates the concurrent query slots (bounded lists), their streams and events.
+cudaError_t slots_setup(msi_index* ix) {
+  if ((int)ix->slots.size() == ix->nslots) return cudaSuccess;
+  cudaError_t e;
+  if (!ix->fork_event && (e = cudaEventCreateWithFlags(&ix->fork_event, cudaEventDisableTiming)) != cudaSuccess) return e;
+  // the seed needs max(leaf capacity, k) candidate entries
+  const int64_t seed_room = std::min<int64_t>(ix->n, (int64_t)ix->cap + MSI_MAX_K);
+  const uint32_t cand_cap = (uint32_t)std::min<int64_t>(
+      ix->n, std::max<int64_t>(seed_room, ix->slot_cap ? ix->slot_cap : std::max<int64_t>(65536, seed_room)));
+  const uint32_t surv_cap = (uint32_t)std::min<int64_t>(ix->n, ix->slot_cap ? ix->slot_cap : 1 << 20);
+  while ((int)ix->slots.size() < ix->nslots) {
+    QueryView qv{};
+    if ((e = alloc_workspace(ix, qv, cand_cap, surv_cap, &ix->device_bytes)) != cudaSuccess) {
+      free_workspace(qv);
+      return e;
+    }
+    qv.counters = ix->qv.counters;
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+      free_workspace(qv);
+      return e;
+    }
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+      cudaStreamDestroy(st);
+      free_workspace(qv);
+      return e;
+    }
+    ix->slots.push_back(qv);
+    ix->slot_streams.push_back(st);
+    ix->slot_events.push_back(ev);
+  }
   return cudaSuccess;
 }
 
@@ -1066,37 +1149,43 @@ static cudaError_t refine_config(msi_index* ix, int k) {
 
 // One query (device pointers), stream-ordered. ev_a / ev_m / ev_b, when given,
 // bracket the series filter and the row refinement.
-cudaError_t query_one(msi_index* ix, const float* q_dev, int k, int64_t* ids_dev, float* dists_dev,
-                      cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b) {
+cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
+                      float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
+                      cudaEvent_t ev_m, cudaEvent_t ev_b) {
   cudaError_t e = refine_config(ix, k);
   if (e != cudaSuccess) return e;
-  QueryView qv = ix->qv;
+  QueryView qv = ws;
   qv.k = k;
-  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)ix->refine_grid * (k <= 32 ? kFiltWarps : kThreads / 32),
+  qv.ovf = ovf;
+  share = std::max(1, share);
+  const int refine_grid = std::max(1, ix->refine_grid / share);
+  const int rows_grid = std::max(1, ix->rows_grid / share);
+  const int blocks_grid = std::max(1, ix->blocks_grid / share);
+  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)refine_grid * (k <= 32 ? kFiltWarps : kThreads / 32),
                                              kMaxRefineWarps);
-  qv.npartials_rows = k <= 32 ? (uint32_t)std::min<int64_t>((int64_t)ix->rows_grid * kRowWarps, kMaxRefineWarps)
+  qv.npartials_rows = k <= 32 ? (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps)
                               : qv.npartials;
   const IndexView v = ix->view();
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);
-  q_seed<<<(unsigned)((seed_max + 7) / 8), kThreads, qbytes, s>>>(v, qv);
+  q_seed<<<(unsigned)std::min<int64_t>((seed_max + 7) / 8, 1024), kThreads, qbytes, s>>>(v, qv);
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
   q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   if (k <= 32) {
-    q_filter_blocks<<<ix->blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
-    q_filter_series<<<ix->refine_grid, kFiltWarps * 32, ix->refine_smem, s>>>(v, qv);
+    q_filter_blocks<<<blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
+    q_filter_series<<<refine_grid, kFiltWarps * 32, ix->refine_smem, s>>>(v, qv);
     if (ev_m) cudaEventRecord(ev_m, s);
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
-    if (k == 1) q_refine_rows<true><<<ix->rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
-    else q_refine_rows<false><<<ix->rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
+    if (k == 1) q_refine_rows<true><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
+    else q_refine_rows<false><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
   } else {
-    q_refine<false><<<ix->refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
+    q_refine<false><<<refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
     if (ev_m) cudaEventRecord(ev_m, s);
   }
   if (ev_b) cudaEventRecord(ev_b, s);
-  q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev);
+  q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev, d64_dev);
   return cudaGetLastError();
 }
 

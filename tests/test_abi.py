@@ -44,7 +44,7 @@ def test_status_strings_and_version(msi):
 
 def _raw_build(msi, series, n, length, segs, card, cap=0, flags=0):
     lib = msi._lib
-    opts = msi._BuildOpts(cap, flags, None)
+    opts = msi._BuildOpts(cap, flags, None, 0, 0)
     out = ctypes.c_void_p(123)
     p = ctypes.c_void_p(series.ctypes.data) if series is not None else None
     st = lib.msi_build(p, n, length, segs, card, ctypes.byref(opts), ctypes.byref(out))

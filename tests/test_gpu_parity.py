@@ -221,3 +221,24 @@ def test_stats_counters(msi):
     assert st["candidates"] >= 6 * 5 and st["rechecked"] >= 6 * 5
     assert st["refine_launches"] == 6 and st["refine_ms"] > 0
     assert st["series_lower_bounded"] < 6 * 8000  # leaves were pruned
+
+
+def test_batched_slots_match_single_queries_and_oracle(msi):
+    """Queries run concurrently on the query slots give, for each query, the answer it
+    gets alone, which is the oracle's; a slot whose bounded lists overflow (many
+    exact ties) hands its query back to the full-capacity workspace."""
+    n, length = 6000, 256
+    X = datagen.walks(201, 0, n, length)
+    X[1000:3500] = X[999]  # 2501 identical series: every one is a tie at distance 0
+    Z = oracle.summarise(X, 16, 256)[0]
+    Q = np.concatenate([datagen.paper_queries(n, length, count=7, data_seed=201), X[[999, 3000]]])
+    for k in (1, 5, 32):
+        batched = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=3, slot_capacity=1024)
+        single = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=1)
+        ids_b, d_b = msi.msi_knn(batched, Q, k)
+        for i, q in enumerate(Q):
+            ids_s, d_s = msi.msi_knn(single, Q[i:i + 1], k)
+            assert np.array_equal(ids_b[i], ids_s[0]) and np.array_equal(d_b[i], d_s[0])
+            oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
+            assert np.array_equal(ids_b[i], oid), (k, i)
+        assert ids_b[-2][0] == 999 and list(ids_b[-1][:min(k, 3)]) == [999, 1000, 1001][:min(k, 3)]

@@ -1,0 +1,73 @@
+"""The multi-rank path on the CPU: two gloo ranks each answer the queries over their
+half of the collection (with the oracle, as a GPU rank answers with its index) and
+merge through paper_2009_00786_gb300.shard; the merged answer must equal the oracle's
+answer over the whole collection, ties included."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+N, LEN, K = 3000, 128, 7
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out_path):
+    import torch.distributed as dist
+
+    from paper_2009_00786_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    X = datagen.walks(61, 0, N, LEN)
+    X[2500] = X[10]  # a tie across the two shards
+    per = N // world
+    first = rank * per
+    Z = oracle.summarise(X[first:first + per], 16, 256)[0]
+    Q = np.concatenate([datagen.paper_queries(N, LEN, count=6, data_seed=61), X[[10]]])
+    ids, d2 = [], []
+    for q in Q:
+        i, d = oracle.knn_scan(Z, oracle.znorm(q)[0], K)
+        ids.append(i + first)
+        d2.append(d)
+    mi, md = shard.gather_merge(np.array(ids), np.array(d2), K)
+    if rank == 0:
+        np.savez(out_path, ids=mi, d2=md)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_merge_to_the_whole_answer(tmp_path):
+    try:
+        import __graft_entry__
+        __graft_entry__.build()
+    except Exception as e:  # the package needs its library only to import
+        pytest.skip(f"library build unavailable: {e}")
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "merged.npz")
+    mp.start_processes(_rank, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    got = np.load(out)
+    X = datagen.walks(61, 0, N, LEN)
+    X[2500] = X[10]
+    Z = oracle.summarise(X, 16, 256)[0]
+    Q = np.concatenate([datagen.paper_queries(N, LEN, count=6, data_seed=61), X[[10]]])
+    for i, q in enumerate(Q):
+        oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], K)
+        assert np.array_equal(got["ids"][i], oid)
+        assert np.array_equal(got["d2"][i], od2)
+    assert list(got["ids"][-1][:2]) == [10, 2500]
+
+
+def test_merge_orders_by_distance_then_id():
+    from paper_2009_00786_gb300.shard import merge_topk
+    a_ids, a_d = np.array([[5, 9]]), np.array([[1.0, 2.0]])
+    b_ids, b_d = np.array([[3, 7]]), np.array([[1.0, 1.5]])
+    mi, md = merge_topk([a_ids, b_ids], [a_d, b_d], 3)
+    assert list(mi[0]) == [3, 5, 7] and list(md[0]) == [1.0, 1.0, 1.5]

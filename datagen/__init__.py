@@ -35,6 +35,8 @@ def _load_host():
         lib.dg_ln_host.restype = ctypes.c_float
         lib.dg_sincos_2pi_host.argtypes = [ctypes.c_float, vp, vp]
         lib.dg_normals_host.argtypes = [c_u64, ctypes.c_uint32, c_u64, c_i32, vp]
+        lib.dg_mixed_host.argtypes = [c_u64, c_i64, c_i64, c_i32, vp]
+        lib.dg_mixed_noisy_host.argtypes = [c_u64, c_u64, vp, ctypes.c_float, c_i64, c_i32, vp]
         _host = lib
     return _host
 
@@ -75,6 +77,23 @@ def noisy_copies(data_seed, noise_seed, ids, sigmas, length):
     out = np.empty((len(ids), length), dtype=np.float32)
     if len(ids):
         _load_host().dg_noisy_copies_host(data_seed, noise_seed, _ptr(ids), _ptr(sigmas), len(ids), length, _ptr(out))
+    return out
+
+
+def mixed(seed, first_id, count, length):
+    """Mixed-shape series (noisy sinusoids and Laplace-step walks with a spike burst)
+    first_id .. first_id+count-1 of collection `seed`: float32 [count, length]."""
+    out = np.empty((count, length), dtype=np.float32)
+    if count:
+        _load_host().dg_mixed_host(seed, first_id, count, length, _ptr(out))
+    return out
+
+
+def mixed_noisy(data_seed, noise_seed, ids, sigma, length):
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    out = np.empty((len(ids), length), dtype=np.float32)
+    if len(ids):
+        _load_host().dg_mixed_noisy_host(data_seed, noise_seed, _ptr(ids), float(sigma), len(ids), length, _ptr(out))
     return out
 
 
@@ -149,3 +168,9 @@ def paper_queries(n_collection, length=256, count=100, data_seed=0, fresh_seed=1
     fresh = walks(fresh_seed, 0, n_fresh, length)
     copies = noisy_copies(data_seed, pick_seed, ids, sigmas, length)
     return np.concatenate([fresh, copies], axis=0)
+
+
+def mixed_queries(count=100, length=256, query_seed=5, noise_seed=6, sigma=0.31622777):
+    """Query set of the mixed-shape workload: fresh draws from the same generator
+    (collection `query_seed`) plus N(0, 0.1) noise (sigma = sqrt 0.1)."""
+    return mixed_noisy(query_seed, noise_seed, np.arange(count), sigma, length)

@@ -198,6 +198,60 @@ DG_FN void dg_random_walk_one(uint64_t seed, uint64_t id, int len, float* out) {
   }
 }
 
+/* Laplace(0, b) draw from 32 random bits by inversion: u in (-1/2, 1/2),
+ * e = -b sign(u) ln(1 - 2|u|). */
+DG_FN float dg_laplace(uint32_t bits, float b) {
+  const float u = DG_SUB(dg_u01_open0(bits), 0.5f);  /* (-0.5, 0.5] */
+  const float a = u < 0.0f ? -u : u;
+  float one_m = DG_SUB(1.0f, DG_MUL(2.0f, a));
+  if (one_m < 5.9604644775390625e-08f) one_m = 5.9604644775390625e-08f;
+  const float mag = DG_MUL(-b, dg_ln(one_m));
+  return u < 0.0f ? -mag : mag;
+}
+
+/* Mixed-shape collection: series `id` of collection `seed` is, with probability 1/2
+ * each (stream SHAPE), either
+ *  - a noisy sinusoid sin(2 pi (f t / len + phi)) + N(0, 0.3), f ~ U[1, 32) cycles,
+ *    phi ~ U[0, 1) of a period; or
+ *  - a random walk with Laplace(0, 1/sqrt 2) (unit-variance) steps, the steps of one
+ *    burst of ceil(len / 20) consecutive points (5% of the series, at a uniform
+ *    offset) multiplied by 10. */
+DG_FN void dg_mixed_one(uint64_t seed, uint64_t id, int len, float* out) {
+  dg_u32x4 sh = dg_bits(seed, DG_STREAM_SHAPE, id, 0);
+  float e[4];
+  if ((sh.v[0] >> 31) == 0u) {
+    const float f = DG_ADD(1.0f, DG_MUL(31.0f, dg_u01(sh.v[1])));
+    const float phi = dg_u01(sh.v[2]);
+    const float inv_len = DG_DIV(1.0f, (float)len);
+    for (int t = 0; t < len; ++t) {
+      if ((t & 3) == 0) dg_normal4(seed, DG_STREAM_WALK, id, (uint32_t)(t >> 2), e);
+      const float a = DG_ADD(DG_MUL(DG_MUL(f, (float)t), inv_len), phi);
+      const float frac = DG_SUB(a, (float)(int)a);
+      float sv, cv;
+      dg_sincos_2pi(frac, &sv, &cv);
+      out[t] = DG_ADD(sv, DG_MUL(0.547722558f, e[t & 3])); /* sqrt(0.3) */
+    }
+  } else {
+    const int burst = (len + 19) / 20;
+    const int start = (int)(((uint64_t)sh.v[3] * (uint64_t)(len - burst + 1)) >> 32);
+    float x = 0.0f;
+    for (int t = 0; t < len; ++t) {
+      dg_u32x4 r;
+      if ((t & 3) == 0) {
+        r = dg_bits(seed, DG_STREAM_WALK, id, (uint32_t)(t >> 2));
+        e[0] = dg_laplace(r.v[0], 0.707106769f);
+        e[1] = dg_laplace(r.v[1], 0.707106769f);
+        e[2] = dg_laplace(r.v[2], 0.707106769f);
+        e[3] = dg_laplace(r.v[3], 0.707106769f);
+      }
+      float step = e[t & 3];
+      if (t >= start && t < start + burst) step = DG_MUL(step, 10.0f);
+      x = (t == 0) ? step : DG_ADD(x, step);
+      out[t] = x;
+    }
+  }
+}
+
 /* Uniform integer in [0, n) for draw number `i` of stream PICK (multiply-shift on
  * 64 random bits; bias below 2^-30 for n < 2^34). */
 DG_FN uint64_t dg_pick(uint64_t seed, uint64_t i, uint64_t n) {

@@ -55,3 +55,26 @@ void dg_normals_host(uint64_t seed, uint32_t stream, uint64_t id, int32_t count,
     out[t] = e[t & 3];
   }
 }
+
+/* Mixed-shape series first_id .. first_id+count-1 of collection `seed`. */
+void dg_mixed_host(uint64_t seed, int64_t first_id, int64_t count, int32_t len, float* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < count; ++i)
+    dg_mixed_one(seed, (uint64_t)(first_id + i), len, out + i * (int64_t)len);
+}
+
+/* Members of a mixed collection plus N(0, sigma^2) noise (stream NOISE of noise_seed,
+ * keyed by i). */
+void dg_mixed_noisy_host(uint64_t data_seed, uint64_t noise_seed, const int64_t* ids, float sigma, int64_t count,
+                         int32_t len, float* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < count; ++i) {
+    float* row = out + i * (int64_t)len;
+    dg_mixed_one(data_seed, (uint64_t)ids[i], len, row);
+    float e[4];
+    for (int t = 0; t < len; ++t) {
+      if ((t & 3) == 0) dg_normal4(noise_seed, DG_STREAM_NOISE, (uint64_t)i, (uint32_t)(t >> 2), e);
+      row[t] = DG_ADD(row[t], DG_MUL(sigma, e[t & 3]));
+    }
+  }
+}

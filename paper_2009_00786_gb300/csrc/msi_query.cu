@@ -550,7 +550,11 @@ q_filter_blocks(IndexView ix, QueryView qv) {
             acc = __fadd_rn(acc, Ts[j * ix.card + min(max(qsym_s[j], sl), sh)]);
           }
         }
-        if (__fmul_rn(acc, seglen) <= bound2) s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, t / kBlocksPerItem);
+        if (__fmul_rn(acc, seglen) <= bound2) {
+          // task: block index, and the block's positions inside the item: [lo, hi) offsets
+          const uint32_t lo_off = max(item.x, blk * 32) - blk * 32, hi_off = min(item.y, blk * 32 + 32) - blk * 32;
+          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, lo_off | (hi_off << 8));
+        }
       }
     }
     __syncthreads();
@@ -562,66 +566,113 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 }
 
 // One warp per surviving block: bounds every position by its SAX word and buffers
-// the survivors {position, bound}, flushed 32 at a time. kUnroll blocks in flight.
+// the survivors {position, bound}, flushed 32 at a time. kUnroll blocks are in flight
+// per warp. Each word is first bounded from its 5-bit symbol prefixes (T5: 32 entries
+// per segment, so the lookups of a warp never conflict); the words that pass are
+// queued per warp and bounded from their full symbols (T) a whole warp at a time.
+constexpr int kQueue = 64;
+
+__device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int w, int cshift, float s) {
+  const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j < w) acc = __fadd_rn(acc, T5s[j * 32 + (((parts[j >> 2] >> (8 * (j & 3))) & 255) >> cshift)]);
+  return __fmul_rn(acc, s);
+}
+
 __global__ void __launch_bounds__(kFiltWarps * 32)
 q_filter_series(IndexView ix, QueryView qv) {
-  extern __shared__ __align__(16) float Ts[];  // [w][card]
+  extern __shared__ __align__(16) float Ts[];  // [w][card], then T5 [w][32]
+  float* T5s = Ts + ix.w * ix.card;
   __shared__ uint2 buf_s[kFiltWarps][64];
+  __shared__ uint4 qw_s[kFiltWarps][kQueue];
+  __shared__ uint32_t qp_s[kFiltWarps][kQueue];
   for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  for (int e = threadIdx.x; e < ix.w * 32; e += blockDim.x) T5s[e] = qv.T5[e];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
+  uint4* qw = qw_s[warp];
+  uint32_t* qp = qp_s[warp];
   QState* st = qv.st;
   const uint32_t ntask = st->blk_count;
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
+  const int cshift = ix.bits > 5 ? ix.bits - 5 : 0;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
-  uint32_t nbuf = 0, n_lb = 0;
+  uint32_t nbuf = 0, nq = 0, n_lb = 0;
+  float bound2 = 0.0f;
+
+  // full bounds of the first 32 queued words (one per lane); survivors to the buffer
+  auto drain32 = [&](uint32_t count) {
+    const bool have = lane < (int)count;
+    const uint32_t p = have ? qp[lane] : 0u;
+    const float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
+    const bool pass = have && lb2 <= bound2;
+    __syncwarp();
+    if (count > 32 && lane < (int)count - 32) {  // move the rest of the queue down
+      qw[lane] = qw[32 + lane];
+      qp[lane] = qp[32 + lane];
+    }
+    const unsigned m = __ballot_sync(kFull, pass);
+    if (pass) buf[nbuf + __popc(m & lt)] = make_uint2(p, __float_as_uint(lb2));
+    nbuf += __popc(m);
+    __syncwarp();
+    if (nbuf >= 32) {  // flush 32 survivors with one atomic, entry by entry
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&st->surv_count, 32u);
+      base = __shfl_sync(kFull, base, 0);
+      if (base + lane < qv.surv_cap) qv.surv[base + lane] = buf[lane];
+      else st->overflow = 1u;
+      __syncwarp();
+      if (lane < (int)nbuf - 32) buf[lane] = buf[32 + lane];
+      nbuf -= 32;
+      __syncwarp();
+    }
+  };
+
   for (uint32_t t0 = gw; t0 < ntask; t0 += stride * kUnroll) {
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u, 0);
-    const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
+    bound2 = lb_bound2(thr, qv.eps, qv.tau);
     uint2 task[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t t = t0 + u * stride;
-      task[u] = t < ntask ? qv.blks[t] : make_uint2(0, 0xffffffffu);
+      task[u] = t < ntask ? qv.blks[t] : make_uint2(0, 0);  // an empty range when past the end
     }
-    uint4 item[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      item[u] = task[u].y != 0xffffffffu ? qv.items[task[u].y] : make_uint4(0, 0, 0, 0);
     uint4 wd[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t p = task[u].x * 32 + lane;
-      wd[u] = p >= item[u].x && p < item[u].y ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+      const bool in = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8);
+      wd[u] = in ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t p = task[u].x * 32 + lane;
-      const bool valid = p >= item[u].x && p < item[u].y && (p < sa || p >= sb);
+      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
-      const float lb2 = valid ? word_lb2(wd[u], Ts, ix.w, ix.card, seglen) : INFINITY;
-      const bool pass = valid && lb2 <= bound2;
-      const unsigned m = __ballot_sync(kFull, pass);
-      if (pass) buf[nbuf + __popc(m & lt)] = make_uint2(p, __float_as_uint(lb2));
-      nbuf += __popc(m);
-      if (nbuf >= 32) {  // flush 32 survivors with one atomic
-        __syncwarp();
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&st->surv_count, 32u);
-        base = __shfl_sync(kFull, base, 0);
-        // entry by entry, so every entry below the capacity is written
-        if (base + lane < qv.surv_cap) qv.surv[base + lane] = buf[lane];
-        else st->overflow = 1u;
-        __syncwarp();
-        if (lane < (int)nbuf - 32) buf[lane] = buf[32 + lane];
-        nbuf -= 32;
-        __syncwarp();
+      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
+      const unsigned m = __ballot_sync(kFull, pass_c);
+      if (pass_c) {
+        qw[nq + __popc(m & lt)] = wd[u];
+        qp[nq + __popc(m & lt)] = p;
+      }
+      nq += __popc(m);
+      __syncwarp();
+      if (nq >= 32) {
+        drain32(nq);
+        nq -= 32;
       }
     }
+  }
+  while (nq > 0) {
+    const uint32_t c = nq;
+    drain32(c);
+    nq = c > 32 ? c - 32 : 0;
   }
   __syncwarp();
   if (nbuf) {
@@ -1126,7 +1177,9 @@ static cudaError_t refine_config(msi_index* ix, int k) {
   if (e != cudaSuccess) return e;
   if (mode) {
     const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, fsmem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32,
+                                                            fsmem + sizeof(float) * (size_t)ix->w * 32)) != cudaSuccess)
+      return e;
     ix->refine_grid = std::max(1, per_sm) * sms;
     ix->refine_smem = fsmem;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, fsmem)) != cudaSuccess) return e;
@@ -1175,7 +1228,7 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   if (ev_a) cudaEventRecord(ev_a, s);
   if (k <= 32) {
     q_filter_blocks<<<blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
-    q_filter_series<<<refine_grid, kFiltWarps * 32, ix->refine_smem, s>>>(v, qv);
+    q_filter_series<<<refine_grid, kFiltWarps * 32, ix->refine_smem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
     if (ev_m) cudaEventRecord(ev_m, s);
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
     if (k == 1) q_refine_rows<true><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);

@@ -60,3 +60,20 @@ def test_noisy_copies_and_picks():
     assert 0.5 < np.std(q[2] - base[2]) < 2.0
     qs = datagen.paper_queries(12345, 128, count=100)
     assert qs.shape == (100, 128) and qs.dtype == np.float32
+
+
+def test_mixed_shapes():
+    X = datagen.mixed(4, 0, 4000, 256)
+    assert np.isfinite(X).all()
+    sd = X.std(axis=1)
+    sinus = sd < 2.0  # sinusoid + N(0, 0.3): std about sqrt(0.5 + 0.3)
+    assert 0.4 < sinus.mean() < 0.6
+    assert np.all(np.abs(sd[sinus] - np.sqrt(0.8)) < 0.25)
+    walks = X[~sinus]
+    steps = np.abs(np.diff(walks, axis=1))
+    # one burst of 13 steps x10 per walk: the largest steps sit in one run
+    big = steps > 8.0
+    assert big.any(axis=1).mean() > 0.5
+    assert np.array_equal(datagen.mixed(4, 100, 5, 256), X[100:105])
+    Q = datagen.mixed_queries(count=5)
+    assert Q.shape == (5, 256) and 0.2 < np.std(Q - datagen.mixed(5, 0, 5, 256)) < 0.45

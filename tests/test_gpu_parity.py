@@ -242,3 +242,19 @@ def test_batched_slots_match_single_queries_and_oracle(msi):
             oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
             assert np.array_equal(ids_b[i], oid), (k, i)
         assert ids_b[-2][0] == 999 and list(ids_b[-1][:min(k, 3)]) == [999, 1000, 1001][:min(k, 3)]
+
+
+@pytest.mark.parametrize("k", [1, 10])
+def test_mixed_shapes_match_oracle(msi, k):
+    """The harder value distributions (noisy sinusoids, Laplace-step walks with spike
+    bursts), with the fresh-draw-plus-noise queries of that workload."""
+    n, length = 20000, 256
+    X = datagen.mixed(4, 0, n, length)
+    Z = oracle.summarise(X, 16, 256)[0]
+    Q = datagen.mixed_queries(count=12)
+    ix = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=128)
+    ids, d = msi.msi_knn(ix, Q, k)
+    for i, q in enumerate(Q):
+        oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
+        assert np.array_equal(ids[i], oid), (k, i)
+        np.testing.assert_allclose(d[i], np.sqrt(od2), rtol=RTOL, atol=1e-6)

@@ -223,6 +223,47 @@ MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats,
 MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
 
 /*
+ * Serving: a request loop over several resident indexes with continuous batching.
+ * The paper answers one query after another (Section IV, "Setup"); this has no
+ * counterpart there. Each index gets query slots (a bounded workspace, a stream and
+ * staging buffers); a dispatcher thread admits waiting requests into free slots as
+ * soon as slots free up, so requests arriving while others run join the work in
+ * flight. Answers are exactly those of msi_knn. Indexes attached to a server must
+ * not be used by other calls until the server is freed.
+ */
+typedef struct msi_server msi_server;
+
+typedef struct msi_server_opts {
+  int32_t slots_per_index;  /* query slots per index, the first with room for any query; */
+                            /* 0 selects 8                                              */
+  int64_t workspace_bytes;  /* device bytes the bounded slots may use (admission by     */
+                            /* memory: slots beyond it are not created); 0 selects 8 GiB */
+  int32_t max_inflight;     /* most queries on the GPU at once; 0: no cap, 1: one at a time */
+  int32_t slot_capacity;    /* candidate / survivor room of a bounded slot (0: default)  */
+} msi_server_opts;
+
+/* Starts a server over n_indexes indexes (host array of handles); opts may be NULL.
+ * Errors: MSI_EINVAL, MSI_ENOMEM (slots), MSI_ECUDA. */
+MSI_API msi_status msi_server_create(msi_index* const* indexes, int32_t n_indexes, const msi_server_opts* opts,
+                                     msi_server** out);
+
+/* Queues one query (HOST memory, float[len] of index `index_no`) for its k nearest
+ * neighbours (1 .. min(n, MSI_MAX_K)); *ticket names it for msi_server_wait. */
+MSI_API msi_status msi_server_submit(msi_server* server, int32_t index_no, const float* query, int32_t k,
+                                     uint64_t* ticket);
+
+/* Waits for a ticket's answer: ids int64[k] and dists float[k] (HOST memory; dists
+ * may be NULL) and the time from submission to completion in ms (may be NULL). */
+MSI_API msi_status msi_server_wait(msi_server* server, uint64_t ticket, int64_t* ids, float* dists,
+                                   double* latency_ms);
+
+/* Requests completed, queries rerun on a full workspace, and slots in use. */
+MSI_API msi_status msi_server_stats(msi_server* server, int64_t* completed, int64_t* reruns, int32_t* slots);
+
+/* Finishes the queued requests, stops the loop and releases the slots. */
+MSI_API void msi_server_free(msi_server* server);
+
+/*
  * msi_lower_bounds_noalloc -- msi_lower_bounds for callers that cannot allocate
  * device memory. The paper has no counterpart: it exists for code that must not
  * call cudaMalloc, such as code running while a stream is captured into a CUDA graph

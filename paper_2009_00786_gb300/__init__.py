@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "MsiError", "Index", "msi_build", "msi_knn", "msi_knn_ex", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
-    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
+    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "Server", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
 ]
 
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
@@ -85,6 +85,23 @@ _lib.msi_set_timing.argtypes = [_vp, _i32]
 _lib.msi_set_timing.restype = ctypes.c_int
 _lib.msi_lower_bounds_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.msi_lower_bounds_noalloc.restype = ctypes.c_int
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("slots_per_index", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int32), ("slot_capacity", ctypes.c_int32)]
+
+
+_lib.msi_server_create.argtypes = [_vp, _i32, ctypes.POINTER(_ServerOpts), ctypes.POINTER(_vp)]
+_lib.msi_server_create.restype = ctypes.c_int
+_lib.msi_server_submit.argtypes = [_vp, _i32, _vp, _i32, ctypes.POINTER(ctypes.c_uint64)]
+_lib.msi_server_submit.restype = ctypes.c_int
+_lib.msi_server_wait.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, ctypes.POINTER(ctypes.c_double)]
+_lib.msi_server_wait.restype = ctypes.c_int
+_lib.msi_server_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
+_lib.msi_server_stats.restype = ctypes.c_int
+_lib.msi_server_free.argtypes = [_vp]
+_lib.msi_server_free.restype = None
 
 
 class MsiError(RuntimeError):
@@ -266,3 +283,49 @@ def msi_lower_bounds_noalloc(index, query, series_lb, leaf_lb, stream=None):
     float32 [n] and [leaves]); the library allocates nothing for this call."""
     _check(_lib.msi_lower_bounds_noalloc(ctypes.c_void_p(index.handle), _ptr(query, np.float32),
                                          _ptr(series_lb, np.float32), _ptr(leaf_lb, np.float32), _stream(stream)))
+
+
+class Server:
+    """msi_server_*: a request loop with continuous batching over resident indexes."""
+
+    def __init__(self, indexes, slots_per_index=0, workspace_bytes=0, max_inflight=0, slot_capacity=0):
+        self._indexes = list(indexes)  # keep the indexes alive
+        arr = (ctypes.c_void_p * len(self._indexes))(*[ix.handle for ix in self._indexes])
+        opts = _ServerOpts(slots_per_index, workspace_bytes, max_inflight, slot_capacity)
+        out = ctypes.c_void_p()
+        _check(_lib.msi_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self._indexes), ctypes.byref(opts),
+                                      ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, index_no, query, k):
+        """msi_server_submit: query is a host float32 array of the index's length."""
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        t = ctypes.c_uint64()
+        _check(_lib.msi_server_submit(ctypes.c_void_p(self.handle), index_no, ctypes.c_void_p(q.ctypes.data), k,
+                                      ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, k):
+        """msi_server_wait: (ids int64 [k], dists float32 [k], latency ms)."""
+        ids = np.empty(k, dtype=np.int64)
+        d = np.empty(k, dtype=np.float32)
+        ms = ctypes.c_double()
+        _check(_lib.msi_server_wait(ctypes.c_void_p(self.handle), ticket, ctypes.c_void_p(ids.ctypes.data),
+                                    ctypes.c_void_p(d.ctypes.data), ctypes.byref(ms)))
+        return ids, d, ms.value
+
+    def stats(self):
+        c, r, sl = _i64(), _i64(), _i32()
+        _check(_lib.msi_server_stats(ctypes.c_void_p(self.handle), ctypes.byref(c), ctypes.byref(r), ctypes.byref(sl)))
+        return {"completed": c.value, "reruns": r.value, "slots": sl.value}
+
+    def close(self):
+        if self.handle:
+            _lib.msi_server_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

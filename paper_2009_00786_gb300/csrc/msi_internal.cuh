@@ -278,6 +278,9 @@ struct msi_index {
   int refine_grid = 0;
   int rows_grid = 0;
   int blocks_grid = 0;
+  bool grids_ready = false;  // persistent grid sizes of every refinement mode
+  int grid_series = 0, grid_blocks = 0, grid_rows1 = 0, grid_rowsk = 0, grid_block_kernel = 0;
+  size_t smem_block_kernel = 0;
   size_t refine_smem = 0;
   int refine_smem_k = -1;
   bool timing = false;
@@ -320,6 +323,10 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
 cudaError_t slots_setup(msi_index* ix);
+cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
+                            int64_t* bytes);
+void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap);
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
 void free_workspace(QueryView& qv);
 cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
                       float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,

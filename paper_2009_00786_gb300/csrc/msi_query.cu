@@ -47,7 +47,32 @@ __device__ __forceinline__ float warp_sqdist(const IndexView& ix, uint32_t id, f
     const float4* r4 = reinterpret_cast<const float4*>(row);
     const float4* q4 = reinterpret_cast<const float4*>(qs);
     const int n4 = ix.len >> 2;
-    if (ix.data_is_z) {
+    if (n4 <= 8 * 32) {  // rows of up to 1024 points: every load issued first
+      float4 x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = lane + 32 * j;
+        x[j] = c < n4 ? __ldg(r4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = lane + 32 * j;
+        if (c < n4) {
+          float4 z = x[j];
+          if (!ix.data_is_z) {
+            z.x = znorm_value(z.x, ms.x, ms.y);
+            z.y = znorm_value(z.y, ms.x, ms.y);
+            z.z = znorm_value(z.z, ms.x, ms.y);
+            z.w = znorm_value(z.w, ms.x, ms.y);
+          }
+          const float4 q = q4[c];
+          float d = __fsub_rn(z.x, q.x); acc = __fmaf_rn(d, d, acc);
+          d = __fsub_rn(z.y, q.y); acc = __fmaf_rn(d, d, acc);
+          d = __fsub_rn(z.z, q.z); acc = __fmaf_rn(d, d, acc);
+          d = __fsub_rn(z.w, q.w); acc = __fmaf_rn(d, d, acc);
+        }
+      }
+    } else if (ix.data_is_z) {
       for (int c = lane; c < n4; c += 32) {
         const float4 x = __ldg(r4 + c), q = q4[c];
         float d = __fsub_rn(x.x, q.x); acc = __fmaf_rn(d, d, acc);
@@ -152,6 +177,30 @@ __device__ uint32_t block_select_u32(Get get, uint32_t count, uint32_t k, uint32
   return prefix;
 }
 
+// Block-wide copy of `count` floats from global to shared memory with every load
+// issued before the first store (up to 4 float4 per thread in flight), so the copy
+// costs one memory round trip instead of one per element.
+__device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ src, int count) {
+  const bool vec = ((((uintptr_t)dst) | ((uintptr_t)src)) & 15) == 0;
+  const int n4 = vec ? count >> 2 : 0;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int base = 0; base < n4; base += 4 * blockDim.x) {
+    float4 r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + j * blockDim.x + threadIdx.x;
+      r[j] = i < n4 ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + j * blockDim.x + threadIdx.x;
+      if (i < n4) d4[i] = r[j];
+    }
+  }
+  for (int i = 4 * n4 + threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 // ------------------------------------------------------------------ q_prep
 __global__ void __launch_bounds__(kThreads)
 q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
@@ -166,10 +215,12 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     thr_up_s[v] = ix.thr_up[v];
     thr_lo_s[v] = ix.thr_lo[v];
   }
+  smem_fill(zs, q, ix.len);  // the raw query, staged with all loads in flight
   __syncthreads();
   if (warp == 0) {
-    const Moments m = warp_moments_generic(q, ix.len);
-    for (int t = lane; t < ix.len; t += 32) zs[t] = m.flag != 0 ? 0.0f : znorm_value(q[t], m.mu, m.rsig);
+    const Moments m = warp_moments_generic(zs, ix.len);
+    __syncwarp();
+    for (int t = lane; t < ix.len; t += 32) zs[t] = m.flag != 0 ? 0.0f : znorm_value(zs[t], m.mu, m.rsig);
     __syncwarp();
     int sym = 0;
     if (lane < ix.w) {
@@ -269,7 +320,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
 __global__ void __launch_bounds__(kThreads)
 q_seed(IndexView ix, QueryView qv) {
   extern __shared__ __align__(16) float qs[];
-  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  smem_fill(qs, qv.qz, ix.len);
   __syncthreads();
   __shared__ unsigned s_min;
   if (threadIdx.x == 0) s_min = 0x7f800000u;
@@ -390,8 +441,8 @@ q_refine(IndexView ix, QueryView qv) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wc = ix.w * ix.card;
-  for (int e = tid; e < wc; e += blockDim.x) Ts[e] = qv.T[e];
-  for (int t = tid; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  smem_fill(Ts, qv.T, wc);
+  smem_fill(qs, qv.qz, ix.len);
   if (tid == 0) { s_bc = 0; s_local = 0x7f800000u; }
   QState* st = qv.st;
   const uint32_t leaf_count = st->leaf_count;
@@ -511,7 +562,7 @@ q_refine(IndexView ix, QueryView qv) {
 //   only by a distance below the current BSF. 1 < k <= 32: each warp keeps its k
 //   best in registers (lane i holds the i-th) and publishes its k-th once it has k.
 constexpr int kFiltWarps = 8;
-constexpr int kUnroll = 8;
+constexpr int kUnroll = 4;
 constexpr int kBlocksPerItem = kItem / 32;
 constexpr int kRows = 4;
 constexpr int kRowWarps = 8;
@@ -527,7 +578,7 @@ q_filter_blocks(IndexView ix, QueryView qv) {
   __shared__ int qsym_s[16];
   __shared__ uint32_t s_cnt, s_base;
   __shared__ uint2 s_out[kBlkThreads];
-  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  smem_fill(Ts, qv.T, ix.w * ix.card);
   if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
   const uint32_t ntask = qv.st->item_count * kBlocksPerItem;
   const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
@@ -588,8 +639,8 @@ q_filter_series(IndexView ix, QueryView qv) {
   __shared__ uint2 buf_s[kFiltWarps][64];
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
-  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
-  for (int e = threadIdx.x; e < ix.w * 32; e += blockDim.x) T5s[e] = qv.T5[e];
+  smem_fill(Ts, qv.T, ix.w * ix.card);
+  smem_fill(T5s, qv.T5, ix.w * 32);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
@@ -696,7 +747,7 @@ template <bool KONE>
 __global__ void __launch_bounds__(kRowWarps * 32)
 q_refine_rows(IndexView ix, QueryView qv) {
   extern __shared__ __align__(16) float qs[];
-  for (int t = threadIdx.x; t < ix.len; t += blockDim.x) qs[t] = qv.qz[t];
+  smem_fill(qs, qv.qz, ix.len);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   QState* st = qv.st;
@@ -708,22 +759,36 @@ q_refine_rows(IndexView ix, QueryView qv) {
   unsigned mine = 0x7f800000u;
   uint32_t n_ref = 0;
   const uint32_t gw = blockIdx.x * kRowWarps + warp;
-  const uint32_t stride = gridDim.x * kRowWarps;
-  for (uint32_t g = gw * kRows; g < nsurv; g += stride * kRows) {
+  const uint32_t step = gridDim.x * kRowWarps * kRows;
+  // three-stage pipeline over this warp's groups of kRows survivors (lanes < kRows
+  // hold one survivor each): the survivor entry of group g + 2 step and the perm /
+  // moments of group g + step are in flight while the rows of group g are read
+  uint2 sv_a = make_uint2(0, 0), sv_b = make_uint2(0, 0);
+  uint32_t id_b = 0;
+  float2 ms_b = make_float2(0.f, 0.f);
+  const uint32_t g0 = gw * kRows;
+  if (lane < kRows && g0 + lane < nsurv) sv_b = qv.surv[g0 + lane];
+  if (lane < kRows && g0 + lane < nsurv) {
+    id_b = __ldg(ix.perm + sv_b.x);
+    if (!ix.data_is_z) ms_b = __ldg(ix.stats + sv_b.x);
+  }
+  if (lane < kRows && g0 + step + lane < nsurv) sv_a = qv.surv[g0 + step + lane];
+  for (uint32_t g = g0; g < nsurv; g += step) {
+    const uint2 sv = sv_b;
+    const uint32_t myid_cur = id_b;
+    const float2 myms_cur = ms_b;
+    if (lane < kRows && g + step + lane < nsurv) {
+      id_b = __ldg(ix.perm + sv_a.x);
+      if (!ix.data_is_z) ms_b = __ldg(ix.stats + sv_a.x);
+    }
+    sv_b = sv_a;
+    if (lane < kRows && g + 2 * step + lane < nsurv) sv_a = qv.surv[g + 2 * step + lane];
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
     const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
-    uint32_t myp = 0, myid = 0;
-    float2 myms = make_float2(0.f, 0.f);
-    bool mine_live = false;
-    if (lane < kRows && g + lane < nsurv) {
-      const uint2 sv = qv.surv[g + lane];
-      myp = sv.x;
-      mine_live = __uint_as_float(sv.y) <= bound2;  // re-test against the current BSF
-      if (mine_live) {
-        myid = __ldg(ix.perm + myp);
-        if (!ix.data_is_z) myms = __ldg(ix.stats + myp);
-      }
-    }
+    const uint32_t myp = sv.x;
+    const bool mine_live = lane < kRows && g + lane < nsurv && __uint_as_float(sv.y) <= bound2;
+    const uint32_t myid = myid_cur;
+    const float2 myms = myms_cur;
     const unsigned rm = __ballot_sync(kFull, mine_live);
     if (!rm) continue;
     uint32_t id[kRows];
@@ -740,12 +805,20 @@ q_refine_rows(IndexView ix, QueryView qv) {
     if ((ix.len & 3) == 0) {
       const int n4 = ix.len >> 2;
       const float4* q4 = reinterpret_cast<const float4*>(qs);
-      for (int c = lane; c < n4; c += 32) {
-        float4 x[kRows];
+      for (int c0 = lane; c0 < n4; c0 += 64) {  // two float4 of every row in flight
+        float4 x2[2][kRows];
 #pragma unroll
-        for (int j = 0; j < kRows; ++j)
-          x[j] = (rm >> j) & 1u ? __ldg(reinterpret_cast<const float4*>(ix.data + (size_t)id[j] * ix.len) + c)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < kRows; ++j)
+            x2[h][j] = ((rm >> j) & 1u) && c0 + 32 * h < n4
+                           ? __ldg(reinterpret_cast<const float4*>(ix.data + (size_t)id[j] * ix.len) + c0 + 32 * h)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+        const int c = c0 + 32 * h;
+        if (c >= n4) break;
+        const float4* x = x2[h];
         const float4 q = q4[c];
 #pragma unroll
         for (int j = 0; j < kRows; ++j) {
@@ -760,6 +833,7 @@ q_refine_rows(IndexView ix, QueryView qv) {
           d = __fsub_rn(z.y, q.y); acc[j] = __fmaf_rn(d, d, acc[j]);
           d = __fsub_rn(z.z, q.z); acc[j] = __fmaf_rn(d, d, acc[j]);
           d = __fsub_rn(z.w, q.w); acc[j] = __fmaf_rn(d, d, acc[j]);
+        }
         }
       }
     } else {
@@ -1042,7 +1116,7 @@ q_lb_all(IndexView ix, QueryView qv, float* __restrict__ series_lb, float* __res
     thr_lo_s[v] = ix.thr_lo[v];
   }
   if (threadIdx.x < ix.w) paa_s[threadIdx.x] = qv.st->qpaa[threadIdx.x];
-  for (int e = threadIdx.x; e < ix.w * ix.card; e += blockDim.x) Ts[e] = qv.T[e];
+  smem_fill(Ts, qv.T, ix.w * ix.card);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (series_lb)
@@ -1074,8 +1148,10 @@ cudaError_t dalloc(T** p, size_t count) {
 
 // One query workspace with room for cand_cap candidates and surv_cap survivors
 // (work items, block lists and leaf lists always have room for any query).
-static cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
-                                   int64_t* bytes) {
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
+
+cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
+                            int64_t* bytes) {
   cudaError_t e;
   const size_t items = (size_t)(ix->n / kItem + 2 * ix->L + 2);
   if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
@@ -1096,10 +1172,15 @@ static cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t 
   qv.ovf = nullptr;
   qv.eps = 1.52587890625e-05f;  // 2^-16
   qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
-  *bytes += (int64_t)(ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
-            (int64_t)items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 +
-            (int64_t)surv_cap * 8;
+  *bytes += workspace_bytes(ix, cand_cap, surv_cap);
   return cudaSuccess;
+}
+
+// Device bytes of one query workspace (alloc_workspace).
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap) {
+  const int64_t items = ix->n / kItem + 2 * ix->L + 2;
+  return (int64_t)(ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
+         items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
 
 void free_workspace(QueryView& qv) {
@@ -1132,16 +1213,23 @@ cudaError_t query_setup(msi_index* ix) {
   return cudaSuccess;
 }
 
+// Candidate and survivor room of a bounded slot: the seed needs max(leaf capacity, k)
+// candidate entries; `requested` (0: the defaults) sets both lists otherwise.
+void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap) {
+  const int64_t seed_room = std::min<int64_t>(ix->n, (int64_t)ix->cap + MSI_MAX_K);
+  *cand_cap = (uint32_t)std::min<int64_t>(
+      ix->n, std::max<int64_t>(seed_room, requested ? requested : std::max<int64_t>(65536, seed_room)));
+  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, requested ? requested : 1 << 20);
+}
+
 // Allocates the concurrent query slots (bounded lists), their streams and events.
 cudaError_t slots_setup(msi_index* ix) {
   if ((int)ix->slots.size() == ix->nslots) return cudaSuccess;
   cudaError_t e;
   if (!ix->fork_event && (e = cudaEventCreateWithFlags(&ix->fork_event, cudaEventDisableTiming)) != cudaSuccess) return e;
   // the seed needs max(leaf capacity, k) candidate entries
-  const int64_t seed_room = std::min<int64_t>(ix->n, (int64_t)ix->cap + MSI_MAX_K);
-  const uint32_t cand_cap = (uint32_t)std::min<int64_t>(
-      ix->n, std::max<int64_t>(seed_room, ix->slot_cap ? ix->slot_cap : std::max<int64_t>(65536, seed_room)));
-  const uint32_t surv_cap = (uint32_t)std::min<int64_t>(ix->n, ix->slot_cap ? ix->slot_cap : 1 << 20);
+  uint32_t cand_cap, surv_cap;
+  slot_capacities(ix, ix->slot_cap, &cand_cap, &surv_cap);
   while ((int)ix->slots.size() < ix->nslots) {
     QueryView qv{};
     if ((e = alloc_workspace(ix, qv, cand_cap, surv_cap, &ix->device_bytes)) != cudaSuccess) {
@@ -1167,33 +1255,47 @@ cudaError_t slots_setup(msi_index* ix) {
   return cudaSuccess;
 }
 
-// Persistent grids of the refinement kernels: the two streaming kernels up to
-// k = 32, the block kernel with a shared-memory top-k buffer above.
+// Persistent grids of the refinement kernels, computed once per index: the two
+// streaming kernels up to k = 32, the block kernel with a shared-memory top-k buffer
+// above; refine_config selects those of k's mode.
 static cudaError_t refine_config(msi_index* ix, int k) {
   const int mode = k == 1 ? 1 : (k <= 32 ? 32 : 0);
-  if (ix->refine_smem_k == mode) return cudaSuccess;
-  int sms = 0, per_sm = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  if (e != cudaSuccess) return e;
-  if (mode) {
-    const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32,
-                                                            fsmem + sizeof(float) * (size_t)ix->w * 32)) != cudaSuccess)
-      return e;
-    ix->refine_grid = std::max(1, per_sm) * sms;
-    ix->refine_smem = fsmem;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, fsmem)) != cudaSuccess) return e;
-    ix->blocks_grid = std::max(1, per_sm) * sms;
-    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
-    e = mode == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<true>, kRowWarps * 32, rsmem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<false>, kRowWarps * 32, rsmem);
+  if (!ix->grids_ready) {
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     if (e != cudaSuccess) return e;
-    ix->rows_grid = std::max(1, per_sm) * sms;
+    const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+    const size_t ssmem = fsmem + sizeof(float) * (size_t)ix->w * 32;
+    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, ssmem)) != cudaSuccess)
+      return e;
+    ix->grid_series = std::max(1, per_sm) * sms;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, fsmem)) != cudaSuccess)
+      return e;
+    ix->grid_blocks = std::max(1, per_sm) * sms;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<true>, kRowWarps * 32, rsmem)) !=
+        cudaSuccess)
+      return e;
+    ix->grid_rows1 = std::max(1, per_sm) * sms;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<false>, kRowWarps * 32, rsmem)) !=
+        cudaSuccess)
+      return e;
+    ix->grid_rowsk = std::max(1, per_sm) * sms;
+    const size_t bsmem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, bsmem)) != cudaSuccess)
+      return e;
+    ix->grid_block_kernel = std::max(1, per_sm) * sms;
+    ix->smem_block_kernel = bsmem;
+    ix->grids_ready = true;
+  }
+  if (mode) {
+    ix->refine_grid = ix->grid_series;
+    ix->refine_smem = sizeof(float) * (size_t)ix->w * ix->card;
+    ix->blocks_grid = ix->grid_blocks;
+    ix->rows_grid = mode == 1 ? ix->grid_rows1 : ix->grid_rowsk;
   } else {
-    const size_t smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, smem)) != cudaSuccess) return e;
-    ix->refine_grid = std::max(1, per_sm) * sms;
-    ix->refine_smem = smem;
+    ix->refine_grid = ix->grid_block_kernel;
+    ix->refine_smem = ix->smem_block_kernel;
     ix->rows_grid = 0;
   }
   ix->refine_smem_k = mode;

@@ -32,7 +32,6 @@ METRIC = "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs pla
 def workload(n_total, length, nq, k, leaf):
     return (f"{n_total // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries (50% fresh walks, "
             f"50% noisy members), k={k}, 16 segments, cardinality 256, leaf capacity {leaf}")
-KERNELS_PER_QUERY = {1: 6}  # q_prep, q_seed, q_leaf_filter, q_filter_series, q_refine_rows, q_finalize
 
 
 def parse():
@@ -49,6 +48,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=2_000_000, help="series in the oracle's timed sample")
     p.add_argument("--cpu-queries", type=int, default=10)
+    p.add_argument("--serving", action="store_true", help="Poisson-arrival serving sweep over three collections")
+    p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
+    p.add_argument("--rates", default="1000,3000,10000,30000,100000")
+    p.add_argument("--serve-requests", type=int, default=3000, help="most requests per rate")
     return p.parse_args()
 
 
@@ -153,10 +156,73 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def serving(args):
+    """Continuous batching vs one query at a time, under Poisson arrivals: three
+    resident random-walk collections (80M x 128, 40M x 256, 8M x 1024 at scale 1),
+    each request targeting a uniform collection with k uniform in 1..100."""
+    import random
+
+    import torch
+
+    import datagen
+    import paper_2009_00786_gb300 as msi
+    dev = torch.device("cuda:0")
+    shapes = [(int(80e6 * args.serve_scale), 128), (int(40e6 * args.serve_scale), 256),
+              (int(8e6 * args.serve_scale), 1024)]
+    s = torch.cuda.Stream()
+    cols, indexes, pools = [], [], []
+    for ci, (n, length) in enumerate(shapes):
+        X = torch.empty((n, length), dtype=torch.float32, device=dev)
+        datagen.walks_device(10 + ci, 0, n, length, X.data_ptr(), s.cuda_stream)
+        s.synchronize()
+        cols.append(X)
+        indexes.append(msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=2000,
+                                     flags=msi.MSI_BUILD_BORROW, query_slots=1))
+        n_fresh, ids, sig = datagen.query_plan(n, 64, fresh_seed=20 + ci, pick_seed=30 + ci)
+        pools.append(np.concatenate([datagen.walks(20 + ci, 0, n_fresh, length),
+                                     datagen.noisy_copies(10 + ci, 30 + ci, ids, sig, length)]))
+    rates = [float(r) for r in args.rates.split(",")]
+    out = {"metric": "serving: exact k-NN queries/s and p50/p99 ms under Poisson arrivals, continuous batching "
+                     "vs one query at a time",
+           "unit": "queries/s", "data": "synthetic",
+           "config": {"workload": " + ".join(f"{n // 1_000_000}M x {l}" for n, l in shapes) +
+                      " fp32 random walks, k uniform in 1..100, uniform collection per request"},
+           "rates": []}
+    for name, opts in (("continuous", dict(slots_per_index=8)), ("one_at_a_time", dict(slots_per_index=1,
+                                                                                        max_inflight=1))):
+        srv = msi.Server(indexes, **opts)
+        for rate in rates:
+            rng = random.Random(int(rate))
+            nreq = int(min(args.serve_requests, max(200, rate * 2)))
+            t = 0.0
+            plan = []
+            for _ in range(nreq):
+                t += rng.expovariate(rate)
+                ci = rng.randrange(3)
+                plan.append((t, ci, pools[ci][rng.randrange(64)], rng.randint(1, 100)))
+            tickets = []
+            t0 = time.perf_counter()
+            for at, ci, q, k in plan:
+                while time.perf_counter() - t0 < at:
+                    pass
+                tickets.append((srv.submit(ci, q, k), k))
+            lat = [srv.wait(tk, k)[2] for tk, k in tickets]
+            wall = time.perf_counter() - t0
+            out["rates"].append({"server": name, "offered_qps": rate, "requests": nreq,
+                                 "achieved_qps": nreq / wall, "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)), **{f"srv_{kk}": v for kk, v in srv.stats().items()}})
+            print(json.dumps(out["rates"][-1]), file=sys.stderr, flush=True)
+        srv.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.serving:
+        serving(args)
         return
     import torch
     import torch.distributed as dist
@@ -225,6 +291,7 @@ def main():
         stream.synchronize()
     torch.cuda.synchronize()
     elapsed_ms = e0.elapsed_time(e1)
+    launches = msi.msi_query_stats_get(index)["kernel_launches"]  # counted by the library
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -310,7 +377,7 @@ def main():
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
                 "d2h_bytes_per_step": nq * k * 12},
-        "gpu_launches": KERNELS_PER_QUERY.get(k, 6) * nq * args.steps,
+        "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},

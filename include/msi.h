@@ -212,6 +212,7 @@ typedef struct msi_query_stats {
   double refine_ms;              /* summed device time of the refinement: series    */
                                  /* filter + row refinement (timing enabled only)   */
   double filter_ms;              /* the series-filter part of refine_ms             */
+  int64_t kernel_launches;       /* kernels the query path launched (all queries)   */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises

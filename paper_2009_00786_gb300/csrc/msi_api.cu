@@ -503,12 +503,14 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->refine_launches = ix->refine_launches;
   st->refine_ms = ix->refine_ms;
   st->filter_ms = ix->filter_ms;
+  st->kernel_launches = ix->kernel_launches.load();
   if (reset) {
     if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_BAD_QUERY)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");
     ix->refine_ms = 0.0;
     ix->filter_ms = 0.0;
     ix->refine_launches = 0;
+    ix->kernel_launches = 0;
   }
   return MSI_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -50,6 +51,7 @@ struct QState {
   unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int blk_count;       // leaf blocks whose envelope bound passed
   unsigned int overflow;        // a candidate or survivor list ran out of room
+  uint32_t front_a, front_b;    // leaf-order positions of the lowest-bound leaf, refined early
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -75,7 +77,8 @@ struct QueryView {
   float* leaf_lb2;              // [L]
   uint4* items;                 // [n / kItem + 2L]: {first pos, end pos, leaf bound^2 bits, leaf}
   uint2* surv;                  // [n]: {leaf-order position, bound^2 bits} of filter survivors
-  uint2* blks;                  // [8 (n / kItem + 2L)]: {block index, item index} of surviving blocks
+  uint2* blks;                  // [8 (n / kItem + 2L)]: {block index, lo | hi << 8} of surviving blocks
+  unsigned long long* blockmin; // [L / 256 + 2]: per leaf-filter block, min (bound^2 bits << 32 | leaf)
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
   double* rc_d;                 // [n]
   uint32_t* rc_id;              // [n]
@@ -288,6 +291,7 @@ struct msi_index {
   double refine_ms = 0.0;
   double filter_ms = 0.0;
   int64_t refine_launches = 0;
+  std::atomic<int64_t> kernel_launches{0};  // query_one runs on caller and server threads
 
   msi::IndexView view() const {
     msi::IndexView v;

@@ -306,6 +306,8 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->surv_count = 0;
     st->blk_count = 0;
     st->overflow = 0;
+    st->front_a = 0;
+    st->front_b = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -409,6 +411,98 @@ q_leaf_filter(IndexView ix, QueryView qv) {
                                          (uint32_t)l);
     }
   }
+  // the block's lowest-bound surviving leaf (ties: lowest leaf), for the early
+  // refinement of the most promising leaf
+  __shared__ unsigned long long s_min[kThreads / 32];
+  unsigned long long mine = keep ? (((unsigned long long)__float_as_uint(lb2) << 32) | (uint32_t)l) : ~0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(kFull, mine, o);
+    mine = other < mine ? other : mine;
+  }
+  if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = ~0ull;
+    for (int w = 0; w < kThreads / 32; ++w) b = s_min[w] < b ? s_min[w] : b;
+    qv.blockmin[blockIdx.x] = b;
+  }
+}
+
+// The lowest-bound surviving leaf, refined before the block and series filters so
+// that they run against a tighter BSF (the priority order of ProcessQueue,
+// Algorithm 8: the most promising leaf first). Every block finds the same leaf from
+// the leaf filter's per-block minima; warps take its positions in a stride. A leaf
+// whose bound already exceeds the BSF is skipped; its positions are excluded from
+// the later passes like the seed's.
+__global__ void __launch_bounds__(kThreads)
+q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
+  extern __shared__ __align__(16) float qs[];
+  __shared__ unsigned long long s_best;
+  __shared__ unsigned s_min;
+  smem_fill(qs, qv.qz, ix.len);
+  unsigned long long best = ~0ull;
+  for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
+    const unsigned long long v = qv.blockmin[i];
+    best = v < best ? v : best;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+  }
+  if (threadIdx.x == 0) {
+    s_best = ~0ull;
+    s_min = 0x7f800000u;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicMin(&s_best, best);
+  __syncthreads();
+  best = s_best;
+  QState* st = qv.st;
+  if (best == ~0ull) return;
+  const float lb2 = __uint_as_float((uint32_t)(best >> 32));
+  if (lb2 > lb_bound2(*(volatile unsigned*)&st->thr_bits, qv.eps, qv.tau)) return;
+  const uint32_t l = (uint32_t)best;
+  const uint32_t a = ix.leaf_begin[l], b = ix.leaf_begin[l + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->front_a = a;
+    st->front_b = b;
+  }
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const unsigned thr = *(volatile unsigned*)&st->thr_bits;
+  const float keep2 = keep_bound2(thr, qv.eps);
+  const uint32_t warps = gridDim.x * (kThreads / 32);
+  const int lane = threadIdx.x & 31;
+  unsigned bestd = 0x7f800000u;
+  uint32_t n_front = 0;
+  for (uint32_t pos = a + blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); pos < b; pos += warps) {
+    if (pos >= sa && pos < sb) continue;  // already refined by the seed
+    const uint32_t id = ix.perm[pos];
+    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
+    const float d2 = warp_sqdist(ix, id, ms, qs);
+    if (lane == 0) {
+      ++n_front;
+      if (d2 <= keep2) {
+        const uint32_t slot = atomicAdd(&st->cand_count, 1u);
+        if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, pos);
+        else st->overflow = 1u;
+      }
+    }
+    bestd = min(bestd, __float_as_uint(d2));
+  }
+  __shared__ unsigned s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  if (lane == 0) {
+    if (bestd < 0x7f800000u) atomicMin(&s_min, bestd);
+    if (n_front) atomicAdd(&s_n, n_front);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_n) atomicAdd(&st->series_refined, s_n);  // one global atomic per block
+    if (qv.k == 1 && s_min < thr) atomicMin(&st->thr_bits, s_min);
+  }
 }
 
 // ------------------------------------------------------------------ q_refine
@@ -446,7 +540,7 @@ q_refine(IndexView ix, QueryView qv) {
   if (tid == 0) { s_bc = 0; s_local = 0x7f800000u; }
   QState* st = qv.st;
   const uint32_t leaf_count = st->leaf_count;
-  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const uint32_t sa = st->seed_a, sb = st->seed_b, fa = st->front_a, fb = st->front_b;
   const float seglen = (float)ix.seglen;
   const uint32_t bcap = (uint32_t)qv.k + kChunk;
   uint32_t n_lb = 0, n_ref = 0, n_leaf = 0;
@@ -472,7 +566,7 @@ q_refine(IndexView ix, QueryView qv) {
       const float bound2 = lb_bound2(s_thr, qv.eps, qv.tau);
       const uint32_t ce = min(e, cb + kChunk);
       for (uint32_t p = cb + tid; p < ce; p += blockDim.x) {
-        if (p >= sa && p < sb) continue;
+        if ((p >= sa && p < sb) || (p >= fa && p < fb)) continue;
         ++n_lb;
         if (word_lb2(ix.words[p], Ts, ix.w, ix.card, seglen) <= bound2) surv[atomicAdd(&s_ns, 1u)] = p;
       }
@@ -648,7 +742,7 @@ q_filter_series(IndexView ix, QueryView qv) {
   uint32_t* qp = qp_s[warp];
   QState* st = qv.st;
   const uint32_t ntask = st->blk_count;
-  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const uint32_t sa = st->seed_a, sb = st->seed_b, fa = st->front_a, fb = st->front_b;
   const float seglen = (float)ix.seglen;
   const int cshift = ix.bits > 5 ? ix.bits - 5 : 0;
   const unsigned lt = (1u << lane) - 1u;
@@ -704,7 +798,8 @@ q_filter_series(IndexView ix, QueryView qv) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t p = task[u].x * 32 + lane;
-      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
+      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb) &&
+                         (p < fa || p >= fb);
       n_lb += valid;
       const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
@@ -1099,8 +1194,8 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     atomicAdd(&c[ST_LEAVES_PROCESSED], s_part[2]);
     atomicAdd(&c[ST_SERIES_LB], s_part[0]);
     const unsigned long long seed = st->seed_b - st->seed_a;
-    atomicAdd(&c[ST_SERIES_REFINED], s_part[1] + seed);
-    atomicAdd(&c[ST_SEED], seed);
+    atomicAdd(&c[ST_SERIES_REFINED], s_part[1] + seed + st->series_refined);
+    atomicAdd(&c[ST_SEED], seed + st->series_refined);
     atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
     atomicAdd(&c[ST_RECHECKED], (unsigned long long)R);
   }
@@ -1163,6 +1258,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   if ((e = dalloc(&qv.items, items)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * items)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.partials, (size_t)3 * kMaxRefineWarps)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.blockmin, (size_t)(ix->L / kThreads + 2))) != cudaSuccess) return e;
   if ((e = dalloc(&qv.cand, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_d, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_id, (size_t)cand_cap)) != cudaSuccess) return e;
@@ -1185,7 +1281,7 @@ int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_ca
 
 void free_workspace(QueryView& qv) {
   void* ptrs[] = {qv.qz, qv.T, qv.T5, qv.st, qv.leaf_list, qv.leaf_lb2, qv.items, qv.blks, qv.partials,
-                  qv.cand, qv.rc_d, qv.rc_id, qv.surv};
+                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   qv = QueryView{};
@@ -1326,7 +1422,10 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);
   q_seed<<<(unsigned)std::min<int64_t>((seed_max + 7) / 8, 1024), kThreads, qbytes, s>>>(v, qv);
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
-  q_leaf_filter<<<(unsigned)((ix->L + kThreads - 1) / kThreads), kThreads, 0, s>>>(v, qv);
+  const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
+  q_leaf_filter<<<nlf, kThreads, 0, s>>>(v, qv);
+  q_front<<<(unsigned)std::min<int64_t>((ix->cap + 7) / 8, 256), kThreads, qbytes, s>>>(v, qv, nlf);
+  if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);  // the k-th best over seed and front
   if (ev_a) cudaEventRecord(ev_a, s);
   if (k <= 32) {
     q_filter_blocks<<<blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
@@ -1341,6 +1440,9 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   }
   if (ev_b) cudaEventRecord(ev_b, s);
   q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev, d64_dev);
+  // q_prep, q_seed, q_leaf_filter, q_front, q_finalize, the refinement (block filter,
+  // series filter and rows for k <= 32; one kernel above) and q_seed_select twice for k > 1.
+  ix->kernel_launches += 5 + (k <= 32 ? 3 : 1) + (k > 1 ? 2 : 0);
   return cudaGetLastError();
 }
 

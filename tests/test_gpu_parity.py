@@ -221,6 +221,14 @@ def test_stats_counters(msi):
     assert st["candidates"] >= 6 * 5 and st["rechecked"] >= 6 * 5
     assert st["refine_launches"] == 6 and st["refine_ms"] > 0
     assert st["series_lower_bounded"] < 6 * 8000  # leaves were pruned
+    # prep, seed, seed pick, leaf filter, front leaf, seed pick, block filter, series
+    # filter, row refinement, finalize
+    assert st["kernel_launches"] == 6 * 10
+    msi.msi_query_stats_get(ix, reset=True)
+    msi.msi_knn(ix, Q[:2], 1)
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 2 * 8
+    msi.msi_knn(ix, Q[:1], 40)  # one block-wise refinement kernel
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 2 * 8 + 8
 
 
 def test_batched_slots_match_single_queries_and_oracle(msi):

@@ -13,6 +13,12 @@ Parity status of each function (what pins it, tests/test_oracle_pins.py):
   mindist                    pinned (lower-bound property by brute force, special cases)
   knn_scan                   pinned (brute force, self-match, duplicates, k = N)
   knn_index                  pinned (equals knn_scan)
+  dtw_sq                     pinned (brute force over warping paths, r = 0 is the
+                             squared Euclidean distance, hand-worked cases)
+  envelope / lb_keogh        pinned (closed form on monotone series, bound property)
+  mindist_env                pinned (bounds LB_Keogh by brute force, reduces to the
+                             PAA mindist for segment-constant queries at r = 0)
+  knn_scan_dtw / knn_index_dtw  pinned (brute force, self-match, index equals scan)
 """
 import ctypes
 import os
@@ -47,6 +53,17 @@ def lib():
         L.orc_knn_scan.argtypes = [vp, i64, i32, vp, i32, vp, vp]
         L.orc_knn_index.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, i32, f64, vp, vp]
         L.orc_knn_index.restype = i64
+        L.orc_dtw_sq.argtypes = [vp, vp, i32, i32]
+        L.orc_dtw_sq.restype = f64
+        L.orc_envelope.argtypes = [vp, i32, i32, vp, vp]
+        L.orc_lb_keogh.argtypes = [vp, vp, vp, i32]
+        L.orc_lb_keogh.restype = f64
+        L.orc_paa_envelope.argtypes = [vp, vp, i32, i32, vp, vp]
+        L.orc_mindist_env.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp]
+        L.orc_mindist_env.restype = f64
+        L.orc_knn_scan_dtw.argtypes = [vp, i64, i32, vp, i32, i32, vp, vp]
+        L.orc_knn_index_dtw.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, i32, i32, f64, vp, vp]
+        L.orc_knn_index_dtw.restype = i64
         _lib = L
     return _lib
 
@@ -150,4 +167,65 @@ def knn_index(Z, words, zq, k, c=256, cap=2000, slack=1e-4):
     d2 = np.empty(k, dtype=np.float64)
     real = lib().orc_knn_index(_p(Z), _p(W), Z.shape[0], Z.shape[1], W.shape[1], c, cap, _p(zq), k,
                                slack, _p(ids), _p(d2))
+    return ids, d2, real
+
+
+# ------------------------------------------------------------------ DTW
+def dtw_sq(a, b, r):
+    """FP64 squared DTW of two fp32 series with a Sakoe-Chiba band of half-width r."""
+    a, b = _f32(a), _f32(b)
+    return lib().orc_dtw_sq(_p(a), _p(b), len(a), r)
+
+
+def envelope(q, r):
+    """LB_Keogh envelope (U, L) of a series for warping window r (float32)."""
+    q = _f32(q)
+    U, L = np.empty_like(q), np.empty_like(q)
+    lib().orc_envelope(_p(q), len(q), r, _p(U), _p(L))
+    return U, L
+
+
+def lb_keogh(U, L, b):
+    """Squared LB_Keogh of series b against the envelope (U, L), FP64."""
+    U, L, b = _f32(U), _f32(L), _f32(b)
+    return lib().orc_lb_keogh(_p(U), _p(L), _p(b), len(b))
+
+
+def paa_envelope(U, L, w):
+    """Per-segment max of U and min of L (FP64)."""
+    U, L = _f32(U), _f32(L)
+    Uh, Lh = np.empty(w), np.empty(w)
+    lib().orc_paa_envelope(_p(U), _p(L), len(U), w, _p(Uh), _p(Lh))
+    return Uh, Lh
+
+
+def mindist_env(Uh, Lh, lo, hi, n, c):
+    """DTW lower bound between a query's PAA envelope and symbol ranges [lo, hi]."""
+    Uh = np.ascontiguousarray(Uh, dtype=np.float64)
+    Lh = np.ascontiguousarray(Lh, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.uint8)
+    hi = np.ascontiguousarray(hi, dtype=np.uint8)
+    beta = breakpoints(c)
+    return lib().orc_mindist_env(_p(Uh), _p(Lh), _p(lo), _p(hi), len(Uh), n, c, _p(beta))
+
+
+def knn_scan_dtw(Z, zq, k, r):
+    """Exact k-NN under DTW (window r) by FP64 serial scan: (ids, DTW^2), ties -> lower id."""
+    Z = _f32(Z)
+    zq = _f32(zq)
+    ids = np.empty(k, dtype=np.int64)
+    d2 = np.empty(k, dtype=np.float64)
+    lib().orc_knn_scan_dtw(_p(Z), Z.shape[0], Z.shape[1], _p(zq), k, r, _p(ids), _p(d2))
+    return ids, d2
+
+
+def knn_index_dtw(Z, words, zq, k, r, c=256, cap=2000, slack=1e-4):
+    """Exact k-NN under DTW through the oracle's flat index: (ids, DTW^2, real_distance_count)."""
+    Z = _f32(Z)
+    W = np.ascontiguousarray(words, dtype=np.uint8)
+    zq = _f32(zq)
+    ids = np.empty(k, dtype=np.int64)
+    d2 = np.empty(k, dtype=np.float64)
+    real = lib().orc_knn_index_dtw(_p(Z), _p(W), Z.shape[0], Z.shape[1], W.shape[1], c, cap, _p(zq), k, r,
+                                   slack, _p(ids), _p(d2))
     return ids, d2, real

@@ -311,9 +311,18 @@ static int orc_leaf_cmp(const void* a, const void* b) {
   return (x->leaf > y->leaf) - (x->leaf < y->leaf);
 }
 
-int64_t orc_knn_index(const float* Z, const uint8_t* words, int64_t N, int32_t n, int32_t w,
-                      int32_t c, int32_t cap, const float* zq, int32_t k, double slack,
-                      int64_t* ids, double* d2) {
+/* Forward declarations of the DTW pieces (defined below). */
+double orc_dtw_sq(const float* a, const float* b, int32_t n, int32_t r);
+void orc_envelope(const float* q, int32_t n, int32_t r, float* U, float* L);
+void orc_paa_envelope(const float* U, const float* L, int32_t n, int32_t w, double* Uh, double* Lh);
+double orc_mindist_env(const double* Uh, const double* Lh, const uint8_t* lo, const uint8_t* hi, int32_t w,
+                       int32_t n, int32_t c, const double* beta);
+
+/* r < 0: Euclidean distance and the PAA mindist; r >= 0: DTW with a band of
+ * half-width r and the mindist of the query's PAA envelope (see below). */
+static int64_t orc_knn_index_metric(const float* Z, const uint8_t* words, int64_t N, int32_t n, int32_t w,
+                                    int32_t c, int32_t cap, const float* zq, int32_t k, double slack, int32_t r,
+                                    int64_t* ids, double* d2) {
   orc_wref* order = (orc_wref*)malloc(sizeof(orc_wref) * (size_t)N);
   for (int64_t i = 0; i < N; ++i) {
     order[i].words = words + i * w;
@@ -336,11 +345,20 @@ int64_t orc_knn_index(const float* Z, const uint8_t* words, int64_t N, int32_t n
   }
   double* beta = (double*)malloc(sizeof(double) * (size_t)(c - 1));
   orc_breakpoints(c, beta);
-  double qpaa[64];
+  double qpaa[64], Uh[64], Lh[64];
   orc_paa64(zq, n, w, qpaa);
+  if (r >= 0) {
+    float* U = (float*)malloc(sizeof(float) * (size_t)n);
+    float* Lo = (float*)malloc(sizeof(float) * (size_t)n);
+    orc_envelope(zq, n, r, U, Lo);
+    orc_paa_envelope(U, Lo, n, w, Uh, Lh);
+    free(U);
+    free(Lo);
+  }
   orc_leaf_lb* queue = (orc_leaf_lb*)malloc(sizeof(orc_leaf_lb) * (size_t)L);
   for (int64_t l = 0; l < L; ++l) {
-    queue[l].lb = orc_mindist(qpaa, lo + l * w, hi + l * w, w, n, c, beta);
+    queue[l].lb = r < 0 ? orc_mindist(qpaa, lo + l * w, hi + l * w, w, n, c, beta)
+                        : orc_mindist_env(Uh, Lh, lo + l * w, hi + l * w, w, n, c, beta);
     queue[l].leaf = l;
   }
   qsort(queue, (size_t)L, sizeof(orc_leaf_lb), orc_leaf_cmp);
@@ -353,9 +371,12 @@ int64_t orc_knn_index(const float* Z, const uint8_t* words, int64_t N, int32_t n
     for (int64_t p = l * cap; p < N && p < (l + 1) * cap; ++p) {
       const double bsf2 = cnt < k ? INFINITY : sqrt(d2[k - 1]);
       const uint8_t* wd = order[p].words;
-      if (orc_mindist(qpaa, wd, wd, w, n, c, beta) > bsf2 + slack) continue;
+      const double lb = r < 0 ? orc_mindist(qpaa, wd, wd, w, n, c, beta)
+                              : orc_mindist_env(Uh, Lh, wd, wd, w, n, c, beta);
+      if (lb > bsf2 + slack) continue;
       ++real;
-      orc_topk_push(d2, ids, &cnt, k, orc_sqdist(Z + order[p].id * n, zq, n), order[p].id);
+      const float* row = Z + order[p].id * n;
+      orc_topk_push(d2, ids, &cnt, k, r < 0 ? orc_sqdist(row, zq, n) : orc_dtw_sq(row, zq, n, r), order[p].id);
     }
   }
   free(order);
@@ -364,4 +385,152 @@ int64_t orc_knn_index(const float* Z, const uint8_t* words, int64_t N, int32_t n
   free(beta);
   free(queue);
   return real;
+}
+
+int64_t orc_knn_index(const float* Z, const uint8_t* words, int64_t N, int32_t n, int32_t w,
+                      int32_t c, int32_t cap, const float* zq, int32_t k, double slack,
+                      int64_t* ids, double* d2) {
+  return orc_knn_index_metric(Z, words, N, n, w, c, cap, zq, k, slack, -1, ids, d2);
+}
+
+/* ------------------------------------------------------------------ DTW
+ * Section IV, "MESSI with DTW": the index is left as it is; the search uses the
+ * LB_Keogh envelope of the query (Keogh and Ratanamahatana 2005) for its lower
+ * bounds and Dynamic Time Warping (Berndt and Clifford 1994) for its real
+ * distances, with a warping window (the paper uses 10% of the series length).
+ *
+ * DTW^2(a, b) = D(n-1, n-1), where D(i, j) = (a_i - b_j)^2 + min(D(i-1, j-1),
+ * D(i-1, j), D(i, j-1)) for |i - j| <= r (a Sakoe-Chiba band of half-width r),
+ * D(-1, -1) = 0 and every other cell off the grid or outside the band is +inf.
+ * Every cell is d = (double)a_i - (double)b_j, then d * d, then the sum with the
+ * minimum: one rounding each; a minimum is exact, so the value of a cell does not
+ * depend on the order in which the cells are visited. */
+double orc_dtw_sq(const float* a, const float* b, int32_t n, int32_t r) {
+  /* prev[j + 1] = D(i - 1, j), cur[j + 1] = D(i, j); index 0 is column -1 */
+  double* prev = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  double* cur = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+  for (int32_t j = 0; j <= n; ++j) prev[j] = INFINITY;
+  prev[0] = 0.0; /* D(-1, -1) */
+  for (int32_t i = 0; i < n; ++i) {
+    for (int32_t j = 0; j <= n; ++j) cur[j] = INFINITY;
+    const int32_t j0 = i - r > 0 ? i - r : 0;
+    const int32_t j1 = i + r < n - 1 ? i + r : n - 1;
+    for (int32_t j = j0; j <= j1; ++j) {
+      const double d = (double)a[i] - (double)b[j];
+      double m = prev[j];                  /* D(i-1, j-1) */
+      if (prev[j + 1] < m) m = prev[j + 1]; /* D(i-1, j)   */
+      if (cur[j] < m) m = cur[j];           /* D(i, j-1)   */
+      cur[j + 1] = d * d + m;
+    }
+    double* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  const double out = prev[n];
+  free(prev);
+  free(cur);
+  return out;
+}
+
+/* LB_Keogh envelope of q for a warping window r: U_i = max, L_i = min of
+ * q_t over |t - i| <= r (inside the series). */
+void orc_envelope(const float* q, int32_t n, int32_t r, float* U, float* L) {
+  for (int32_t i = 0; i < n; ++i) {
+    float u = q[i], l = q[i];
+    for (int32_t t = i - r; t <= i + r; ++t) {
+      if (t < 0 || t >= n) continue;
+      if (q[t] > u) u = q[t];
+      if (q[t] < l) l = q[t];
+    }
+    U[i] = u;
+    L[i] = l;
+  }
+}
+
+/* LB_Keogh(q, b)^2 = sum_i (b_i - U_i)^2 where b_i > U_i, (L_i - b_i)^2 where
+ * b_i < L_i: a lower bound of DTW^2(q, b) for the same window. */
+double orc_lb_keogh(const float* U, const float* L, const float* b, int32_t n) {
+  double acc = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    if (b[i] > U[i]) d = (double)b[i] - (double)U[i];
+    else if (b[i] < L[i]) d = (double)L[i] - (double)b[i];
+    acc += d * d;
+  }
+  return acc;
+}
+
+/* The envelope reduced per segment (Keogh's PAA envelope): Uh_j = max of U over
+ * segment j, Lh_j = min of L over it. */
+void orc_paa_envelope(const float* U, const float* L, int32_t n, int32_t w, double* Uh, double* Lh) {
+  const int32_t s = n / w;
+  for (int32_t j = 0; j < w; ++j) {
+    double u = -INFINITY, l = INFINITY;
+    for (int32_t t = j * s; t < (j + 1) * s; ++t) {
+      if ((double)U[t] > u) u = (double)U[t];
+      if ((double)L[t] < l) l = (double)L[t];
+    }
+    Uh[j] = u;
+    Lh[j] = l;
+  }
+}
+
+/* Lower bound of DTW between the query and every series whose symbols lie in
+ * [lo_j, hi_j]: sqrt(s * sum_j d_j^2), d_j the gap between the value range
+ * [beta_lo, beta_{hi+1}) and the segment's envelope interval [Lh_j, Uh_j] (0 when
+ * they meet). A series' PAA value lies in its region; the mean of a segment's points
+ * above Uh_j is at least its gap to Uh_j, and by convexity the squared gaps of the
+ * points sum to at least s times the squared gap of the mean, so this bounds
+ * LB_Keogh, which bounds DTW. */
+double orc_mindist_env(const double* Uh, const double* Lh, const uint8_t* lo, const uint8_t* hi, int32_t w,
+                       int32_t n, int32_t c, const double* beta) {
+  const double s = (double)(n / w);
+  double acc = 0.0;
+  for (int32_t j = 0; j < w; ++j) {
+    const double lower = lo[j] == 0 ? -INFINITY : beta[lo[j] - 1];
+    const double upper = hi[j] >= c - 1 ? INFINITY : beta[hi[j]];
+    double d = 0.0;
+    if (lower > Uh[j]) d = lower - Uh[j];
+    else if (upper < Lh[j]) d = Lh[j] - upper;
+    acc += d * d;
+  }
+  return sqrt(s * acc);
+}
+
+/* Exact k-NN under DTW by serial scan: the FP64 DTW^2 of every series, the k
+ * smallest by (D, id). */
+void orc_knn_scan_dtw(const float* Z, int64_t N, int32_t n, const float* zq, int32_t k, int32_t r, int64_t* ids,
+                      double* d2) {
+  int32_t nt = 1;
+#ifdef _OPENMP
+  nt = omp_get_max_threads();
+#endif
+  double* pd = (double*)malloc(sizeof(double) * (size_t)k * (size_t)nt);
+  int64_t* pi = (int64_t*)malloc(sizeof(int64_t) * (size_t)k * (size_t)nt);
+  int32_t* pc = (int32_t*)calloc((size_t)nt, sizeof(int32_t));
+#pragma omp parallel num_threads(nt)
+  {
+    int32_t me = 0;
+#ifdef _OPENMP
+    me = omp_get_thread_num();
+#endif
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i)
+      orc_topk_push(pd + (int64_t)me * k, pi + (int64_t)me * k, &pc[me], k, orc_dtw_sq(Z + i * n, zq, n, r), i);
+  }
+  int32_t cnt = 0;
+  for (int32_t th = 0; th < nt; ++th)
+    for (int32_t j = 0; j < pc[th]; ++j)
+      orc_topk_push(d2, ids, &cnt, k, pd[(int64_t)th * k + j], pi[(int64_t)th * k + j]);
+  free(pd);
+  free(pi);
+  free(pc);
+}
+
+/* Exact k-NN under DTW through the oracle's flat index (the same leaves and
+ * priority order as orc_knn_index, with the envelope bounds). */
+int64_t orc_knn_index_dtw(const float* Z, const uint8_t* words, int64_t N, int32_t n, int32_t w, int32_t c,
+                          int32_t cap, const float* zq, int32_t k, int32_t r, double slack, int64_t* ids,
+                          double* d2) {
+  return orc_knn_index_metric(Z, words, N, n, w, c, cap, zq, k, slack, r, ids, d2);
 }

@@ -291,7 +291,7 @@ def main():
         stream.synchronize()
     torch.cuda.synchronize()
     elapsed_ms = e0.elapsed_time(e1)
-    launches = msi.msi_query_stats_get(index)["kernel_launches"]  # counted by the library
+    timed_launches = msi.msi_query_stats_get(index)["kernel_launches"]  # counted by the library
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -377,7 +377,7 @@ def main():
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
                 "d2h_bytes_per_step": nq * k * 12},
-        "gpu_launches": launches,
+        "gpu_launches": timed_launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},

@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=2_000_000, help="series in the oracle's timed sample")
     p.add_argument("--cpu-queries", type=int, default=10)
     p.add_argument("--serving", action="store_true", help="Poisson-arrival serving sweep over three collections")
+    p.add_argument("--dtw", action="store_true", help="exact k-NN under DTW (window 10%%) on the same workload")
+    p.add_argument("--window", type=int, default=-1, help="DTW half-width (default len / 10)")
     p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
     p.add_argument("--serve-requests", type=int, default=3000, help="most requests per rate")
@@ -216,6 +218,79 @@ def serving(args):
     print(json.dumps(out))
 
 
+def dtw_bench(args):
+    """Exact k-NN under DTW (Section IV, MESSI with DTW) on the benchmark's collection
+    and query mix: the same index, a Sakoe-Chiba window of 10% of the length."""
+    import torch
+
+    import datagen
+    import oracle
+    import paper_2009_00786_gb300 as msi
+    dev = torch.device("cuda:0")
+    n, length, nq, k = args.n, args.len, args.queries, args.k
+    r = args.window if args.window >= 0 else length // 10
+    stream = torch.cuda.Stream()
+    X = torch.empty((n, length), dtype=torch.float32, device=dev)
+    datagen.walks_device(0, 0, n, length, X.data_ptr(), stream.cuda_stream)
+    n_fresh, ids, sig = datagen.query_plan(n, nq)
+    Q = torch.empty((nq, length), dtype=torch.float32, device=dev)
+    datagen.walks_device(1, 0, n_fresh, length, Q.data_ptr(), stream.cuda_stream)
+    ids_d, sig_d = torch.from_numpy(ids).to(dev), torch.from_numpy(sig).to(dev)
+    datagen.noisy_copies_device(0, 2, ids_d.data_ptr(), sig_d.data_ptr(), nq - n_fresh, length,
+                                Q[n_fresh:].data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    index = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=args.leaf, flags=msi.MSI_BUILD_BORROW,
+                          stream=stream)
+    for _ in range(args.warmup):
+        msi.msi_knn_dtw(index, Q, k, window=r, stream=stream)
+    stream.synchronize()
+    msi.msi_query_stats_get(index, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            msi.msi_knn_dtw(index, Q, k, window=r, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = msi.msi_query_stats_get(index, reset=True)
+    lat = []
+    qe0, qe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(nq):
+        qe0.record(stream)
+        msi.msi_knn_dtw(index, Q[i:i + 1], k, window=r, stream=stream)
+        qe1.record(stream)
+        qe1.synchronize()
+        lat.append(qe0.elapsed_time(qe1))
+    # the oracle's FP64 DTW scan on a bounded sample, scaled to the collection
+    ns = min(args.cpu_sample // 10, n)
+    Z = oracle.summarise(datagen.walks(0, 0, ns, length), 16, 256, want_paa=False)[0]
+    Qh = Q[: args.cpu_queries // 2].cpu().numpy()
+    t0 = time.perf_counter()
+    for q in Qh:
+        oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], k, r)
+    t_scan = (time.perf_counter() - t0) / len(Qh)
+    line = {
+        "metric": f"exact {k}-NN DTW queries/s and p50/p99 ms at {n // 1_000_000}M x {length} fp32 "
+                  f"(Sakoe-Chiba window {r})",
+        "value": nq * args.steps / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload(n, length, nq, k, args.leaf) + f", DTW window {r}"},
+        "plain": {"qps": nq / (sum(lat) / 1e3), "p50_ms": float(np.percentile(lat, 50)),
+                  "p99_ms": float(np.percentile(lat, 99))},
+        "gpu_launches": st["kernel_launches"],
+        "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if not kk.endswith("_ms")},
+        "clocks": clocks.summary(),
+        "cpu_baseline": {"value": 1.0 / (t_scan * n / ns), "unit": "queries/s",
+                         "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())), "kind": "oracle",
+                         "sample": f"FP64 DTW scan of {ns} of the {n} series for {len(Qh)} queries; "
+                                   f"{t_scan * 1e3:.1f} ms/query scaled x{n / ns:g}"},
+    }
+    index.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -223,6 +298,9 @@ def main():
         return
     if args.serving:
         serving(args)
+        return
+    if args.dtw:
+        dtw_bench(args)
         return
     import torch
     import torch.distributed as dist

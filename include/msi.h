@@ -135,6 +135,24 @@ MSI_API msi_status msi_knn(msi_index* index, const float* queries, int64_t nq, i
 MSI_API msi_status msi_knn_ex(msi_index* index, const float* queries, int64_t nq, int32_t k, int64_t* ids,
                               float* dists, double* sqdists64, void* stream);
 
+/*
+ * Exact k-NN under Dynamic Time Warping (Section IV, "MESSI with DTW"): the same
+ * index, searched with the LB_Keogh envelope of each query (the per-segment maximum
+ * of its upper envelope and minimum of its lower one give the iSAX lower bounds),
+ * and DTW as the real distance, with a Sakoe-Chiba warping window of half-width
+ * `window` points (the paper uses 10% of the length: window = len / 10):
+ *   DTW^2(q, y) = D(len-1, len-1),  D(i, j) = (q_i - y_j)^2 + min(D(i-1, j-1),
+ *   D(i-1, j), D(i, j-1)) for |i - j| <= window, D(-1, -1) = 0, +inf elsewhere,
+ * on the z-normalised query and series. The answer is the k smallest by (FP64
+ * DTW^2, id), like msi_knn_ex's; dists = sqrt(DTW^2) rounded to fp32 and
+ * sqdists64 = the FP64 DTW^2 (either may be NULL).
+ *   window  >= 0; values >= len mean an unconstrained warping (len - 1).
+ * Other arguments, layouts and errors as msi_knn_ex; MSI_EINVAL for a negative
+ * window.
+ */
+MSI_API msi_status msi_knn_dtw(msi_index* index, const float* queries, int64_t nq, int32_t k, int32_t window,
+                               int64_t* ids, float* dists, double* sqdists64, void* stream);
+
 /* Releases the index and all its device memory. NULL is a no-op. */
 MSI_API void msi_free(msi_index* index);
 

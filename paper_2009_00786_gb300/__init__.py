@@ -64,6 +64,7 @@ _lib.msi_build.restype = ctypes.c_int
 _lib.msi_knn.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
 _lib.msi_knn.restype = ctypes.c_int
 _lib.msi_knn_ex.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]
+_lib.msi_knn_dtw.argtypes = [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
 _lib.msi_knn_ex.restype = ctypes.c_int
 _lib.msi_free.argtypes = [_vp]
 _lib.msi_free.restype = None
@@ -225,6 +226,28 @@ def msi_knn_ex(index, queries, k, stream=None):
         d64p = ctypes.c_void_p(d64.ctypes.data)
     _check(_lib.msi_knn_ex(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, _ptr(ids, np.int64),
                            _ptr(dists, np.float32), d64p, _stream(stream)))
+    return ids, dists, d64
+
+
+def msi_knn_dtw(index, queries, k, window=None, stream=None):
+    """msi_knn_dtw: exact k-NN under DTW with a Sakoe-Chiba window of half-width
+    `window` points (default len // 10). Returns (ids, dists, sqdists64) like msi_knn_ex."""
+    if window is None:
+        window = index.len // 10
+    nq = queries.shape[0]
+    if _is_torch(queries):
+        import torch
+        ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        d64 = torch.empty((nq, k), dtype=torch.float64, device=queries.device)
+        d64p = ctypes.c_void_p(d64.data_ptr())
+    else:
+        ids = np.empty((nq, k), dtype=np.int64)
+        dists = np.empty((nq, k), dtype=np.float32)
+        d64 = np.empty((nq, k), dtype=np.float64)
+        d64p = ctypes.c_void_p(d64.ctypes.data)
+    _check(_lib.msi_knn_dtw(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, int(window),
+                            _ptr(ids, np.int64), _ptr(dists, np.float32), d64p, _stream(stream)))
     return ids, dists, d64
 
 

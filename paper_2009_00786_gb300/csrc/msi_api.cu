@@ -248,8 +248,9 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
   return msi_knn_ex(ix, queries, nq, k, ids, dists, nullptr, stream);
 }
 
-msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
-                      double* sqdists64, void* stream) {
+// window < 0: Euclidean k-NN (msi_knn_ex); window >= 0: DTW k-NN (msi_knn_dtw).
+static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t window, int64_t* ids,
+                           float* dists, double* sqdists64, void* stream) {
   g_err.clear();
   if (!ix) return fail(MSI_EINVAL, "index is NULL");
   if (nq < 0) return fail(MSI_EINVAL, "nq = %lld is negative", (long long)nq);
@@ -311,10 +312,10 @@ msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k
         const int sl = (int)(i % ix->nslots);
         e = msi::query_one(ix, ix->slots[sl], ix->nslots, qd + i * ix->len, k, id_base + i * k,
                            d_base ? d_base + i * k : nullptr, d64_base ? d64_base + i * k : nullptr, ix->ws_ovf + i,
-                           ix->slot_streams[sl], ea, em, eb);
+                           ix->slot_streams[sl], ea, em, eb, window);
       } else {
         e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
-                           d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb);
+                           d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb, window);
       }
       if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
     }
@@ -334,7 +335,7 @@ msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k
       for (int64_t i = 0; i < cnt; ++i) {
         if (!ovf[i]) continue;
         e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
-                           d64_base ? d64_base + i * k : nullptr, nullptr, s, nullptr, nullptr, nullptr);
+                           d64_base ? d64_base + i * k : nullptr, nullptr, s, nullptr, nullptr, nullptr, window);
         if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
         ++ix->overflow_reruns;
       }
@@ -375,6 +376,18 @@ msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k
     if (bad) return fail(MSI_EINVAL, "%llu queries hold NaN or infinity", bad);
   }
   return MSI_OK;
+}
+
+msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
+                      double* sqdists64, void* stream) {
+  return knn_impl(ix, queries, nq, k, -1, ids, dists, sqdists64, stream);
+}
+
+msi_status msi_knn_dtw(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t window, int64_t* ids,
+                       float* dists, double* sqdists64, void* stream) {
+  g_err.clear();
+  if (window < 0) return fail(MSI_EINVAL, "window = %d is negative", window);
+  return knn_impl(ix, queries, nq, k, window, ids, dists, sqdists64, stream);
 }
 
 void msi_free(msi_index* ix) { free_index(ix); }

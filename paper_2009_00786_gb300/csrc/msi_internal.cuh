@@ -41,7 +41,9 @@ struct IndexView {
 // Per-query device state (one instance per in-flight query).
 struct QState {
   float qpaa[16];
-  int32_t qsym[16];
+  float qup[16], qlo[16];       // per-segment interval the bounds measure gaps to: the PAA
+                                // value (Euclidean) or the envelope's [min, max] (DTW)
+  int32_t qsym[16];             // a symbol inside that interval, per segment
   unsigned long long qkey;
   uint32_t seed_a, seed_b;      // leaf-order positions refined by the approximate search
   unsigned int thr_bits;        // fp32 bits of the current k-th best squared distance
@@ -89,6 +91,8 @@ struct QueryView {
   uint32_t cand_cap;            // entries of cand / rc_d / rc_id
   uint32_t surv_cap;            // entries of surv
   uint32_t* ovf;                // per-query overflow flag written by q_finalize (or nullptr)
+  float* qenv;                  // [2][len]: LB_Keogh envelope of the query, upper then lower (DTW)
+  int window = -1;              // DTW: Sakoe-Chiba half-width; -1: Euclidean distance
   int k;
   float eps;                    // relative margin on squared distances
   float tau;                    // absolute margin on lower bounds (distance units)
@@ -283,6 +287,7 @@ struct msi_index {
   int blocks_grid = 0;
   bool grids_ready = false;  // persistent grid sizes of every refinement mode
   int grid_series = 0, grid_blocks = 0, grid_rows1 = 0, grid_rowsk = 0, grid_block_kernel = 0;
+  int grid_dtw = 0, grid_dtw_check = 0;  // DTW refinement and FP64 re-check
   size_t smem_block_kernel = 0;
   size_t refine_smem = 0;
   int refine_smem_k = -1;
@@ -332,9 +337,10 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
 void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap);
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
 void free_workspace(QueryView& qv);
+// window < 0: Euclidean distance; window >= 0: DTW with that Sakoe-Chiba half-width.
 cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
                       float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
-                      cudaEvent_t ev_m, cudaEvent_t ev_b);
+                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window = -1);
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);

@@ -114,9 +114,10 @@ __device__ __forceinline__ float word_lb2(uint4 wd, const float* Ts, int w, int 
 }
 
 // Squared iSAX lower bound of a leaf from its per-segment symbol envelope: the gap
-// between the query's PAA value and the region from the lower edge of the smallest
-// symbol to the upper edge of the largest (0 inside).
-__device__ __forceinline__ float leaf_lb2(const IndexView& ix, int64_t l, const float* paa_s,
+// between the query's interval [lo_j, up_j] (the PAA value itself for the Euclidean
+// distance, the envelope's range for DTW) and the region from the lower edge of the
+// smallest symbol to the upper edge of the largest (0 where they meet).
+__device__ __forceinline__ float leaf_lb2(const IndexView& ix, int64_t l, const float* up_s, const float* lo_s,
                                           const float* thr_lo_s, const float* thr_up_s) {
   const uint4 lo = ix.env[2 * l], hi = ix.env[2 * l + 1];
   const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
@@ -125,10 +126,10 @@ __device__ __forceinline__ float leaf_lb2(const IndexView& ix, int64_t l, const 
   for (int j = 0; j < 16; ++j) {
     if (j < ix.w) {
       const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
-      const float p = paa_s[j], lower = thr_lo_s[sl], upper = thr_up_s[sh + 1];
+      const float u = up_s[j], lq = lo_s[j], lower = thr_lo_s[sl], upper = thr_up_s[sh + 1];
       float d = 0.0f;
-      if (p < lower) d = __fsub_rn(lower, p);
-      else if (p > upper) d = __fsub_rn(p, upper);
+      if (u < lower) d = __fsub_rn(lower, u);
+      else if (lq > upper) d = __fsub_rn(lq, upper);
       acc = __fadd_rn(acc, __fmul_rn(d, d));
     }
   }
@@ -238,14 +239,53 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
   }
   __syncthreads();
   for (int t = tid; t < ix.len; t += blockDim.x) qv.qz[t] = zs[t];
+  // the interval each bound measures gaps to: the PAA value (Euclidean), or for DTW
+  // the LB_Keogh envelope reduced per segment (Keogh's PAA envelope: the max of the
+  // upper envelope and the min of the lower one over the segment, i.e. the max / min
+  // of the query over the segment widened by the warping window)
+  __shared__ float iv_up_s[16], iv_lo_s[16];
+  if (qv.window >= 0) {
+    const int r = qv.window;
+    for (int t = tid; t < ix.len; t += blockDim.x) {
+      float u = zs[t], l = zs[t];
+      const int a = max(0, t - r), b = min(ix.len - 1, t + r);
+      for (int x = a; x <= b; ++x) {
+        u = fmaxf(u, zs[x]);
+        l = fminf(l, zs[x]);
+      }
+      qv.qenv[t] = u;
+      qv.qenv[ix.len + t] = l;
+    }
+    for (int j = warp; j < ix.w; j += kThreads / 32) {
+      const int a = max(0, j * ix.seglen - r), b = min(ix.len - 1, (j + 1) * ix.seglen - 1 + r);
+      float u = -INFINITY, l = INFINITY;
+      for (int x = a + lane; x <= b; x += 32) {
+        u = fmaxf(u, zs[x]);
+        l = fminf(l, zs[x]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        u = fmaxf(u, __shfl_xor_sync(kFull, u, o));
+        l = fminf(l, __shfl_xor_sync(kFull, l, o));
+      }
+      if (lane == 0) {
+        iv_up_s[j] = u;
+        iv_lo_s[j] = l;
+      }
+    }
+  } else if (tid < ix.w) {
+    iv_up_s[tid] = paa_s[tid];
+    iv_lo_s[tid] = paa_s[tid];
+  }
+  __syncthreads();
   const int wc = ix.w * ix.card;
   for (int e = tid; e < wc; e += blockDim.x) {
     const int j = e / ix.card, v = e - j * ix.card;
-    const float p = paa_s[j];
+    const float u = iv_up_s[j], l = iv_lo_s[j];
     const float lower = thr_lo_s[v], upper = thr_up_s[v + 1];
     float d = 0.0f;
-    if (p < lower) d = __fsub_rn(lower, p);
-    else if (p > upper) d = __fsub_rn(p, upper);
+    if (u < lower) d = __fsub_rn(lower, u);
+    else if (l > upper) d = __fsub_rn(l, upper);
     qv.T[e] = __fmul_rn(d, d);
   }
   // coarse table: gap to the union of the regions sharing a 5-bit symbol prefix
@@ -255,17 +295,24 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
       const int j = e >> 5, c = e & 31;
       float d = 0.0f;
       if (c < (1 << cb)) {
-        const float p = paa_s[j];
+        const float u = iv_up_s[j], l = iv_lo_s[j];
         const float lower = thr_lo_s[c << cs], upper = thr_up_s[(c + 1) << cs];
-        if (p < lower) d = __fsub_rn(lower, p);
-        else if (p > upper) d = __fsub_rn(p, upper);
+        if (u < lower) d = __fsub_rn(lower, u);
+        else if (l > upper) d = __fsub_rn(l, upper);
       }
       qv.T5[e] = __fmul_rn(d, d);
     }
   }
   if (tid < ix.w) {
     qv.st->qpaa[tid] = paa_s[tid];
-    qv.st->qsym[tid] = sym_s[tid];
+    qv.st->qup[tid] = iv_up_s[tid];
+    qv.st->qlo[tid] = iv_lo_s[tid];
+    // a symbol whose region meets the interval (the block filter's clamp needs one):
+    // the PAA's own symbol, moved into [symbol of lo, symbol of up] for DTW
+    int sym = sym_s[tid];
+    if (qv.window >= 0)
+      sym = min(max(sym, sax_symbol(thr_up_s, ix.card, iv_lo_s[tid])), sax_symbol(thr_up_s, ix.card, iv_up_s[tid]));
+    qv.st->qsym[tid] = sym;
   }
   // approximate search: the last leaf whose first key is <= the query key
   const unsigned long long qkey = key_s;
@@ -360,12 +407,15 @@ q_seed_select(QueryView qv) {
 // ------------------------------------------------------------------ q_leaf_filter
 __global__ void __launch_bounds__(kThreads)
 q_leaf_filter(IndexView ix, QueryView qv) {
-  __shared__ float thr_up_s[257], thr_lo_s[257], paa_s[16];
+  __shared__ float thr_up_s[257], thr_lo_s[257], up_s[16], lo_s[16];
   for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
     thr_up_s[v] = ix.thr_up[v];
     thr_lo_s[v] = ix.thr_lo[v];
   }
-  if (threadIdx.x < ix.w) paa_s[threadIdx.x] = qv.st->qpaa[threadIdx.x];
+  if (threadIdx.x < ix.w) {
+    up_s[threadIdx.x] = qv.st->qup[threadIdx.x];
+    lo_s[threadIdx.x] = qv.st->qlo[threadIdx.x];
+  }
   __syncthreads();
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool keep = false;
@@ -374,7 +424,7 @@ q_leaf_filter(IndexView ix, QueryView qv) {
     const uint32_t b = ix.leaf_begin[l], e = ix.leaf_begin[l + 1];
     const uint32_t sa = qv.st->seed_a, sb = qv.st->seed_b;
     if (!(b >= sa && e <= sb)) {
-      lb2 = leaf_lb2(ix, l, paa_s, thr_lo_s, thr_up_s);
+      lb2 = leaf_lb2(ix, l, up_s, lo_s, thr_lo_s, thr_up_s);
       keep = lb2 <= lb_bound2(qv.st->thr_bits, qv.eps, qv.tau);
     }
   }
@@ -429,18 +479,13 @@ q_leaf_filter(IndexView ix, QueryView qv) {
   }
 }
 
-// The lowest-bound surviving leaf, refined before the block and series filters so
-// that they run against a tighter BSF (the priority order of ProcessQueue,
-// Algorithm 8: the most promising leaf first). Every block finds the same leaf from
-// the leaf filter's per-block minima; warps take its positions in a stride. A leaf
-// whose bound already exceeds the BSF is skipped; its positions are excluded from
-// the later passes like the seed's.
-__global__ void __launch_bounds__(kThreads)
-q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
-  extern __shared__ __align__(16) float qs[];
+// The lowest (bound bits << 32 | leaf) key over the leaf filter's per-block minima,
+// in every thread of the block; ~0 when no leaf survived or when the leaf's bound
+// exceeds the BSF as thread 0 reads it (one reading for the whole block, so that the
+// block takes one decision).
+__device__ unsigned long long front_key(const QueryView& qv, uint32_t nblockmin) {
   __shared__ unsigned long long s_best;
-  __shared__ unsigned s_min;
-  smem_fill(qs, qv.qz, ix.len);
+  __shared__ unsigned s_thr;
   unsigned long long best = ~0ull;
   for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
     const unsigned long long v = qv.blockmin[i];
@@ -453,16 +498,31 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   }
   if (threadIdx.x == 0) {
     s_best = ~0ull;
-    s_min = 0x7f800000u;
+    s_thr = *(volatile unsigned*)&qv.st->thr_bits;
   }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) atomicMin(&s_best, best);
   __syncthreads();
   best = s_best;
+  if (best != ~0ull && __uint_as_float((uint32_t)(best >> 32)) > lb_bound2(s_thr, qv.eps, qv.tau)) best = ~0ull;
+  return best;
+}
+
+// The lowest-bound surviving leaf, refined before the block and series filters so
+// that they run against a tighter BSF (the priority order of ProcessQueue,
+// Algorithm 8: the most promising leaf first). Every block finds the same leaf from
+// the leaf filter's per-block minima; warps take its positions in a stride. A leaf
+// whose bound already exceeds the BSF is skipped; its positions are excluded from
+// the later passes like the seed's.
+__global__ void __launch_bounds__(kThreads)
+q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
+  extern __shared__ __align__(16) float qs[];
+  __shared__ unsigned s_min;
+  smem_fill(qs, qv.qz, ix.len);
+  if (threadIdx.x == 0) s_min = 0x7f800000u;
+  const unsigned long long best = front_key(qv, nblockmin);
   QState* st = qv.st;
-  if (best == ~0ull) return;
-  const float lb2 = __uint_as_float((uint32_t)(best >> 32));
-  if (lb2 > lb_bound2(*(volatile unsigned*)&st->thr_bits, qv.eps, qv.tau)) return;
+  if (best == ~0ull) return;  // the same in every thread of the block
   const uint32_t l = (uint32_t)best;
   const uint32_t a = ix.leaf_begin[l], b = ix.leaf_begin[l + 1];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1076,11 +1136,13 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
   __shared__ uint32_t hist[256], sel[2], s_cnt;
   if (threadIdx.x == 0 && qv.ovf) *qv.ovf = qv.st->overflow;
   if (qv.st->overflow) return;  // the query is run again with room for all n
-  final_select(qv, hist, sel);
-  __syncthreads();
-  static_assert(sizeof(sk) >= 4 * 1024 * sizeof(uint32_t), "re-check list must hold 4 * blockDim entries");
-  recheck(ix, qv, reinterpret_cast<uint32_t*>(sk), &s_cnt);
-  __syncthreads();
+  if (qv.window < 0) {  // DTW: q_final_pick and q_recheck_dtw did this part
+    final_select(qv, hist, sel);
+    __syncthreads();
+    static_assert(sizeof(sk) >= 4 * 1024 * sizeof(uint32_t), "re-check list must hold 4 * blockDim entries");
+    recheck(ix, qv, reinterpret_cast<uint32_t*>(sk), &s_cnt);
+    __syncthreads();
+  }
   const uint32_t R = qv.st->rc_count;
   const int k = qv.k;
   int nsort;
@@ -1201,16 +1263,319 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
   }
 }
 
+// ------------------------------------------------------------------ DTW
+// Section IV, "MESSI with DTW": the index is unchanged; the bounds measure gaps to
+// the query's LB_Keogh envelope (q_prep), and real distances are DTW distances with a
+// Sakoe-Chiba band of half-width r: D(i, j) = (q_i - y_j)^2 + min(D(i-1, j-1),
+// D(i-1, j), D(i, j-1)) for |i - j| <= r, D(-1, -1) = 0, +inf elsewhere; the
+// distance is D(n-1, n-1). The kernels below mirror q_seed, q_front and the row
+// refinement with a warp per candidate: the candidate's z values are staged in the
+// warp's slice of shared memory, screened by LB_Keogh, then run through the band.
+constexpr int kDtwWarps = 4;
+
+// Shared memory of the DTW kernels for series of `len` points: the query, its
+// envelope (upper, lower) and per warp a candidate row and a boundary row, in fp32;
+// the FP64 re-check holds the query and per warp a row (fp32) and a boundary (FP64).
+__host__ __device__ inline size_t dtw_smem(int len) { return sizeof(float) * (size_t)((len + 3) & ~3) * (3 + 2 * kDtwWarps); }
+__host__ __device__ inline size_t dtw_check_smem(int len) {
+  return sizeof(float) * (size_t)((len + 3) & ~3) * (1 + 3 * kDtwWarps);
+}
+
+template <typename V>
+__device__ __forceinline__ V dtw_cell(float x, float y, V m);
+template <>
+__device__ __forceinline__ float dtw_cell<float>(float x, float y, float m) {
+  const float d = __fsub_rn(x, y);
+  return __fmaf_rn(d, d, m);
+}
+// FP64: d = x - y, d * d, + m, one rounding each and no fused operation: the same
+// bits as a sequential evaluation of the recurrence (a minimum is exact, so the order
+// in which cells are visited does not change a cell's value).
+template <>
+__device__ __forceinline__ double dtw_cell<double>(float x, float y, double m) {
+  const double d = __dsub_rn((double)x, (double)y);
+  return __dadd_rn(__dmul_rn(d, d), m);
+}
+
+// Banded DTW^2 of the query (qs) and a staged candidate (ys), one warp, as a systolic
+// wavefront over stripes of 32 query points: lane l owns row i = i0 + l and at step t
+// computes the cell (i, jbeg + t - l). The cell above, D(i-1, j), is the value lane
+// l - 1 computed one step earlier (a shuffle); the diagonal one, D(i-1, j-1), is the
+// value received from lane l - 1 the step before; the left one is the lane's own
+// previous value. Lane 0 takes both from `edge`, the last row of the previous stripe,
+// which lane 31 writes as it goes (each entry after lane 0 has read it). A stripe
+// whose last row has no cell at or below `abandon` ends the computation with +inf:
+// every warping path crosses that row and the cells after it add non-negative terms.
+template <typename V>
+__device__ V warp_dtw(const float* qs, const float* ys, V* edge, int n, int r, V abandon) {
+  const int lane = threadIdx.x & 31;
+  const V inf = (V)INFINITY;
+  for (int j = lane; j < n; j += 32) edge[j] = inf;
+  __syncwarp();
+  V result = inf;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const int last = min(n - 1, i0 + 31);
+    const int jbeg = max(0, i0 - r), jend = min(n - 1, last + r);
+    const int steps = jend - jbeg + 1 + (last - i0);
+    const bool row = i < n;
+    const float x = row ? qs[i] : 0.0f;
+    const int jlo = max(0, i - r), jhi = min(n - 1, i + r);
+    const bool writer = lane == 31 && i0 + 32 < n;
+    V prev = inf, upd = inf, rowmin = inf;
+    for (int t = 0; t < steps; ++t) {
+      const int j = jbeg + t - lane;
+      V up = __shfl_up_sync(kFull, prev, 1);
+      V diag = upd;
+      if (lane == 0) {
+        up = j < n ? edge[j] : inf;  // j >= 0 for lane 0
+        diag = j >= 1 && j <= n ? edge[j - 1] : (i0 == 0 && j == 0 ? (V)0 : inf);
+      }
+      V cur = inf;
+      if (row && j >= jlo && j <= jhi) {
+        V m = diag < up ? diag : up;
+        m = prev < m ? prev : m;
+        cur = dtw_cell<V>(x, ys[j], m);
+        rowmin = cur < rowmin ? cur : rowmin;
+        if (i == n - 1 && j == n - 1) result = cur;
+      }
+      if (writer && j >= 0 && j < n) edge[j] = cur;
+      prev = cur;
+      upd = up;
+    }
+    __syncwarp();
+    if (i0 + 32 < n && __shfl_sync(kFull, rowmin, 31) > abandon) return inf;
+  }
+  return __shfl_sync(kFull, result, (n - 1) & 31);
+}
+
+// The z-normalised values of series `id` into the warp's slice (16-byte aligned).
+__device__ __forceinline__ void stage_row(const IndexView& ix, uint32_t id, float2 ms, float* ys) {
+  const int lane = threadIdx.x & 31;
+  const float* row = ix.data + (size_t)id * ix.len;
+  if ((ix.len & 3) == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    float4* y4 = reinterpret_cast<float4*>(ys);
+    for (int c = lane; c < (ix.len >> 2); c += 32) {
+      float4 v = __ldg(r4 + c);
+      if (!ix.data_is_z) {
+        v.x = znorm_value(v.x, ms.x, ms.y);
+        v.y = znorm_value(v.y, ms.x, ms.y);
+        v.z = znorm_value(v.z, ms.x, ms.y);
+        v.w = znorm_value(v.w, ms.x, ms.y);
+      }
+      y4[c] = v;
+    }
+  } else {
+    for (int t = lane; t < ix.len; t += 32) {
+      const float v = __ldg(row + t);
+      ys[t] = ix.data_is_z ? v : znorm_value(v, ms.x, ms.y);
+    }
+  }
+  __syncwarp();
+}
+
+// Real DTW distances of the approximate-search leaf's members (the initial BSF).
+// k = 1: each distance abandons above the best so far, which is tightened as the
+// members finish; k > 1: every member's full distance (the k-th is picked from them).
+__global__ void __launch_bounds__(kDtwWarps * 32)
+q_seed_dtw(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float sm[];
+  const int n4 = (ix.len + 3) & ~3, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qs = sm;
+  float* ys = qs + 3 * n4 + warp * 2 * n4;
+  float* edge = ys + n4;
+  smem_fill(qs, qv.qz, ix.len);
+  __syncthreads();
+  QState* st = qv.st;
+  volatile unsigned int* thr_v = &st->thr_bits;
+  const uint32_t a = st->seed_a, b = st->seed_b;
+  for (uint32_t gw = blockIdx.x * kDtwWarps + warp; gw < b - a; gw += gridDim.x * kDtwWarps) {
+    const uint32_t pos = a + gw;
+    stage_row(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    const float ab = qv.k == 1 ? keep_bound2(thr, qv.eps) : INFINITY;
+    const float d2 = warp_dtw<float>(qs, ys, edge, ix.len, qv.window, ab);
+    if (lane == 0) {
+      if (gw < qv.cand_cap) qv.cand[gw] = pack(d2, pos);
+      else st->overflow = 1u;
+      if (qv.k == 1 && __float_as_uint(d2) < thr) atomicMin(&st->thr_bits, __float_as_uint(d2));
+    }
+    __syncwarp();
+  }
+}
+
+// The lowest-bound surviving leaf under DTW (as q_front): refined before the filters,
+// its positions excluded from them.
+__global__ void __launch_bounds__(kDtwWarps * 32)
+q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
+  extern __shared__ __align__(16) float sm[];
+  const int n4 = (ix.len + 3) & ~3, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qs = sm;
+  float* ys = qs + 3 * n4 + warp * 2 * n4;
+  float* edge = ys + n4;
+  smem_fill(qs, qv.qz, ix.len);
+  const unsigned long long best = front_key(qv, nblockmin);  // synchronises the block
+  QState* st = qv.st;
+  if (best == ~0ull) return;  // the same in every thread of the block
+  volatile unsigned int* thr_v = &st->thr_bits;
+  const uint32_t l = (uint32_t)best;
+  const uint32_t fa = ix.leaf_begin[l], fb = ix.leaf_begin[l + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->front_a = fa;
+    st->front_b = fb;
+  }
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  __shared__ unsigned s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  uint32_t n_front = 0;
+  for (uint32_t pos = fa + blockIdx.x * kDtwWarps + warp; pos < fb; pos += gridDim.x * kDtwWarps) {
+    if (pos >= sa && pos < sb) continue;  // already refined by the seed
+    stage_row(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    const float keep2 = keep_bound2(thr, qv.eps);
+    const float d2 = warp_dtw<float>(qs, ys, edge, ix.len, qv.window, keep2);
+    if (lane == 0) {
+      ++n_front;
+      if (d2 <= keep2) {
+        const uint32_t slot = atomicAdd(&st->cand_count, 1u);
+        if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, pos);
+        else st->overflow = 1u;
+        if (qv.k == 1 && __float_as_uint(d2) < thr) atomicMin(&st->thr_bits, __float_as_uint(d2));
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && n_front) atomicAdd(&s_n, n_front);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_n) atomicAdd(&st->series_refined, s_n);
+}
+
+// One warp per survivor of the series filter: re-test its bound against the current
+// BSF, stage its row, screen it by LB_Keogh against the envelope, then its DTW
+// distance (abandoned above the keep bound). The BSF: an atomicMin for k = 1; for
+// k <= 32 the warp keeps its k best in registers and publishes its k-th; above 32 the
+// seed's k-th stays the bound.
+template <bool KONE>
+__global__ void __launch_bounds__(kDtwWarps * 32)
+q_refine_dtw(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float sm[];
+  const int n = ix.len, n4 = (n + 3) & ~3, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qs = sm;
+  float* qU = qs + n4;
+  float* qL = qU + n4;
+  float* ys = qL + n4 + warp * 2 * n4;
+  float* edge = ys + n4;
+  smem_fill(qs, qv.qz, n);
+  smem_fill(qU, qv.qenv, n);
+  smem_fill(qL, qv.qenv + n, n);
+  __syncthreads();
+  QState* st = qv.st;
+  volatile unsigned int* thr_v = &st->thr_bits;
+  const uint32_t nsurv = st->overflow ? 0u : min(st->surv_count, qv.surv_cap);
+  const int k = qv.k;
+  unsigned mine = 0x7f800000u;  // lanes < k: this warp's k best, ascending (1 < k <= 32)
+  uint32_t n_ref = 0;
+  const uint32_t gw = blockIdx.x * kDtwWarps + warp;
+  for (uint32_t sidx = gw; sidx < nsurv; sidx += gridDim.x * kDtwWarps) {
+    const uint2 sv = qv.surv[sidx];
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+    if (__uint_as_float(sv.y) > lb_bound2(thr, qv.eps, qv.tau)) continue;
+    stage_row(ix, ix.perm[sv.x], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[sv.x], ys);
+    const float keep2 = keep_bound2(thr, qv.eps);
+    // LB_Keogh^2 in fp32 (relative error below eps); screened with a factor (1 + eps)
+    float acc = 0.0f;
+    for (int t = lane; t < n; t += 32) {
+      const float y = ys[t], u = qU[t], l = qL[t];
+      const float d = y > u ? __fsub_rn(y, u) : (y < l ? __fsub_rn(l, y) : 0.0f);
+      acc = __fmaf_rn(d, d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (acc > __fmul_ru(keep2, 1.0f + qv.eps)) {
+      __syncwarp();
+      continue;
+    }
+    ++n_ref;
+    const float d2 = warp_dtw<float>(qs, ys, edge, n, qv.window, keep2);
+    if (lane == 0 && d2 <= keep2) {
+      const uint32_t slot = atomicAdd(&st->cand_count, 1u);
+      if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, sv.x);
+      else st->overflow = 1u;
+    }
+    const unsigned v = __float_as_uint(d2);
+    if (KONE) {
+      if (lane == 0 && v < thr) atomicMin(&st->thr_bits, v);
+    } else if (k <= 32 && v < __shfl_sync(kFull, mine, k - 1)) {
+      const int p = __popc(__ballot_sync(kFull, lane < k && mine <= v));
+      const unsigned upv = __shfl_up_sync(kFull, mine, 1);
+      if (lane >= p && lane < k) mine = lane == p ? v : upv;
+      const unsigned kth = __shfl_sync(kFull, mine, k - 1);
+      if (lane == 0 && kth < thr) atomicMin(&st->thr_bits, kth);
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && gw < kMaxRefineWarps) qv.partials[kMaxRefineWarps + gw] = n_ref;
+}
+
+// The k-th smallest candidate and the re-check bound (one block of 1024).
+__global__ void __launch_bounds__(1024)
+q_final_pick(QueryView qv) {
+  __shared__ uint32_t hist[256], sel[2];
+  if (qv.st->overflow) return;
+  final_select(qv, hist, sel);
+}
+
+// FP64 DTW of every candidate at or below the re-check bound: each warp takes 32
+// candidates at a time and computes those that pass, one after another.
+__global__ void __launch_bounds__(kDtwWarps * 32)
+q_recheck_dtw(IndexView ix, QueryView qv) {
+  extern __shared__ __align__(16) float sm[];
+  const int n4 = (ix.len + 3) & ~3, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qs = sm;
+  float* ys = qs + n4 + warp * 3 * n4;
+  double* edge = reinterpret_cast<double*>(ys + n4);  // 16-byte aligned: n4 is a multiple of 4
+  if (qv.st->overflow) return;
+  smem_fill(qs, qv.qz, ix.len);
+  __syncthreads();
+  const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
+  const uint32_t bound = qv.st->final_bits;
+  const uint32_t warps = gridDim.x * kDtwWarps;
+  for (uint32_t base = (blockIdx.x * kDtwWarps + warp) * 32; base < count; base += warps * 32) {
+    const uint32_t i = base + lane;
+    const unsigned long long c = i < count ? qv.cand[i] : ~0ull;
+    unsigned m = __ballot_sync(kFull, i < count && (uint32_t)(c >> 32) <= bound);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const uint32_t pos = (uint32_t)__shfl_sync(kFull, c, src);
+      const uint32_t id = ix.perm[pos];
+      stage_row(ix, id, ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
+      const double d = warp_dtw<double>(qs, ys, edge, ix.len, qv.window, (double)INFINITY);
+      if (lane == 0) {
+        const uint32_t slot = atomicAdd(&qv.st->rc_count, 1u);
+        qv.rc_d[slot] = d;
+        qv.rc_id[slot] = id;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // ------------------------------------------------------------------ lower bounds
 __global__ void __launch_bounds__(kThreads)
 q_lb_all(IndexView ix, QueryView qv, float* __restrict__ series_lb, float* __restrict__ leaf_lb) {
-  __shared__ float thr_up_s[257], thr_lo_s[257], paa_s[16];
+  __shared__ float thr_up_s[257], thr_lo_s[257], up_s[16], lo_s[16];
   extern __shared__ float Ts[];
   for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
     thr_up_s[v] = ix.thr_up[v];
     thr_lo_s[v] = ix.thr_lo[v];
   }
-  if (threadIdx.x < ix.w) paa_s[threadIdx.x] = qv.st->qpaa[threadIdx.x];
+  if (threadIdx.x < ix.w) {
+    up_s[threadIdx.x] = qv.st->qup[threadIdx.x];
+    lo_s[threadIdx.x] = qv.st->qlo[threadIdx.x];
+  }
   smem_fill(Ts, qv.T, ix.w * ix.card);
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1219,7 +1584,7 @@ q_lb_all(IndexView ix, QueryView qv, float* __restrict__ series_lb, float* __res
       series_lb[ix.perm[p]] = __fsqrt_rn(word_lb2(ix.words[p], Ts, ix.w, ix.card, (float)ix.seglen));
   if (leaf_lb)
     for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L; l += stride)
-      leaf_lb[l] = __fsqrt_rn(leaf_lb2(ix, l, paa_s, thr_lo_s, thr_up_s));
+      leaf_lb[l] = __fsqrt_rn(leaf_lb2(ix, l, up_s, lo_s, thr_lo_s, thr_up_s));
 }
 
 // z-normalised collection in collection order, from the index's storage.
@@ -1263,6 +1628,8 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   if ((e = dalloc(&qv.rc_d, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_id, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.surv, (size_t)surv_cap)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.qenv, 2 * (size_t)ix->len)) != cudaSuccess) return e;
+  qv.window = -1;
   qv.cand_cap = cand_cap;
   qv.surv_cap = surv_cap;
   qv.ovf = nullptr;
@@ -1275,13 +1642,13 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
 // Device bytes of one query workspace (alloc_workspace).
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap) {
   const int64_t items = ix->n / kItem + 2 * ix->L + 2;
-  return (int64_t)(ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
+  return (int64_t)(3 * ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
          items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
 
 void free_workspace(QueryView& qv) {
   void* ptrs[] = {qv.qz, qv.T, qv.T5, qv.st, qv.leaf_list, qv.leaf_lb2, qv.items, qv.blks, qv.partials,
-                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv};
+                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv, qv.qenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   qv = QueryView{};
@@ -1305,6 +1672,16 @@ cudaError_t query_setup(msi_index* ix) {
   const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
   if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
+  // DTW kernels: room for the longest series (the attribute is a ceiling only)
+  const int dtw_max = (int)dtw_smem(MSI_MAX_LEN), chk_max = (int)dtw_check_smem(MSI_MAX_LEN);
+  if ((e = cudaFuncSetAttribute(q_seed_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, dtw_max)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(q_front_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, dtw_max)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(q_refine_dtw<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dtw_max)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(q_refine_dtw<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dtw_max)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(q_recheck_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, chk_max)) != cudaSuccess)
+    return e;
   ix->ws_ready = true;
   return cudaSuccess;
 }
@@ -1382,6 +1759,14 @@ static cudaError_t refine_config(msi_index* ix, int k) {
       return e;
     ix->grid_block_kernel = std::max(1, per_sm) * sms;
     ix->smem_block_kernel = bsmem;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_dtw<false>, kDtwWarps * 32,
+                                                           dtw_smem(ix->len))) != cudaSuccess)
+      return e;
+    ix->grid_dtw = std::max(1, per_sm) * sms;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_recheck_dtw, kDtwWarps * 32,
+                                                           dtw_check_smem(ix->len))) != cudaSuccess)
+      return e;
+    ix->grid_dtw_check = std::max(1, per_sm) * sms;
     ix->grids_ready = true;
   }
   if (mode) {
@@ -1400,15 +1785,69 @@ static cudaError_t refine_config(msi_index* ix, int k) {
 
 // One query (device pointers), stream-ordered. ev_a / ev_m / ev_b, when given,
 // bracket the series filter and the row refinement.
+// The DTW chain: q_prep (envelope), q_seed_dtw, [q_seed_select], q_leaf_filter,
+// q_front_dtw, [q_seed_select], q_filter_blocks, q_filter_series (the Euclidean
+// filters run unchanged on the envelope's tables), q_refine_dtw, q_final_pick,
+// q_recheck_dtw, q_finalize.
+static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const float* q_dev, int k, int64_t* ids_dev,
+                                 float* dists_dev, double* d64_dev, cudaStream_t s, cudaEvent_t ev_a,
+                                 cudaEvent_t ev_m, cudaEvent_t ev_b, int window) {
+  cudaError_t e = refine_config(ix, 1);  // the filters' grids
+  if (e != cudaSuccess) return e;
+  qv.window = std::min(window, ix->len - 1);
+  // fp32 DTW sums up to 2 len - 1 cells along a path: relative error below
+  // (2 len + 2) 2^-24; the margin covers twice that (both the BSF and the candidate)
+  qv.eps = std::max(1.52587890625e-05f, (float)(4 * ix->len + 16) * 5.9604644775390625e-08f);
+  const int series_grid = std::max(1, ix->grid_series / share);
+  const int blocks_grid = std::max(1, ix->grid_blocks / share);
+  const int dtw_grid = std::max(1, ix->grid_dtw / share);
+  const int chk_grid = std::max(1, std::min(ix->grid_dtw_check / share, (int)((qv.cand_cap + 127) / 128)));
+  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)series_grid * kFiltWarps, kMaxRefineWarps);
+  qv.npartials_rows = (uint32_t)std::min<int64_t>((int64_t)dtw_grid * kDtwWarps, kMaxRefineWarps);
+  const IndexView v = ix->view();
+  const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  const size_t dsm = dtw_smem(ix->len), csm = dtw_check_smem(ix->len);
+  const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+  q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
+  const int64_t seed_max = std::max<int64_t>(ix->cap, k);
+  q_seed_dtw<<<(unsigned)std::min<int64_t>((seed_max + kDtwWarps - 1) / kDtwWarps, 1024), kDtwWarps * 32, dsm, s>>>(
+      v, qv);
+  if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
+  const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
+  q_leaf_filter<<<nlf, kThreads, 0, s>>>(v, qv);
+  q_front_dtw<<<(unsigned)std::min<int64_t>((ix->cap + kDtwWarps - 1) / kDtwWarps, 512), kDtwWarps * 32, dsm, s>>>(
+      v, qv, nlf);
+  if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
+  if (ev_a) cudaEventRecord(ev_a, s);
+  q_filter_blocks<<<blocks_grid, kBlkThreads, fsmem, s>>>(v, qv);
+  q_filter_series<<<series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
+  if (ev_m) cudaEventRecord(ev_m, s);
+  if (k == 1) q_refine_dtw<true><<<dtw_grid, kDtwWarps * 32, dsm, s>>>(v, qv);
+  else q_refine_dtw<false><<<dtw_grid, kDtwWarps * 32, dsm, s>>>(v, qv);
+  if (ev_b) cudaEventRecord(ev_b, s);
+  q_final_pick<<<1, 1024, 0, s>>>(qv);
+  q_recheck_dtw<<<chk_grid, kDtwWarps * 32, csm, s>>>(v, qv);
+  q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev, d64_dev);
+  ix->kernel_launches += 10 + (k > 1 ? 2 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
                       float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
-                      cudaEvent_t ev_m, cudaEvent_t ev_b) {
+                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window) {
+  share = std::max(1, share);
+  if (window >= 0) {
+    QueryView qv = ws;
+    qv.k = k;
+    qv.ovf = ovf;
+    return query_one_dtw(ix, qv, share, q_dev, k, ids_dev, dists_dev, d64_dev, s, ev_a, ev_m, ev_b, window);
+  }
   cudaError_t e = refine_config(ix, k);
   if (e != cudaSuccess) return e;
   QueryView qv = ws;
   qv.k = k;
   qv.ovf = ovf;
-  share = std::max(1, share);
+  qv.window = -1;
   const int refine_grid = std::max(1, ix->refine_grid / share);
   const int rows_grid = std::max(1, ix->rows_grid / share);
   const int blocks_grid = std::max(1, ix->blocks_grid / share);
@@ -1457,6 +1896,7 @@ cudaError_t lower_bounds_on(const msi_index* ix, const QueryView& qv_in, const f
                             float* leaf_lb_dev, cudaStream_t s) {
   QueryView qv = qv_in;
   qv.k = 1;
+  qv.window = -1;  // Euclidean bounds
   const IndexView v = ix->view();
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, 1);

@@ -84,6 +84,11 @@ def test_knn_and_helpers_reject_null_index(msi):
     q = np.zeros(256, np.float32)
     assert lib.msi_knn(None, ctypes.c_void_p(q.ctypes.data), 1, 1, ctypes.c_void_p(ids.ctypes.data), None, None) == msi.MSI_EINVAL
     assert "NULL" in msi.msi_last_error()
+    qp, ip = ctypes.c_void_p(q.ctypes.data), ctypes.c_void_p(ids.ctypes.data)
+    assert lib.msi_knn_dtw(None, qp, 1, 1, 25, ip, None, None, None) == msi.MSI_EINVAL
+    assert "NULL" in msi.msi_last_error()
+    assert lib.msi_knn_dtw(None, qp, 1, 1, -1, ip, None, None, None) == msi.MSI_EINVAL
+    assert "negative" in msi.msi_last_error()
     info = msi._IndexInfo()
     assert lib.msi_index_info_get(None, ctypes.byref(info)) == msi.MSI_EINVAL
     assert lib.msi_set_timing(None, 1) == msi.MSI_EINVAL

@@ -92,3 +92,29 @@ def test_full_scan_of_sampled_queries(setup):
     for j, i in enumerate(picks):
         assert ids[i, 0] == best[j][1], f"query {i}: {ids[i, 0]} vs oracle {best[j][1]}"
         np.testing.assert_allclose(dists[i, 0], np.sqrt(best[j][0]), rtol=1e-4)
+
+
+def test_dtw_at_full_size_against_sampled_scans(setup):
+    """msi_knn_dtw over the full collection (window 10%): the returned FP64 DTW^2
+    equals the oracle's for the returned id, no series of 40 sampled blocks (327K
+    series, regenerated on the host) comes before the answer in (DTW^2, id) order, and
+    a noisy member is never closer than the answer."""
+    msi, index, ids, dists, Q, n_fresh, members = setup
+    picks = [0, 1, n_fresh + 1, n_fresh]  # two fresh walks, sigma = 0.1 and 0.01 copies
+    r = LEN // 10
+    ids_d, d_d, d64_d = msi.msi_knn_dtw(index, Q[picks], 1, window=r)
+    zqs = [oracle.znorm(Q[i])[0] for i in picks]
+    for j, zq in enumerate(zqs):
+        zi = oracle.znorm(datagen.walks(0, int(ids_d[j, 0]), 1, LEN)[0])[0]
+        assert oracle.dtw_sq(zi, zq, r) == d64_d[j, 0]
+        assert d_d[j, 0] == np.float32(np.sqrt(d64_d[j, 0]))
+        if picks[j] >= n_fresh:
+            zm = oracle.znorm(datagen.walks(0, int(members[picks[j] - n_fresh]), 1, LEN)[0])[0]
+            assert d64_d[j, 0] <= oracle.dtw_sq(zm, zq, r)
+    rng = np.random.default_rng(17)
+    for start in rng.integers(0, N - 8192, size=40):
+        Z = oracle.summarise(datagen.walks(0, int(start), 8192, LEN), 16, 256, want_paa=False)[0]
+        for j, zq in enumerate(zqs):
+            oid, od2 = oracle.knn_scan_dtw(Z, zq, 1, r)
+            assert (od2[0], int(oid[0]) + int(start)) >= (d64_d[j, 0], int(ids_d[j, 0])), \
+                f"query {picks[j]}: series {int(oid[0]) + int(start)} beats the answer"

@@ -123,6 +123,8 @@ void free_index(msi_index* ix) {
 
 namespace msi {
 void set_last_error(const char* what) { g_err = what; }
+void destroy_index(msi_index* ix) { free_index(ix); }
+void breakpoint_edges(int card, float* up, float* lo) { region_edges(card, up, lo); }
 }  // namespace msi
 
 extern "C" {
@@ -281,7 +283,8 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
   }
   const bool host_out = !ids_dev || !d_dev || !d64_dev;
   // several queries of at most 32 neighbours run concurrently on the query slots
-  const bool batched = nq > 1 && k <= 32 && ix->nslots > 1 && !ix->timing;
+  // (DTW queries use the full workspace: their survivor lists outgrow a slot's)
+  const bool batched = nq > 1 && k <= 32 && ix->nslots > 1 && !ix->timing && window < 0;
   if (batched && (e = msi::slots_setup(ix)) != cudaSuccess) return cuda_fail(e, "allocating query slots");
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t cnt = std::min<int64_t>(chunk, nq - c0);

@@ -1306,8 +1306,13 @@ __device__ __forceinline__ double dtw_cell<double>(float x, float y, double m) {
 // which lane 31 writes as it goes (each entry after lane 0 has read it). A stripe
 // whose last row has no cell at or below `abandon` ends the computation with +inf:
 // every warping path crosses that row and the cells after it add non-negative terms.
+// With `cb` (one entry per stripe), a stripe also ends it when its last row's minimum
+// plus cb[stripe] exceeds `abandon_cb`: cb holds the LB_Keogh terms of the columns a
+// path can only reach in later rows, each of which it visits at least once at a cost
+// of at least its term (the cumulative bound of Rakthanmanon et al., KDD 2012).
 template <typename V>
-__device__ V warp_dtw(const float* qs, const float* ys, V* edge, int n, int r, V abandon) {
+__device__ V warp_dtw(const float* qs, const float* ys, V* edge, int n, int r, V abandon,
+                      const float* cb = nullptr, float abandon_cb = INFINITY) {
   const int lane = threadIdx.x & 31;
   const V inf = (V)INFINITY;
   for (int j = lane; j < n; j += 32) edge[j] = inf;
@@ -1344,7 +1349,11 @@ __device__ V warp_dtw(const float* qs, const float* ys, V* edge, int n, int r, V
       upd = up;
     }
     __syncwarp();
-    if (i0 + 32 < n && __shfl_sync(kFull, rowmin, 31) > abandon) return inf;
+    if (i0 + 32 < n) {
+      const V m31 = __shfl_sync(kFull, rowmin, 31);
+      if (m31 > abandon) return inf;
+      if (cb && __fadd_rn((float)m31, cb[i0 >> 5]) > abandon_cb) return inf;
+    }
   }
   return __shfl_sync(kFull, result, (n - 1) & 31);
 }
@@ -1478,27 +1487,55 @@ q_refine_dtw(IndexView ix, QueryView qv) {
   unsigned mine = 0x7f800000u;  // lanes < k: this warp's k best, ascending (1 < k <= 32)
   uint32_t n_ref = 0;
   const uint32_t gw = blockIdx.x * kDtwWarps + warp;
+  const int r = qv.window, nstripes = (n + 31) >> 5;
+  __shared__ float cb_s[kDtwWarps][MSI_MAX_LEN / 32];
+  float* cb = cb_s[warp];
   for (uint32_t sidx = gw; sidx < nsurv; sidx += gridDim.x * kDtwWarps) {
     const uint2 sv = qv.surv[sidx];
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
     if (__uint_as_float(sv.y) > lb_bound2(thr, qv.eps, qv.tau)) continue;
     stage_row(ix, ix.perm[sv.x], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[sv.x], ys);
     const float keep2 = keep_bound2(thr, qv.eps);
-    // LB_Keogh^2 in fp32 (relative error below eps); screened with a factor (1 + eps)
+    // LB_Keogh^2 in fp32 (relative error below eps); screened with a factor (1 + eps).
+    // The terms go to `edge` (free until the DTW starts) for the cumulative bound.
+    const float keep_lb = __fmul_ru(keep2, 1.0f + qv.eps);
     float acc = 0.0f;
     for (int t = lane; t < n; t += 32) {
       const float y = ys[t], u = qU[t], l = qL[t];
       const float d = y > u ? __fsub_rn(y, u) : (y < l ? __fsub_rn(l, y) : 0.0f);
-      acc = __fmaf_rn(d, d, acc);
+      const float term = __fmul_rn(d, d);
+      edge[t] = term;
+      acc = __fadd_rn(acc, term);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (acc > __fmul_ru(keep2, 1.0f + qv.eps)) {
+    if (acc > keep_lb) {
       __syncwarp();
       continue;
     }
+    // suffix sums of the terms, 32 at a time from the end; then per stripe the sum
+    // over the columns beyond its band (j >= 32 (stripe + 1) + r)
+    __syncwarp();
+    float run = 0.0f;
+    for (int c0 = (n - 1) & ~31; c0 >= 0; c0 -= 32) {
+      float v = c0 + lane < n ? edge[c0 + lane] : 0.0f;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(kFull, v, o);
+        if (lane + o < 32) v = __fadd_rn(v, y);
+      }
+      v = __fadd_rn(v, run);
+      if (c0 + lane < n) edge[c0 + lane] = v;
+      run = __shfl_sync(kFull, v, 0);
+    }
+    __syncwarp();
+    for (int st_i = lane; st_i < nstripes; st_i += 32) {
+      const int j = 32 * (st_i + 1) + r;
+      cb[st_i] = j < n ? edge[j] : 0.0f;
+    }
+    __syncwarp();
     ++n_ref;
-    const float d2 = warp_dtw<float>(qs, ys, edge, n, qv.window, keep2);
+    const float d2 = warp_dtw<float>(qs, ys, edge, n, r, keep2, cb, keep_lb);
     if (lane == 0 && d2 <= keep2) {
       const uint32_t slot = atomicAdd(&st->cand_count, 1u);
       if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, sv.x);

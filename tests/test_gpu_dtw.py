@@ -2,8 +2,8 @@
 ids, the same FP64 DTW^2 bit for bit, the fp32 distance its rounding; over several
 shapes (several leaves and blocks, a ragged last leaf, a length that is not a
 multiple of 4), windows from 0 (the Euclidean distance) to unconstrained, k from 1
-to past the warp-level top-k, both storage modes, the concurrent query slots, exact
-ties and constant series."""
+to past the warp-level top-k, both storage modes, an index with bounded query
+slots, exact ties and constant series."""
 import numpy as np
 import pytest
 
@@ -99,8 +99,8 @@ def test_dtw_borrowed_device_collection(msi):
 
 def test_dtw_ties_constant_series_and_slots(msi):
     """Exact ties go to the lowest id; constant series (z = 0) are ordinary members;
-    queries answered concurrently on bounded query slots (with overflow reruns)
-    match the oracle."""
+    an index built with small query slots answers DTW queries exactly (they run on
+    its full workspace)."""
     n, length = 5000, 128
     X = datagen.walks(305, 0, n, length)
     X[1000:1300] = X[999]        # 301 identical series

@@ -153,6 +153,34 @@ MSI_API msi_status msi_knn_ex(msi_index* index, const float* queries, int64_t nq
 MSI_API msi_status msi_knn_dtw(msi_index* index, const float* queries, int64_t nq, int32_t k, int32_t window,
                                int64_t* ids, float* dists, double* sqdists64, void* stream);
 
+/*
+ * Writes the index to a file (no counterpart in the paper, which builds its index in
+ * memory for every run, Section III-A): its parameters, its arrays (SAX words, leaf
+ * order, per-series moments, leaves, envelopes, block envelopes, keys) with a
+ * checksum, and for an index that owns its collection the z-normalised collection. A
+ * borrowed collection (MSI_BUILD_BORROW) is not written.
+ *   path  file name, created or truncated.
+ * Waits for the device. Errors: MSI_EINVAL (NULL argument), MSI_ECUDA (device read),
+ * MSI_EINTERNAL (file I/O; msi_last_error names the step).
+ */
+MSI_API msi_status msi_index_save(msi_index* index, const char* path);
+
+/*
+ * Reads an index written by msi_index_save onto the current device.
+ *   series  for an index saved from a borrowed collection: the same collection, device
+ *           memory on the current device, 16-byte aligned, kept alive by the caller;
+ *           NULL for an index that holds its collection.
+ *   opts    query_slots and slot_capacity as in msi_build (leaf capacity and flags
+ *           come from the file); may be NULL.
+ *   out     receives the index (free with msi_free).
+ * The file is checked (magic, version, parameters, exact size, checksum of the index
+ * arrays) before and while it is read. Errors: MSI_EINVAL (not an index file, a
+ * truncated or inconsistent one, a series pointer missing or not expected),
+ * MSI_ENOMEM / MSI_ECUDA; nothing is returned on error.
+ */
+MSI_API msi_status msi_index_load(const char* path, const float* series, const msi_build_opts* opts,
+                                  msi_index** out);
+
 /* Releases the index and all its device memory. NULL is a no-op. */
 MSI_API void msi_free(msi_index* index);
 

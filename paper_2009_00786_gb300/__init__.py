@@ -65,6 +65,8 @@ _lib.msi_knn.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
 _lib.msi_knn.restype = ctypes.c_int
 _lib.msi_knn_ex.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]
 _lib.msi_knn_dtw.argtypes = [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
+_lib.msi_index_save.argtypes = [_vp, ctypes.c_char_p]
+_lib.msi_index_load.argtypes = [ctypes.c_char_p, _vp, ctypes.POINTER(_BuildOpts), ctypes.POINTER(_vp)]
 _lib.msi_knn_ex.restype = ctypes.c_int
 _lib.msi_free.argtypes = [_vp]
 _lib.msi_free.restype = None
@@ -227,6 +229,21 @@ def msi_knn_ex(index, queries, k, stream=None):
     _check(_lib.msi_knn_ex(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), nq, k, _ptr(ids, np.int64),
                            _ptr(dists, np.float32), d64p, _stream(stream)))
     return ids, dists, d64
+
+
+def msi_index_save(index, path):
+    """msi_index_save: writes the index (and an owned collection) to `path`."""
+    _check(_lib.msi_index_save(ctypes.c_void_p(index.handle), os.fsencode(path)))
+
+
+def msi_index_load(path, series=None, query_slots=0, slot_capacity=0, stream=None):
+    """msi_index_load: an Index read from `path`; `series` is the same device
+    collection for an index saved from a borrowed collection, else None."""
+    opts = _BuildOpts(0, 0, _stream(stream), query_slots, slot_capacity)
+    out = ctypes.c_void_p()
+    _check(_lib.msi_index_load(os.fsencode(path), _ptr(series, np.float32) if series is not None else None,
+                               ctypes.byref(opts), ctypes.byref(out)))
+    return Index(out.value, keepalive=series)
 
 
 def msi_knn_dtw(index, queries, k, window=None, stream=None):

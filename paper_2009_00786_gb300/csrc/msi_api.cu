@@ -282,9 +282,9 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
     }
   }
   const bool host_out = !ids_dev || !d_dev || !d64_dev;
-  // several queries of at most 32 neighbours run concurrently on the query slots
+  // several queries run concurrently on the query slots
   // (DTW queries use the full workspace: their survivor lists outgrow a slot's)
-  const bool batched = nq > 1 && k <= 32 && ix->nslots > 1 && !ix->timing && window < 0;
+  const bool batched = nq > 1 && ix->nslots > 1 && !ix->timing && window < 0;
   if (batched && (e = msi::slots_setup(ix)) != cudaSuccess) return cuda_fail(e, "allocating query slots");
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t cnt = std::min<int64_t>(chunk, nq - c0);

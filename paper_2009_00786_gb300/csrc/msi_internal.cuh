@@ -16,6 +16,7 @@ namespace msi {
 constexpr int kWarp = 32;
 constexpr int kItem = 256;  // leaf positions per refinement work item
 constexpr int kMaxRefineWarps = 1 << 16;
+constexpr int kMaxFront = 8;  // leaves refined before the filters, at most
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ index
@@ -53,7 +54,8 @@ struct QState {
   unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int blk_count;       // leaf blocks whose envelope bound passed
   unsigned int overflow;        // a candidate or survivor list ran out of room
-  uint32_t front_a, front_b;    // leaf-order positions of the lowest-bound leaf, refined early
+  uint32_t nfront;              // leaves refined early (the lowest-bound survivors)
+  uint32_t front_leaf[8];       // their ids; the filters skip them
   unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
@@ -346,6 +348,11 @@ cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev
                          cudaStream_t s);
 // Sets the calling thread's msi_last_error() text (msi_api.cu).
 void set_last_error(const char* what);
+// Frees an index and all its device memory (msi_api.cu).
+void destroy_index(msi_index* ix);
+// Region edge tables of a cardinality: up[v] = smallest float >= beta_v, lo[v] =
+// largest float <= beta_v, v = 0..card (msi_api.cu).
+void breakpoint_edges(int card, float* up, float* lo);
 cudaError_t lower_bounds_on(const msi_index* ix, const QueryView& qv, const float* q_dev, float* series_lb_dev,
                             float* leaf_lb_dev, cudaStream_t s);
 }  // namespace msi

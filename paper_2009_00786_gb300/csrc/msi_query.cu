@@ -353,8 +353,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->surv_count = 0;
     st->blk_count = 0;
     st->overflow = 0;
-    st->front_a = 0;
-    st->front_b = 0;
+    st->nfront = 0;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -479,34 +478,55 @@ q_leaf_filter(IndexView ix, QueryView qv) {
   }
 }
 
-// The lowest (bound bits << 32 | leaf) key over the leaf filter's per-block minima,
-// in every thread of the block; ~0 when no leaf survived or when the leaf's bound
-// exceeds the BSF as thread 0 reads it (one reading for the whole block, so that the
-// block takes one decision).
-__device__ unsigned long long front_key(const QueryView& qv, uint32_t nblockmin) {
+// The m lowest (bound bits << 32 | leaf) keys among the leaf filter's per-block minima
+// whose bound passes the BSF as thread 0 reads it (one reading for the whole block,
+// so that the block takes one decision): their leaves in s_leaf, their first
+// positions in s_beg, the running total of their sizes in s_pre[0..count]. Returns the
+// count, the same in every thread.
+__device__ int front_leaves(const IndexView& ix, const QueryView& qv, uint32_t nblockmin, int m, uint32_t* s_leaf,
+                            uint32_t* s_beg, uint32_t* s_pre) {
   __shared__ unsigned long long s_best;
   __shared__ unsigned s_thr;
-  unsigned long long best = ~0ull;
-  for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
-    const unsigned long long v = qv.blockmin[i];
-    best = v < best ? v : best;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
-    best = other < best ? other : best;
-  }
   if (threadIdx.x == 0) {
-    s_best = ~0ull;
     s_thr = *(volatile unsigned*)&qv.st->thr_bits;
+    s_pre[0] = 0;
+  }
+  unsigned long long last = 0;
+  int count = 0;
+  for (int round = 0; round < m; ++round) {
+    unsigned long long best = ~0ull;
+    for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
+      const unsigned long long v = qv.blockmin[i];
+      if ((round == 0 || v > last) && v < best) best = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+      best = other < best ? other : best;
+    }
+    if (threadIdx.x == 0) s_best = ~0ull;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMin(&s_best, best);
+    __syncthreads();
+    best = s_best;
+    __syncthreads();  // every thread has read s_best before the next round resets it
+    if (best == ~0ull || __uint_as_float((uint32_t)(best >> 32)) > lb_bound2(s_thr, qv.eps, qv.tau)) break;
+    if (threadIdx.x == 0) {
+      const uint32_t l = (uint32_t)best;
+      s_leaf[count] = l;
+      s_beg[count] = ix.leaf_begin[l];
+      s_pre[count + 1] = s_pre[count] + (ix.leaf_begin[l + 1] - ix.leaf_begin[l]);
+    }
+    last = best;
+    ++count;
   }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) atomicMin(&s_best, best);
-  __syncthreads();
-  best = s_best;
-  if (best != ~0ull && __uint_as_float((uint32_t)(best >> 32)) > lb_bound2(s_thr, qv.eps, qv.tau)) best = ~0ull;
-  return best;
+  return count;
 }
+
+// Leaves refined early, by how many neighbours are wanted: k = 1 tightens its BSF
+// with every distance, a k-th best needs a wider sample of close series.
+__host__ __device__ inline int front_count(int k) { return k == 1 ? 1 : kMaxFront; }
 
 // The lowest-bound surviving leaf, refined before the block and series filters so
 // that they run against a tighter BSF (the priority order of ProcessQueue,
@@ -518,17 +538,17 @@ __global__ void __launch_bounds__(kThreads)
 q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   extern __shared__ __align__(16) float qs[];
   __shared__ unsigned s_min;
+  __shared__ uint32_t s_leaf[kMaxFront], s_beg[kMaxFront], s_pre[kMaxFront + 1];
   smem_fill(qs, qv.qz, ix.len);
   if (threadIdx.x == 0) s_min = 0x7f800000u;
-  const unsigned long long best = front_key(qv, nblockmin);
+  const int nf = front_leaves(ix, qv, nblockmin, front_count(qv.k), s_leaf, s_beg, s_pre);
   QState* st = qv.st;
-  if (best == ~0ull) return;  // the same in every thread of the block
-  const uint32_t l = (uint32_t)best;
-  const uint32_t a = ix.leaf_begin[l], b = ix.leaf_begin[l + 1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->front_a = a;
-    st->front_b = b;
+  if (nf == 0) return;  // the same in every thread of the block
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < nf) st->front_leaf[threadIdx.x] = s_leaf[threadIdx.x];
+    if (threadIdx.x == 0) st->nfront = (uint32_t)nf;
   }
+  const uint32_t total = s_pre[nf];
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const unsigned thr = *(volatile unsigned*)&st->thr_bits;
   const float keep2 = keep_bound2(thr, qv.eps);
@@ -536,7 +556,10 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   const int lane = threadIdx.x & 31;
   unsigned bestd = 0x7f800000u;
   uint32_t n_front = 0;
-  for (uint32_t pos = a + blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); pos < b; pos += warps) {
+  for (uint32_t g = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); g < total; g += warps) {
+    int f = 0;
+    while (g >= s_pre[f + 1]) ++f;
+    const uint32_t pos = s_beg[f] + (g - s_pre[f]);
     if (pos >= sa && pos < sb) continue;  // already refined by the seed
     const uint32_t id = ix.perm[pos];
     const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
@@ -566,6 +589,10 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
 }
 
 // ------------------------------------------------------------------ q_refine
+// Every k runs the streaming filters and row refinement (k > 32 keeps the k-th best of
+// the seed and front leaves as its bound); false sends k > 32 to q_refine below.
+constexpr bool kStreamAllK = true;
+
 struct RefineSmem {
   static size_t bytes(int w, int card, int len, int k) {
     size_t b = sizeof(float) * (size_t)w * card;  // T
@@ -600,7 +627,7 @@ q_refine(IndexView ix, QueryView qv) {
   if (tid == 0) { s_bc = 0; s_local = 0x7f800000u; }
   QState* st = qv.st;
   const uint32_t leaf_count = st->leaf_count;
-  const uint32_t sa = st->seed_a, sb = st->seed_b, fa = st->front_a, fb = st->front_b;
+  const uint32_t sa = st->seed_a, sb = st->seed_b, nfront = st->nfront;
   const float seglen = (float)ix.seglen;
   const uint32_t bcap = (uint32_t)qv.k + kChunk;
   uint32_t n_lb = 0, n_ref = 0, n_leaf = 0;
@@ -611,7 +638,9 @@ q_refine(IndexView ix, QueryView qv) {
     if (tid == 0) s_thr = *thr_v;
     __syncthreads();
     const uint32_t l = qv.leaf_list[li];
-    if (qv.leaf_lb2[li] > lb_bound2(s_thr, qv.eps, qv.tau)) {
+    bool front = false;  // refined early
+    for (uint32_t f = 0; f < nfront; ++f) front |= st->front_leaf[f] == l;
+    if (front || qv.leaf_lb2[li] > lb_bound2(s_thr, qv.eps, qv.tau)) {
       __syncthreads();
       continue;
     }
@@ -626,7 +655,7 @@ q_refine(IndexView ix, QueryView qv) {
       const float bound2 = lb_bound2(s_thr, qv.eps, qv.tau);
       const uint32_t ce = min(e, cb + kChunk);
       for (uint32_t p = cb + tid; p < ce; p += blockDim.x) {
-        if ((p >= sa && p < sb) || (p >= fa && p < fb)) continue;
+        if (p >= sa && p < sb) continue;
         ++n_lb;
         if (word_lb2(ix.words[p], Ts, ix.w, ix.card, seglen) <= bound2) surv[atomicAdd(&s_ns, 1u)] = p;
       }
@@ -732,8 +761,11 @@ q_filter_blocks(IndexView ix, QueryView qv) {
   __shared__ int qsym_s[16];
   __shared__ uint32_t s_cnt, s_base;
   __shared__ uint2 s_out[kBlkThreads];
+  __shared__ uint32_t fl_s[kMaxFront];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
+  const uint32_t nfront = qv.st->nfront;
+  if (threadIdx.x < nfront) fl_s[threadIdx.x] = qv.st->front_leaf[threadIdx.x];
   const uint32_t ntask = qv.st->item_count * kBlocksPerItem;
   const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
   const float seglen = (float)ix.seglen;
@@ -744,7 +776,9 @@ q_filter_blocks(IndexView ix, QueryView qv) {
     if (t < ntask) {
       const uint4 item = qv.items[t / kBlocksPerItem];
       const uint32_t blk = (item.x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
-      if (__uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
+      bool front = false;  // a leaf refined early
+      for (uint32_t f = 0; f < nfront; ++f) front |= fl_s[f] == item.w;
+      if (!front && __uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
         const uint4 lo = __ldg(ix.benv + 2 * blk), hi = __ldg(ix.benv + 2 * blk + 1);
         const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
         float acc = 0.0f;
@@ -802,7 +836,7 @@ q_filter_series(IndexView ix, QueryView qv) {
   uint32_t* qp = qp_s[warp];
   QState* st = qv.st;
   const uint32_t ntask = st->blk_count;
-  const uint32_t sa = st->seed_a, sb = st->seed_b, fa = st->front_a, fb = st->front_b;
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
   const int cshift = ix.bits > 5 ? ix.bits - 5 : 0;
   const unsigned lt = (1u << lane) - 1u;
@@ -858,8 +892,7 @@ q_filter_series(IndexView ix, QueryView qv) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t p = task[u].x * 32 + lane;
-      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb) &&
-                         (p < fa || p >= fb);
+      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
       const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
@@ -1029,7 +1062,7 @@ q_refine_rows(IndexView ix, QueryView qv) {
     }
     if (KONE) {
       if (mine_live && __float_as_uint(d2) < thr2) atomicMin(&st->thr_bits, __float_as_uint(d2));
-    } else {
+    } else if (k <= 32) {  // above 32 the k-th best of the seed and front leaves stays the bound
       const unsigned kth_old = __shfl_sync(kFull, mine, k - 1);
       for (int j = 0; j < kRows; ++j) {
         if (!((rm >> j) & 1u)) continue;
@@ -1424,22 +1457,25 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
   float* ys = qs + 3 * n4 + warp * 2 * n4;
   float* edge = ys + n4;
   smem_fill(qs, qv.qz, ix.len);
-  const unsigned long long best = front_key(qv, nblockmin);  // synchronises the block
+  __shared__ uint32_t s_leaf[kMaxFront], s_beg[kMaxFront], s_pre[kMaxFront + 1];
+  const int nf = front_leaves(ix, qv, nblockmin, front_count(qv.k), s_leaf, s_beg, s_pre);
   QState* st = qv.st;
-  if (best == ~0ull) return;  // the same in every thread of the block
+  if (nf == 0) return;  // the same in every thread of the block
   volatile unsigned int* thr_v = &st->thr_bits;
-  const uint32_t l = (uint32_t)best;
-  const uint32_t fa = ix.leaf_begin[l], fb = ix.leaf_begin[l + 1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->front_a = fa;
-    st->front_b = fb;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < nf) st->front_leaf[threadIdx.x] = s_leaf[threadIdx.x];
+    if (threadIdx.x == 0) st->nfront = (uint32_t)nf;
   }
+  const uint32_t total = s_pre[nf];
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   __shared__ unsigned s_n;
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
   uint32_t n_front = 0;
-  for (uint32_t pos = fa + blockIdx.x * kDtwWarps + warp; pos < fb; pos += gridDim.x * kDtwWarps) {
+  for (uint32_t g = blockIdx.x * kDtwWarps + warp; g < total; g += gridDim.x * kDtwWarps) {
+    int f = 0;
+    while (g >= s_pre[f + 1]) ++f;
+    const uint32_t pos = s_beg[f] + (g - s_pre[f]);
     if (pos >= sa && pos < sb) continue;  // already refined by the seed
     stage_row(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
@@ -1488,8 +1524,11 @@ q_refine_dtw(IndexView ix, QueryView qv) {
   uint32_t n_ref = 0;
   const uint32_t gw = blockIdx.x * kDtwWarps + warp;
   const int r = qv.window, nstripes = (n + 31) >> 5;
-  __shared__ float cb_s[kDtwWarps][MSI_MAX_LEN / 32];
+  __shared__ float cb_s[kDtwWarps][MSI_MAX_LEN / 32], ec_s[kDtwWarps][MSI_MAX_LEN / 32];
   float* cb = cb_s[warp];
+  float* ecs = ec_s[warp];
+  int W = 1;  // envelope table span: the largest power of two <= r + 1
+  while (2 * W <= r + 1) W <<= 1;
   for (uint32_t sidx = gw; sidx < nsurv; sidx += gridDim.x * kDtwWarps) {
     const uint2 sv = qv.surv[sidx];
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
@@ -1532,8 +1571,57 @@ q_refine_dtw(IndexView ix, QueryView qv) {
     for (int st_i = lane; st_i < nstripes; st_i += 32) {
       const int j = 32 * (st_i + 1) + r;
       cb[st_i] = j < n ? edge[j] : 0.0f;
+      ecs[st_i] = 0.0f;
     }
     __syncwarp();
+    // LB_Keogh with the roles exchanged (the candidate's envelope against the query):
+    // every row i is visited at least once, at a cost of at least the gap between q_i
+    // and the candidate's max / min over |t - i| <= r. The window extremes come from a
+    // doubling table (span W) in `edge`, built once for the maxima and once for the
+    // minima; the terms are summed per stripe of 32 rows.
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int t = lane; t < n; t += 32) edge[t] = ys[t];
+      __syncwarp();
+      for (int h = 1; h < W; h <<= 1) {  // edge[t] = extreme over [t, min(n, t + 2h))
+        for (int c0 = 0; c0 < n; c0 += 32) {
+          const int t = c0 + lane;
+          float v = 0.0f;
+          if (t < n) {
+            v = edge[t];
+            if (t + h < n) v = pass == 0 ? fmaxf(v, edge[t + h]) : fminf(v, edge[t + h]);
+          }
+          __syncwarp();
+          if (t < n) edge[t] = v;
+          __syncwarp();
+        }
+      }
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        const int t = c0 + lane;
+        float term = 0.0f;
+        if (t < n) {
+          const int a = max(0, t - r), b = min(n - 1, t + r);
+          float e = edge[a];
+          for (int x = a + W; x + W <= b + 1; x += W) e = pass == 0 ? fmaxf(e, edge[x]) : fminf(e, edge[x]);
+          e = pass == 0 ? fmaxf(e, edge[b - W + 1]) : fminf(e, edge[b - W + 1]);
+          const float q = qs[t];
+          const float d = pass == 0 ? (q > e ? __fsub_rn(q, e) : 0.0f) : (q < e ? __fsub_rn(e, q) : 0.0f);
+          term = __fmul_rn(d, d);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(kFull, term, o);
+        if (lane == 0) ecs[c0 >> 5] += term;
+      }
+      __syncwarp();
+    }
+    // total and per-stripe suffix (rows after the stripe) of the exchanged bound
+    float ec_total = 0.0f;
+    for (int st_i = nstripes - 1; st_i >= 0; --st_i) {  // uniform: every lane keeps the sums
+      const float here = ecs[st_i];
+      if (lane == 0) cb[st_i] = fmaxf(cb[st_i], ec_total);
+      ec_total = __fadd_rn(ec_total, here);
+    }
+    __syncwarp();
+    if (ec_total > keep_lb) continue;
     ++n_ref;
     const float d2 = warp_dtw<float>(qs, ys, edge, n, r, keep2, cb, keep_lb);
     if (lane == 0 && d2 <= keep2) {
@@ -1769,7 +1857,7 @@ cudaError_t slots_setup(msi_index* ix) {
 // streaming kernels up to k = 32, the block kernel with a shared-memory top-k buffer
 // above; refine_config selects those of k's mode.
 static cudaError_t refine_config(msi_index* ix, int k) {
-  const int mode = k == 1 ? 1 : (k <= 32 ? 32 : 0);
+  const int mode = k == 1 ? 1 : (k <= 32 || kStreamAllK ? 32 : 0);
   if (!ix->grids_ready) {
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
@@ -1888,10 +1976,11 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   const int refine_grid = std::max(1, ix->refine_grid / share);
   const int rows_grid = std::max(1, ix->rows_grid / share);
   const int blocks_grid = std::max(1, ix->blocks_grid / share);
-  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)refine_grid * (k <= 32 ? kFiltWarps : kThreads / 32),
+  const bool stream = k <= 32 || kStreamAllK;
+  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)refine_grid * (stream ? kFiltWarps : kThreads / 32),
                                              kMaxRefineWarps);
-  qv.npartials_rows = k <= 32 ? (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps)
-                              : qv.npartials;
+  qv.npartials_rows = stream ? (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps)
+                             : qv.npartials;
   const IndexView v = ix->view();
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
@@ -1903,7 +1992,7 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   q_front<<<(unsigned)std::min<int64_t>((ix->cap + 7) / 8, 256), kThreads, qbytes, s>>>(v, qv, nlf);
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);  // the k-th best over seed and front
   if (ev_a) cudaEventRecord(ev_a, s);
-  if (k <= 32) {
+  if (stream) {
     q_filter_blocks<<<blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
     q_filter_series<<<refine_grid, kFiltWarps * 32, ix->refine_smem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
     if (ev_m) cudaEventRecord(ev_m, s);
@@ -1917,8 +2006,9 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   if (ev_b) cudaEventRecord(ev_b, s);
   q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev, d64_dev);
   // q_prep, q_seed, q_leaf_filter, q_front, q_finalize, the refinement (block filter,
-  // series filter and rows for k <= 32; one kernel above) and q_seed_select twice for k > 1.
-  ix->kernel_launches += 5 + (k <= 32 ? 3 : 1) + (k > 1 ? 2 : 0);
+  // series filter and rows when streaming; one kernel otherwise) and q_seed_select
+  // twice for k > 1.
+  ix->kernel_launches += 5 + (stream ? 3 : 1) + (k > 1 ? 2 : 0);
   return cudaGetLastError();
 }
 

@@ -111,3 +111,32 @@ def test_product_package_does_not_load_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
                 assert "liboracle" not in text and "oracle.c" not in text, f
+
+
+def test_index_load_rejects_bad_files_before_the_device(msi, tmp_path):
+    import struct
+    lib = msi._lib
+    out = ctypes.c_void_p(7)
+    missing = str(tmp_path / "missing.idx").encode()
+    assert lib.msi_index_load(missing, None, None, ctypes.byref(out)) == msi.MSI_EINVAL and out.value is None
+    garbage = tmp_path / "garbage.idx"
+    garbage.write_bytes(b"not an index at all" * 10)
+    assert lib.msi_index_load(str(garbage).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
+    assert "not an index file" in msi.msi_last_error()
+    # a consistent header (n = 1000, len 256, 16 segments, cardinality 256, 4 leaves)
+    # whose arrays are missing: rejected by its size
+    hdr = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 1, 112, 1000, 256, 16, 256, 8, 16, 2000, 0, 1, 4,
+                      (1000 + 31) // 32, 0, 0, 0, 0, 0)
+    assert len(hdr) == 112
+    short = tmp_path / "short.idx"
+    short.write_bytes(hdr + b"\0" * 100)
+    assert lib.msi_index_load(str(short).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
+    assert "truncated" in msi.msi_last_error()
+    # the same header claiming a borrowed collection needs one
+    hdr_b = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 1, 112, 1000, 256, 16, 256, 8, 16, 2000, 1, 0, 4,
+                        (1000 + 31) // 32, 0, 0, 0, 0, 0)
+    borrowed = tmp_path / "borrowed.idx"
+    borrowed.write_bytes(hdr_b)
+    assert lib.msi_index_load(str(borrowed).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
+    assert "borrows" in msi.msi_last_error()
+    assert lib.msi_index_save(None, str(tmp_path / "x.idx").encode()) == msi.MSI_EINVAL

@@ -414,11 +414,12 @@ def main():
     st = msi.msi_query_stats_get(index, reset=True)
     launches = max(1, st["refine_launches"])
     main_refined = st["series_refined"] - st["seed_series"]
-    # algorithmic bytes per launch (kernel table):
-    # series filter: 16 per SAX word bounded + 32 per block envelope + 8 per survivor
-    # written; row refinement: 8 per survivor read + 4 len + 4 + 8 per refined series
-    # (row, perm, moments) + 8 per kept candidate
-    filt_bytes = (16 * st["series_lower_bounded"] + 32 * st["blocks_examined"] + 8 * main_refined) / launches
+    # algorithmic bytes per launch:
+    # q_filter_series: 16 per SAX word bounded + 8 per block task read + 8 per survivor
+    # written (survivors counted by the rows they became); row refinement: 8 per
+    # survivor read + 4 len + 4 + 8 per refined series (row, perm, moments) + 8 per kept
+    # candidate
+    filt_bytes = (16 * st["series_lower_bounded"] + 8 * st["blocks_examined"] + 8 * main_refined) / launches
     rows_bytes = ((8 + 4 * length + 4 + 8) * main_refined + 8 * st["candidates"]) / launches
     filt_s = st["filter_ms"] / launches / 1e3
     rows_s = (st["refine_ms"] - st["filter_ms"]) / launches / 1e3

@@ -61,12 +61,17 @@ typedef struct msi_index msi_index; /* opaque; owns all the device memory it use
 #define MSI_BUILD_BORROW 0x1u /* index a DEVICE collection in place, without a copy: the
                                  caller keeps the buffer alive and unchanged until
                                  msi_free; distances z-normalise its values on the fly */
+#define MSI_BUILD_BALANCED_SPLIT 0x2u /* split each node that exceeds the leaf capacity on the
+                                 segment whose next symbol bit divides its members most
+                                 evenly (Section II-B), and route the approximate search
+                                 down that tree; default: one bit per level, segments in
+                                 turn (both give exact answers)                        */
 
 typedef struct msi_build_opts {
   int32_t leaf_capacity; /* most series per leaf; 0 selects MSI_DEFAULT_LEAF_CAPACITY */
   uint32_t flags;        /* MSI_BUILD_* bits                                          */
   void* stream;          /* cudaStream_t or NULL                                       */
-  int32_t query_slots;   /* queries msi_knn runs at once (k <= 32); 0 selects 8, 1 runs */
+  int32_t query_slots;   /* Euclidean queries msi_knn runs at once; 0 selects 8, 1 runs */
                          /* them one after another                                     */
   int32_t slot_capacity; /* candidates / survivors a concurrent slot holds; 0 selects  */
                          /* max(65536, leaf_capacity + MSI_MAX_K) and 2^20; a query     */
@@ -116,7 +121,7 @@ MSI_API msi_status msi_build(const float* series, int64_t n, int32_t len, int32_
  *   ids      int64[nq][k]: ids (row positions in the collection), host or device.
  *   dists    float[nq][k]: Euclidean distances, host or device; may be NULL.
  *   stream   see the conventions above.
- * With nq > 1 and k <= 32 the queries run concurrently on the index's query slots
+ * With nq > 1 the queries run concurrently on the index's query slots
  * (msi_build_opts.query_slots), each slot on its own stream joined back to `stream`;
  * the call then waits for its work before returning, whatever the output memory.
  * Errors: MSI_EINVAL, MSI_ENOMEM (query workspace), MSI_ECUDA.
@@ -255,9 +260,9 @@ typedef struct msi_query_stats {
   int64_t candidates;            /* (distance, id) pairs kept for the final pick    */
   int64_t rechecked;             /* FP64 re-computations at the k-th boundary       */
   int64_t refine_launches;       /* refinements timed (one per query)               */
-  double refine_ms;              /* summed device time of the refinement: series    */
-                                 /* filter + row refinement (timing enabled only)   */
-  double filter_ms;              /* the series-filter part of refine_ms             */
+  double refine_ms;              /* summed device time of q_filter_series and the   */
+                                 /* row (or DTW) refinement (timing enabled only)   */
+  double filter_ms;              /* the q_filter_series part of refine_ms           */
   int64_t kernel_launches;       /* kernels the query path launched (all queries)   */
 } msi_query_stats;
 

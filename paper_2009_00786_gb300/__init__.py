@@ -16,11 +16,12 @@ from . import build as _build
 __all__ = [
     "MsiError", "Index", "msi_build", "msi_knn", "msi_knn_ex", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
-    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "Server", "MSI_BUILD_BORROW", "MSI_MAX_K", "library_path",
+    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "Server", "MSI_BUILD_BORROW", "MSI_BUILD_BALANCED_SPLIT", "MSI_MAX_K", "library_path",
 ]
 
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
 MSI_BUILD_BORROW = 0x1
+MSI_BUILD_BALANCED_SPLIT = 0x2
 MSI_MAX_K = 1024
 MSI_MAX_LEN = 4096
 

@@ -104,7 +104,8 @@ void free_index(msi_index* ix) {
   if (cur != ix->device) cudaSetDevice(ix->device);
   void* ptrs[] = {ix->data_owned, ix->words,     ix->perm,         ix->stats,   ix->leaf_begin, ix->env,
                   ix->benv,       ix->leaf_key,  ix->thr_up,       ix->thr_lo,  ix->qv.counters, ix->ws_qraw,
-                  ix->ws_ids,     ix->ws_dists,  ix->ws_ovf,       ix->ws_d64};
+                  ix->ws_ids,     ix->ws_dists,  ix->ws_ovf,       ix->ws_d64,  ix->root_child,  ix->tree_child,
+                  ix->tree_seg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   msi::free_workspace(ix->qv);
@@ -161,7 +162,7 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
   const int32_t cap = (opts && opts->leaf_capacity) ? opts->leaf_capacity : MSI_DEFAULT_LEAF_CAPACITY;
   if (cap < 1 || cap > (1 << 24)) return fail(MSI_EINVAL, "leaf_capacity = %d outside [1, 2^24]", cap);
   const uint32_t flags = opts ? opts->flags : 0u;
-  if (flags & ~MSI_BUILD_BORROW) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
+  if (flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT)) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
   const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : 8;
   if (slots < 1 || slots > 64) return fail(MSI_EINVAL, "query_slots = %d outside [1, 64]", slots);
   const int32_t slot_cap = opts ? opts->slot_capacity : 0;

@@ -358,6 +358,151 @@ __global__ void split_level(const unsigned long long* __restrict__ keys, const N
   }
 }
 
+// ------------------------------------------------------- balanced split
+// MSI_BUILD_BALANCED_SPLIT: below the root fan-out a node above capacity splits on
+// the segment whose next symbol bit divides its members most evenly (SplitNode,
+// Section II-B), segments with bits left only. Each node is one CTA: it counts the
+// next bit of every segment over its members, picks the segment, and partitions its
+// range stably on that bit (ids and words move together). Node depths are 4 bits per
+// segment. A node whose members agree on the chosen bit passes to the next level
+// whole; one with no bit left in any segment is cut into pieces of `cap`.
+struct BNode {
+  uint32_t begin, end, id, pad;
+  unsigned long long depth;  // bits used per segment, 4 bits each
+};
+
+__device__ __forceinline__ int bnode_depth(unsigned long long d, int j) { return (int)((d >> (4 * j)) & 15ull); }
+
+__device__ __forceinline__ uint32_t word_symbol(uint4 wd, int j) {
+  const uint32_t part = j < 4 ? wd.x : (j < 8 ? wd.y : (j < 12 ? wd.z : wd.w));
+  return (part >> (8 * (j & 3))) & 255u;
+}
+
+// root children as balanced-split nodes: ids 0..R-1, one bit per segment; the root
+// table maps each key prefix to its child
+__global__ void bal_roots(const Node* __restrict__ nodes, const uint32_t* __restrict__ count,
+                          const unsigned long long* __restrict__ keys, int w, int root_bits,
+                          BNode* __restrict__ out, int32_t* __restrict__ root_child) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *count) return;
+  const Node nd = nodes[i];
+  unsigned long long depth = 0;
+  for (int j = 0; j < w; ++j) depth |= 1ull << (4 * j);
+  out[i] = BNode{nd.begin, nd.end, i, 0u, depth};
+  root_child[keys[nd.begin] >> (64 - root_bits)] = (int32_t)i;
+}
+
+__global__ void gather_words(const uint32_t* __restrict__ ids, int64_t n, const uint4* __restrict__ words_in,
+                             uint4* __restrict__ words_out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) words_out[p] = words_in[ids[p]];
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+bal_split(const BNode* __restrict__ in, uint32_t* __restrict__ ids, uint4* __restrict__ words,
+          uint32_t* __restrict__ ids_tmp, uint4* __restrict__ words_tmp, BNode* __restrict__ out,
+          uint32_t* __restrict__ out_count, uint32_t out_cap, uint8_t* __restrict__ leaf_flag,
+          int32_t* __restrict__ tree_child, int8_t* __restrict__ tree_seg, uint32_t* __restrict__ tree_count,
+          uint32_t tree_cap, int w, int bits, uint32_t cap, uint32_t* __restrict__ overflow) {
+  const BNode nd = in[blockIdx.x];
+  const uint32_t size = nd.end - nd.begin;
+  bool open = false;  // some segment has a bit left
+  for (int j = 0; j < w; ++j) open |= bnode_depth(nd.depth, j) < bits;
+  if (size <= cap || !open) {
+    for (uint32_t p = nd.begin + threadIdx.x * cap; p < nd.end; p += blockDim.x * cap) leaf_flag[p] = 1;
+    if (threadIdx.x == 0) {
+      tree_child[2 * nd.id] = tree_child[2 * nd.id + 1] = -1 - (int32_t)nd.begin;  // leaf index later
+      tree_seg[nd.id] = -1;
+    }
+    return;
+  }
+  __shared__ uint32_t ones[16];
+  __shared__ int s_j;
+  if (threadIdx.x < 16) ones[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (uint32_t p0 = nd.begin; p0 < nd.end; p0 += blockDim.x) {
+    const uint32_t p = p0 + threadIdx.x;
+    const uint4 wd = p < nd.end ? words[p] : make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < w; ++j) {
+      const int b = bnode_depth(nd.depth, j);
+      const bool bit = p < nd.end && b < bits && ((word_symbol(wd, j) >> (bits - 1 - b)) & 1u);
+      const unsigned m = __ballot_sync(kFull, bit);
+      if (lane == 0 && m) atomicAdd(&ones[j], (uint32_t)__popc(m));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = -1;
+    long long best_gap = 0;
+    for (int j = 0; j < w; ++j) {
+      if (bnode_depth(nd.depth, j) >= bits) continue;
+      long long gap = 2ll * ones[j] - (long long)size;
+      gap = gap < 0 ? -gap : gap;
+      if (best < 0 || gap < best_gap) {
+        best = j;
+        best_gap = gap;
+      }
+    }
+    s_j = best;
+  }
+  __syncthreads();
+  const int j = s_j;
+  const int b = bnode_depth(nd.depth, j);
+  const uint32_t n1 = ones[j], n0 = size - n1;
+  uint32_t base0 = 0, base1 = 0;
+  for (uint32_t p0 = nd.begin; p0 < nd.end; p0 += blockDim.x) {
+    const uint32_t p = p0 + threadIdx.x;
+    const bool in = p < nd.end;
+    const uint4 wd = in ? words[p] : make_uint4(0, 0, 0, 0);
+    const uint32_t id = in ? ids[p] : 0u;
+    const uint32_t bit = in ? (word_symbol(wd, j) >> (bits - 1 - b)) & 1u : 0u;
+    uint32_t tot1;
+    const uint32_t ex1 = block_exclusive_scan(bit, &tot1);
+    if (in) {
+      const uint32_t dst = bit ? nd.begin + n0 + base1 + ex1 : nd.begin + base0 + (threadIdx.x - ex1);
+      ids_tmp[dst] = id;
+      words_tmp[dst] = wd;
+    }
+    base1 += tot1;
+    base0 += min((uint32_t)blockDim.x, nd.end - p0) - tot1;
+  }
+  __syncthreads();
+  for (uint32_t p = nd.begin + threadIdx.x; p < nd.end; p += blockDim.x) {
+    ids[p] = ids_tmp[p];
+    words[p] = words_tmp[p];
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long d2 = nd.depth + (1ull << (4 * j));
+    int32_t c[2] = {-1, -1};
+    const uint32_t lo[2] = {nd.begin, nd.begin + n0}, hi[2] = {nd.begin + n0, nd.end};
+    for (int h = 0; h < 2; ++h) {
+      if (lo[h] == hi[h]) continue;
+      const uint32_t id = atomicAdd(tree_count, 1u);
+      const uint32_t slot = atomicAdd(out_count, 1u);
+      if (id >= tree_cap || slot >= out_cap) {
+        *overflow = 1u;
+        continue;
+      }
+      c[h] = (int32_t)id;
+      out[slot] = BNode{lo[h], hi[h], id, 0u, d2};
+    }
+    // a side without members points to the other, so routing always reaches a leaf
+    tree_child[2 * nd.id] = c[0] >= 0 ? c[0] : c[1];
+    tree_child[2 * nd.id + 1] = c[1] >= 0 ? c[1] : c[0];
+    tree_seg[nd.id] = (int8_t)j;
+  }
+}
+
+// leaf entries of the tree: first position -> leaf index
+__global__ void bal_leaf_ids(int32_t* __restrict__ tree_child, const int8_t* __restrict__ tree_seg,
+                             const uint32_t* __restrict__ count, const uint32_t* __restrict__ rank) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *count || tree_seg[i] >= 0) return;
+  const uint32_t begin = (uint32_t)(-1 - tree_child[2 * i]);
+  tree_child[2 * i] = tree_child[2 * i + 1] = -1 - (int32_t)rank[begin];
+}
+
 __global__ void flags_to_u32(const uint8_t* __restrict__ f, int64_t n, uint32_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = f[i];
@@ -556,7 +701,10 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   const uint32_t one = 1;
   MSI_TRY(cudaMemcpyAsync(na, &root, sizeof root, cudaMemcpyHostToDevice, s));
   MSI_TRY(cudaMemcpyAsync(counts, &one, sizeof one, cudaMemcpyHostToDevice, s));
-  for (int depth = 0; depth <= total_bits; ++depth) {
+  const bool balanced = (ix->flags & MSI_BUILD_BALANCED_SPLIT) != 0;
+  // round-robin: every level to the last key bit; balanced: the root fan-out only
+  const int last_depth = balanced ? root_bits - 1 : total_bits;
+  for (int depth = 0; depth <= last_depth; ++depth) {
     MSI_TRY(cudaMemsetAsync(counts + 1, 0, sizeof(uint32_t), s));
     split_level<<<grid_for(node_cap, 256), 256, 0, s>>>(ka, na, counts, nb, counts + 1, flags, depth, root_bits,
                                                        total_bits, (uint32_t)ix->cap, (uint32_t)node_cap,
@@ -565,6 +713,55 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
     MSI_TRY(cudaMemcpyAsync(counts, counts + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     std::swap(na, nb);
   }
+  uint32_t* tree_count = nullptr;
+  if (balanced) {
+    *stage = "balanced split";
+    uint32_t R = 0;
+    MSI_TRY(cudaMemcpyAsync(&R, counts, sizeof R, cudaMemcpyDeviceToHost, s));
+    MSI_TRY(cudaStreamSynchronize(s));
+    // each level adds at most two nodes per node above capacity (at most n / cap of
+    // them); a chain of levels is at most w * bits long
+    const int64_t per_level = 2 * (n / ix->cap + 1);
+    const int64_t level_cap = std::max<int64_t>(R, per_level);
+    const int64_t tree_cap = std::min<int64_t>(0x7ffffff0ll, (int64_t)R + per_level * (w * ix->bits + 1));
+    ix->root_bits = root_bits;
+    MSI_TRY(dalloc(&ix->root_child, (size_t)1 << root_bits));
+    MSI_TRY(dalloc(&ix->tree_child, 2 * (size_t)tree_cap));
+    MSI_TRY(dalloc(&ix->tree_seg, (size_t)tree_cap));
+    MSI_TRY(cudaMemsetAsync(ix->root_child, 0xff, sizeof(int32_t) << root_bits, s));
+    BNode *ba, *bb;
+    uint4 *wsort, *wtmp;
+    uint32_t* itmp;
+    MSI_TRY(tmp.get(&ba, level_cap));
+    MSI_TRY(tmp.get(&bb, level_cap));
+    MSI_TRY(tmp.get(&wsort, n));
+    MSI_TRY(tmp.get(&wtmp, n));
+    MSI_TRY(tmp.get(&itmp, n));
+    MSI_TRY(tmp.get(&tree_count, 1));
+    MSI_TRY(cudaMemcpyAsync(tree_count, counts, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    bal_roots<<<grid_for(R, 256), 256, 0, s>>>(na, counts, ka, w, root_bits, ba, ix->root_child);
+    gather_words<<<grid_for(n, 256), 256, 0, s>>>(va, n, o.words, wsort);
+    MSI_TRY(cudaGetLastError());
+    uint32_t live = R;
+    for (int level = 0; live > 0; ++level) {
+      if (level > w * ix->bits + 1) {  // every level uses one more bit of some segment
+        *stage = "balanced split: too many levels";
+        return cudaErrorUnknown;
+      }
+      MSI_TRY(cudaMemsetAsync(counts + 1, 0, sizeof(uint32_t), s));
+      bal_split<<<live, kScanThreads, 0, s>>>(ba, va, wsort, itmp, wtmp, bb, counts + 1, (uint32_t)level_cap, flags,
+                                              ix->tree_child, ix->tree_seg, tree_count, (uint32_t)tree_cap, w,
+                                              ix->bits, (uint32_t)ix->cap, counts + 2);
+      MSI_TRY(cudaGetLastError());
+      MSI_TRY(cudaMemcpyAsync(&live, counts + 1, sizeof live, cudaMemcpyDeviceToHost, s));
+      MSI_TRY(cudaStreamSynchronize(s));
+      std::swap(ba, bb);
+    }
+    uint32_t tn = 0;
+    MSI_TRY(cudaMemcpyAsync(&tn, tree_count, sizeof tn, cudaMemcpyDeviceToHost, s));
+    MSI_TRY(cudaStreamSynchronize(s));
+    ix->tree_nodes = std::min<int64_t>(tn, tree_cap);
+  }
   // leaf begins: exclusive scan of the flags gives each leaf's rank
   uint32_t* rank;
   uint32_t* sums2;
@@ -572,6 +769,11 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(tmp.get(&sums2, (size_t)((n + 1 + kScanTile - 1) / kScanTile + 1)));
   flags_to_u32<<<grid_for(n + 1, 256), 256, 0, s>>>(flags, n + 1, rank);
   MSI_TRY(exclusive_scan(rank, rank, n + 1, sums2, s));
+  if (balanced) {
+    bal_leaf_ids<<<grid_for(ix->tree_nodes, 256), 256, 0, s>>>(ix->tree_child, ix->tree_seg, tree_count, rank);
+    MSI_TRY(cudaGetLastError());
+    ix->device_bytes += (int64_t)(sizeof(int32_t) << ix->root_bits) + 9 * ix->tree_nodes;
+  }
   uint32_t L32 = 0, node_overflow = 0;
   MSI_TRY(cudaMemcpyAsync(&L32, rank + n, sizeof L32, cudaMemcpyDeviceToHost, s));
   MSI_TRY(cudaMemcpyAsync(&node_overflow, counts + 2, sizeof node_overflow, cudaMemcpyDeviceToHost, s));

@@ -34,9 +34,15 @@ struct IndexView {
   const float* thr_up;      // [card+1]: region upper edges: thr_up[v] = smallest float >= beta_v,
                             //   thr_up[0] = -inf, thr_up[card] = +inf (also the SAX thresholds)
   const float* thr_lo;      // [card+1]: conservative lower edges: largest float <= beta_v
+  // balanced-split tree (MSI_BUILD_BALANCED_SPLIT; null otherwise): the node of each
+  // root prefix (-1: none), each node's children (a leaf: both -1 - leaf index) and
+  // split segment (-1 for a leaf)
+  const int32_t* root_child;
+  const int32_t* tree_child;
+  const int8_t* tree_seg;
   int64_t n;
   int64_t L;
-  int len, w, card, bits, seglen;
+  int len, w, card, bits, seglen, root_bits;
 };
 
 // Per-query device state (one instance per in-flight query).
@@ -263,6 +269,11 @@ struct msi_index {
   uint64_t* leaf_key = nullptr;
   float* thr_up = nullptr;
   float* thr_lo = nullptr;
+  int32_t* root_child = nullptr;  // balanced-split tree (see IndexView)
+  int32_t* tree_child = nullptr;
+  int8_t* tree_seg = nullptr;
+  int64_t tree_nodes = 0;
+  int root_bits = 0;
   float h_thr_up[257];
   float h_thr_lo[257];
   int64_t device_bytes = 0;
@@ -284,15 +295,9 @@ struct msi_index {
   int64_t* ws_ids = nullptr;    // staging for host outputs [kQueryChunk][MSI_MAX_K]
   float* ws_dists = nullptr;
   double* ws_d64 = nullptr;
-  int refine_grid = 0;
-  int rows_grid = 0;
-  int blocks_grid = 0;
   bool grids_ready = false;  // persistent grid sizes of every refinement mode
-  int grid_series = 0, grid_blocks = 0, grid_rows1 = 0, grid_rowsk = 0, grid_block_kernel = 0;
+  int grid_series = 0, grid_blocks = 0, grid_rows1 = 0, grid_rowsk = 0;
   int grid_dtw = 0, grid_dtw_check = 0;  // DTW refinement and FP64 re-check
-  size_t smem_block_kernel = 0;
-  size_t refine_smem = 0;
-  int refine_smem_k = -1;
   bool timing = false;
   std::vector<cudaEvent_t> events;  // refinement timing: three per query (start, after filter, end)
   double refine_ms = 0.0;
@@ -313,6 +318,10 @@ struct msi_index {
     v.leaf_key = leaf_key;
     v.thr_up = thr_up;
     v.thr_lo = thr_lo;
+    v.root_child = root_child;
+    v.tree_child = tree_child;
+    v.tree_seg = tree_seg;
+    v.root_bits = root_bits;
     v.n = n;
     v.L = L;
     v.len = len;

@@ -5,7 +5,8 @@
 // passes. The file holds a fixed header (parameters, array sizes and an FNV-1a
 // checksum of the index arrays) followed by the arrays in a fixed order: SAX words,
 // leaf order, per-series moments, leaf boundaries, leaf envelopes, block envelopes,
-// leaf keys and, for an index that owns its collection, the z-normalised collection.
+// leaf keys, the balanced-split tree when there is one and, for an index that owns its
+// collection, the z-normalised collection.
 // A borrowed collection is not written; loading such an index takes the collection
 // again. Everything is little-endian, as both hosts that run this library are.
 #include <cuda_runtime.h>
@@ -34,7 +35,9 @@ struct FileHeader {
   int64_t L;
   int64_t nblk;
   uint64_t index_checksum;  // FNV-1a over every array but the collection
-  uint64_t reserved[4];
+  int64_t tree_nodes;       // balanced-split tree (0 without one)
+  int64_t root_bits;
+  uint64_t reserved[2];
 };
 
 // One array of the file: device pointer and byte count.
@@ -53,6 +56,11 @@ std::vector<Section> sections(msi_index* ix, int64_t nblk, bool with_data) {
       {ix->benv, sizeof(uint4) * 2 * (size_t)nblk},
       {ix->leaf_key, sizeof(uint64_t) * (size_t)ix->L},
   };
+  if (ix->tree_child) {  // balanced-split tree
+    v.push_back({ix->root_child, sizeof(int32_t) << ix->root_bits});
+    v.push_back({ix->tree_child, 2 * sizeof(int32_t) * (size_t)ix->tree_nodes});
+    v.push_back({ix->tree_seg, sizeof(int8_t) * (size_t)ix->tree_nodes});
+  }
   if (with_data) v.push_back({ix->data_owned, sizeof(float) * (size_t)ix->n * ix->len});
   return v;
 }
@@ -136,6 +144,8 @@ msi_status msi_index_save(msi_index* ix, const char* path) {
   h.data_is_z = ix->data_is_z ? 1 : 0;
   h.L = ix->L;
   h.nblk = nblk;
+  h.tree_nodes = ix->tree_child ? ix->tree_nodes : 0;
+  h.root_bits = ix->tree_child ? ix->root_bits : 0;
   // the header goes first with a zero checksum and is rewritten at the end
   if (fwrite(&h, sizeof h, 1, out.f) != 1) {
     st = fail(MSI_EINTERNAL, "writing the header");
@@ -185,8 +195,12 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
                         h.w <= MSI_MAX_SEGMENTS && h.len % h.w == 0 && h.seglen == h.len / h.w && h.card >= 2 &&
                         h.card <= MSI_MAX_CARDINALITY && (h.card & (h.card - 1)) == 0 && (1 << h.bits) == h.card &&
                         h.cap >= 1 && h.L >= 1 && h.L <= h.n && h.nblk == (h.n + 31) / 32 &&
-                        (h.flags & ~MSI_BUILD_BORROW) == 0 && h.data_is_z == ((h.flags & MSI_BUILD_BORROW) ? 0 : 1);
-  if (!shape_ok) return fail(MSI_EINVAL, "inconsistent index file header");
+                        (h.flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT)) == 0 &&
+                        h.data_is_z == ((h.flags & MSI_BUILD_BORROW) ? 0 : 1);
+  const bool tree = (h.flags & MSI_BUILD_BALANCED_SPLIT) != 0;
+  const bool tree_ok = tree ? (h.root_bits == h.w && h.tree_nodes >= 1 && h.tree_nodes <= 2 * h.n + (1ll << h.w))
+                            : (h.root_bits == 0 && h.tree_nodes == 0);
+  if (!shape_ok || !tree_ok) return fail(MSI_EINVAL, "inconsistent index file header");
   const bool borrow = (h.flags & MSI_BUILD_BORROW) != 0;
   if (borrow && !series) return fail(MSI_EINVAL, "the index borrows its collection: pass the same collection");
   if (!borrow && series) return fail(MSI_EINVAL, "the index holds its collection: series must be NULL");
@@ -195,7 +209,9 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
     const size_t idx_bytes = (sizeof(uint4) + sizeof(uint32_t) + sizeof(float2)) * (size_t)h.n +
                              sizeof(uint32_t) * (size_t)(h.L + 1) + sizeof(uint4) * 2 * (size_t)h.L +
                              sizeof(uint4) * 2 * (size_t)h.nblk + sizeof(uint64_t) * (size_t)h.L;
-    const size_t want = sizeof(FileHeader) + idx_bytes + (borrow ? 0 : sizeof(float) * (size_t)h.n * h.len);
+    const size_t tree_bytes = tree ? (sizeof(int32_t) << h.root_bits) + 9 * (size_t)h.tree_nodes : 0;
+    const size_t want =
+        sizeof(FileHeader) + idx_bytes + tree_bytes + (borrow ? 0 : sizeof(float) * (size_t)h.n * h.len);
     if (fseek(in.f, 0, SEEK_END) != 0) return fail(MSI_EINTERNAL, "seeking the index file");
     const long long got = ftell(in.f);
     if (got < 0 || (size_t)got != want) return fail(MSI_EINVAL, "truncated or oversized index file");
@@ -230,6 +246,8 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
   ix->slot_cap = slot_cap;
   ix->L = h.L;
   ix->data_is_z = !borrow;
+  ix->tree_nodes = h.tree_nodes;
+  ix->root_bits = (int)h.root_bits;
   msi::breakpoint_edges(h.card, ix->h_thr_up, ix->h_thr_lo);
   Pinned stage;
   msi_status st = MSI_OK;
@@ -247,6 +265,9 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
       (e = cudaMalloc(&ix->env, sizeof(uint4) * 2 * (size_t)h.L)) != cudaSuccess ||
       (e = cudaMalloc(&ix->benv, sizeof(uint4) * 2 * (size_t)h.nblk)) != cudaSuccess ||
       (e = cudaMalloc(&ix->leaf_key, sizeof(uint64_t) * (size_t)h.L)) != cudaSuccess ||
+      (tree && (e = cudaMalloc(&ix->root_child, sizeof(int32_t) << h.root_bits)) != cudaSuccess) ||
+      (tree && (e = cudaMalloc(&ix->tree_child, 2 * sizeof(int32_t) * (size_t)h.tree_nodes)) != cudaSuccess) ||
+      (tree && (e = cudaMalloc(&ix->tree_seg, (size_t)h.tree_nodes)) != cudaSuccess) ||
       (!borrow && (e = cudaMalloc(&ix->data_owned, sizeof(float) * (size_t)h.n * h.len)) != cudaSuccess) ||
       (e = cudaMallocHost(&stage.p, kStage)) != cudaSuccess) {
     st = cuda_fail(e, "allocating the index");

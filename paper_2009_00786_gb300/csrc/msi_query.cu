@@ -2,23 +2,27 @@
 //
 // The paper's search workers, priority queues and BSF lock become one short chain
 // of kernels per query, all on one stream:
-//   q_prep         query iSAX summary (Algorithm 5, first step) and the per-segment
-//                  squared-gap table; the approximate-search leaf found by the
-//                  query's key, as descending the tree would (Algorithm 5, approxSearch);
-//   q_seed         real distances of that leaf's members: the initial BSF;
-//   q_seed_select  (k > 1) the k-th smallest of them;
-//   q_leaf_filter  lower bound of every leaf against the BSF; survivors listed
-//                  (TraverseRootSubtree, Algorithm 7, flattened over the leaves);
-//   q_refine       persistent CTAs take listed leaves, re-test each leaf against the
-//                  current BSF (ProcessQueue, Algorithm 8), lower-bound every member
-//                  from its SAX word and compute the real distance of the survivors
-//                  (CalculateRealDistance, Algorithm 9); the BSF is an atomicMin on the
-//                  bits of a non-negative float;
-//   q_finalize     the k-th smallest candidate squared distance, FP64 distances of
-//                  every candidate within the fp32 error margin of it, and the k
-//                  smallest by (FP64 distance, id): the answer.
-// Pruning is conservative: a bound prunes only when it exceeds the BSF by more than
-// the fp32 rounding of both sides can explain, so the answer is the exact one.
+//   q_prep          query iSAX summary (Algorithm 5, first step) and the per-segment
+//                   squared-gap tables; the approximate-search leaf found by the
+//                   query's key, as descending the tree would (Algorithm 5, approxSearch);
+//   q_seed          real distances of that leaf's members: the initial BSF;
+//   q_seed_select   (k > 1) the k-th smallest of them;
+//   q_leaf_filter   lower bound of every leaf against the BSF; survivors become work
+//                   items (TraverseRootSubtree, Algorithm 7, flattened over the leaves);
+//   q_front         the lowest-bound surviving leaves refined first (the head of the
+//                   priority order of ProcessQueue, Algorithm 8);
+//   q_filter_blocks bounds of 32-position blocks of the surviving leaves;
+//   q_filter_series per-series bounds from the SAX words (Algorithm 9's lower bound);
+//   q_refine_rows   real distances of the survivors (CalculateRealDistance,
+//                   Algorithm 9); the BSF is an atomicMin on the bits of a
+//                   non-negative float, each item re-tested against it (Algorithm 8);
+//   q_finalize      the k-th smallest candidate squared distance, FP64 distances of
+//                   every candidate within the fp32 error margin of it, and the k
+//                   smallest by (FP64 distance, id): the answer.
+// Under DTW (Section IV) q_seed, q_front and q_refine_rows have DTW counterparts and
+// the FP64 re-check runs in its own kernel. Pruning is conservative: a bound prunes
+// only when it exceeds the BSF by more than the fp32 rounding of both sides can
+// explain, so the answer is the exact one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +33,6 @@ namespace msi {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 1024;  // leaf positions lower-bounded per refinement step
 
 // A candidate: (fp32 squared distance bits << 32) | leaf-order position.
 __device__ __forceinline__ unsigned long long pack(float d2, uint32_t pos) {
@@ -336,7 +339,24 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     __syncthreads();
   }
   if (tid == 0) {
-    const int64_t l = lo_s;
+    int64_t l = lo_s;
+    if (ix.tree_child) {
+      // balanced-split tree: descend from the query's root child by the next bit of
+      // each node's split segment (the search above is the fallback when the query's
+      // root prefix has no child)
+      int32_t node = ix.root_child[qkey >> (64 - ix.root_bits)];
+      if (node >= 0) {
+        int depth[16];
+        for (int j = 0; j < 16; ++j) depth[j] = 1;
+        for (int step = 0; step < 16 * 8 + 2 && ix.tree_seg[node] >= 0; ++step) {
+          const int j = ix.tree_seg[node];
+          const int bit = (sym_s[j] >> (ix.bits - 1 - depth[j])) & 1;
+          ++depth[j];
+          node = ix.tree_child[2 * node + bit];
+        }
+        if (ix.tree_seg[node] < 0) l = -1 - ix.tree_child[2 * node];
+      }
+    }
     int64_t a = ix.leaf_begin[l], b = ix.leaf_begin[l + 1];
     if (b - a < k) {
       b = min(ix.n, max(b, a + (int64_t)k));
@@ -525,8 +545,10 @@ __device__ int front_leaves(const IndexView& ix, const QueryView& qv, uint32_t n
 }
 
 // Leaves refined early, by how many neighbours are wanted: k = 1 tightens its BSF
-// with every distance, a k-th best needs a wider sample of close series.
-__host__ __device__ inline int front_count(int k) { return k == 1 ? 1 : kMaxFront; }
+// with every distance, a k-th best needs a wider sample of close series. (For k = 1 a
+// block that reads a BSF already tightened by other blocks takes a prefix of the same
+// list: the leaves it leaves out are pruned by that BSF.)
+__host__ __device__ inline int front_count(int k) { return k == 1 ? 4 : kMaxFront; }
 
 // The lowest-bound surviving leaf, refined before the block and series filters so
 // that they run against a tighter BSF (the priority order of ProcessQueue,
@@ -585,147 +607,6 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   if (threadIdx.x == 0) {
     if (s_n) atomicAdd(&st->series_refined, s_n);  // one global atomic per block
     if (qv.k == 1 && s_min < thr) atomicMin(&st->thr_bits, s_min);
-  }
-}
-
-// ------------------------------------------------------------------ q_refine
-// Every k runs the streaming filters and row refinement (k > 32 keeps the k-th best of
-// the seed and front leaves as its bound); false sends k > 32 to q_refine below.
-constexpr bool kStreamAllK = true;
-
-struct RefineSmem {
-  static size_t bytes(int w, int card, int len, int k) {
-    size_t b = sizeof(float) * (size_t)w * card;  // T
-    b = (b + 15) & ~size_t(15);
-    b += sizeof(float) * (size_t)((len + 3) & ~3);  // query z
-    b += sizeof(uint32_t) * kChunk * 2;              // survivor positions, d2
-    if (k > 1) b += sizeof(uint32_t) * 2 * (size_t)(k + kChunk);  // top-k buffer + compaction
-    return b;
-  }
-};
-
-template <bool KONE>
-__global__ void __launch_bounds__(kThreads)
-q_refine(IndexView ix, QueryView qv) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* Ts = reinterpret_cast<float*>(smem);
-  size_t off = ((sizeof(float) * (size_t)ix.w * ix.card) + 15) & ~size_t(15);
-  float* qs = reinterpret_cast<float*>(smem + off);
-  off += sizeof(float) * (size_t)((ix.len + 3) & ~3);
-  uint32_t* surv = reinterpret_cast<uint32_t*>(smem + off);
-  off += sizeof(uint32_t) * kChunk;
-  float* sd2 = reinterpret_cast<float*>(smem + off);
-  off += sizeof(uint32_t) * kChunk;
-  uint32_t* bufA = reinterpret_cast<uint32_t*>(smem + off);
-  uint32_t* bufB = bufA + (qv.k + kChunk);
-  __shared__ uint32_t s_ns, s_bc, s_thr, s_local, s_hist[256], s_sel[2];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wc = ix.w * ix.card;
-  smem_fill(Ts, qv.T, wc);
-  smem_fill(qs, qv.qz, ix.len);
-  if (tid == 0) { s_bc = 0; s_local = 0x7f800000u; }
-  QState* st = qv.st;
-  const uint32_t leaf_count = st->leaf_count;
-  const uint32_t sa = st->seed_a, sb = st->seed_b, nfront = st->nfront;
-  const float seglen = (float)ix.seglen;
-  const uint32_t bcap = (uint32_t)qv.k + kChunk;
-  uint32_t n_lb = 0, n_ref = 0, n_leaf = 0;
-  volatile unsigned int* thr_v = &st->thr_bits;
-  __syncthreads();
-
-  for (uint32_t li = blockIdx.x; li < leaf_count; li += gridDim.x) {
-    if (tid == 0) s_thr = *thr_v;
-    __syncthreads();
-    const uint32_t l = qv.leaf_list[li];
-    bool front = false;  // refined early
-    for (uint32_t f = 0; f < nfront; ++f) front |= st->front_leaf[f] == l;
-    if (front || qv.leaf_lb2[li] > lb_bound2(s_thr, qv.eps, qv.tau)) {
-      __syncthreads();
-      continue;
-    }
-    const uint32_t b = ix.leaf_begin[l], e = ix.leaf_begin[l + 1];
-    ++n_leaf;
-    for (uint32_t cb = b; cb < e; cb += kChunk) {
-      if (tid == 0) {
-        s_ns = 0;
-        s_thr = *thr_v;
-      }
-      __syncthreads();
-      const float bound2 = lb_bound2(s_thr, qv.eps, qv.tau);
-      const uint32_t ce = min(e, cb + kChunk);
-      for (uint32_t p = cb + tid; p < ce; p += blockDim.x) {
-        if (p >= sa && p < sb) continue;
-        ++n_lb;
-        if (word_lb2(ix.words[p], Ts, ix.w, ix.card, seglen) <= bound2) surv[atomicAdd(&s_ns, 1u)] = p;
-      }
-      __syncthreads();
-      const uint32_t ns = s_ns;
-      for (uint32_t i = warp; i < ns; i += kThreads / 32) {
-        const uint32_t p = surv[i];
-        const uint32_t id = ix.perm[p];
-        const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[p];
-        const float d2 = warp_sqdist(ix, id, ms, qs);
-        if (lane == 0) {
-          ++n_ref;
-          const unsigned thr = *thr_v;
-          if (d2 <= keep_bound2(thr, qv.eps)) {
-            const uint32_t slot = atomicAdd(&st->cand_count, 1u);
-            if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, p);
-            else st->overflow = 1u;
-          }
-          if (KONE) atomicMin(&st->thr_bits, __float_as_uint(d2));
-          else sd2[i] = d2;
-        }
-      }
-      __syncthreads();
-      if (!KONE && ns > 0) {
-        // buffered local top-k: keep values at or below the local k-th best; when
-        // k or more are held, select the k-th, keep k of them, publish the bound
-        const float local = __uint_as_float(s_local);
-        for (uint32_t i = tid; i < ns; i += blockDim.x)
-          if (sd2[i] <= local) {
-            const uint32_t slot = atomicAdd(&s_bc, 1u);
-            if (slot < bcap) bufA[slot] = __float_as_uint(sd2[i]);
-          }
-        __syncthreads();
-        const uint32_t bc = min(s_bc, bcap);
-        if (bc >= (uint32_t)qv.k) {
-          const uint32_t kth = block_select_u32([&](uint32_t i) { return bufA[i]; }, bc, (uint32_t)qv.k,
-                                                s_hist, s_sel);
-          if (tid == 0) { s_ns = 0; s_local = kth; }
-          __syncthreads();
-          // compact: all values below kth, then values equal to kth up to k in total
-          for (uint32_t i = tid; i < bc; i += blockDim.x)
-            if (bufA[i] < kth) bufB[atomicAdd(&s_ns, 1u)] = bufA[i];
-          __syncthreads();
-          for (uint32_t i = tid; i < bc; i += blockDim.x)
-            if (bufA[i] == kth) {
-              const uint32_t slot = atomicAdd(&s_ns, 1u);
-              if (slot < (uint32_t)qv.k) bufB[slot] = kth;
-            }
-          __syncthreads();
-          const uint32_t kept = min(s_ns, (uint32_t)qv.k);
-          for (uint32_t i = tid; i < kept; i += blockDim.x) bufA[i] = bufB[i];
-          if (tid == 0) {
-            s_bc = kept;
-            atomicMin(&st->thr_bits, kth);
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
-  // reduce the work counters
-  for (int o = 16; o > 0; o >>= 1) {
-    n_lb += __shfl_xor_sync(kFull, n_lb, o);
-    n_ref += __shfl_xor_sync(kFull, n_ref, o);
-  }
-  const uint32_t gw = blockIdx.x * (kThreads / 32) + warp;
-  if (lane == 0 && gw < kMaxRefineWarps) {
-    qv.partials[gw] = n_lb;
-    qv.partials[kMaxRefineWarps + gw] = n_ref;
-    qv.partials[2 * kMaxRefineWarps + gw] = warp == 0 ? n_leaf : 0u;
   }
 }
 
@@ -1794,9 +1675,6 @@ cudaError_t query_setup(msi_index* ix) {
   if ((e = dalloc(&ix->ws_d64, (size_t)kQueryChunk * MSI_MAX_K)) != cudaSuccess) return e;
   if ((e = dalloc(&ix->ws_ovf, (size_t)kQueryChunk)) != cudaSuccess) return e;
   ix->device_bytes += (int64_t)kQueryChunk * (ix->len * 4 + MSI_MAX_K * 20 + 4);
-  const size_t max_smem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
-  if ((e = cudaFuncSetAttribute(q_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(q_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)) != cudaSuccess) return e;
   // DTW kernels: room for the longest series (the attribute is a ceiling only)
   const int dtw_max = (int)dtw_smem(MSI_MAX_LEN), chk_max = (int)dtw_check_smem(MSI_MAX_LEN);
   if ((e = cudaFuncSetAttribute(q_seed_dtw, cudaFuncAttributeMaxDynamicSharedMemorySize, dtw_max)) != cudaSuccess ||
@@ -1853,11 +1731,9 @@ cudaError_t slots_setup(msi_index* ix) {
   return cudaSuccess;
 }
 
-// Persistent grids of the refinement kernels, computed once per index: the two
-// streaming kernels up to k = 32, the block kernel with a shared-memory top-k buffer
-// above; refine_config selects those of k's mode.
-static cudaError_t refine_config(msi_index* ix, int k) {
-  const int mode = k == 1 ? 1 : (k <= 32 || kStreamAllK ? 32 : 0);
+// Persistent grid sizes of the filter and refinement kernels (occupancy x SMs),
+// computed once per index; query_one divides them among the concurrent queries.
+static cudaError_t refine_config(msi_index* ix) {
   if (!ix->grids_ready) {
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
@@ -1879,11 +1755,6 @@ static cudaError_t refine_config(msi_index* ix, int k) {
         cudaSuccess)
       return e;
     ix->grid_rowsk = std::max(1, per_sm) * sms;
-    const size_t bsmem = RefineSmem::bytes(ix->w, ix->card, ix->len, MSI_MAX_K);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine<false>, kThreads, bsmem)) != cudaSuccess)
-      return e;
-    ix->grid_block_kernel = std::max(1, per_sm) * sms;
-    ix->smem_block_kernel = bsmem;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_dtw<false>, kDtwWarps * 32,
                                                            dtw_smem(ix->len))) != cudaSuccess)
       return e;
@@ -1894,22 +1765,11 @@ static cudaError_t refine_config(msi_index* ix, int k) {
     ix->grid_dtw_check = std::max(1, per_sm) * sms;
     ix->grids_ready = true;
   }
-  if (mode) {
-    ix->refine_grid = ix->grid_series;
-    ix->refine_smem = sizeof(float) * (size_t)ix->w * ix->card;
-    ix->blocks_grid = ix->grid_blocks;
-    ix->rows_grid = mode == 1 ? ix->grid_rows1 : ix->grid_rowsk;
-  } else {
-    ix->refine_grid = ix->grid_block_kernel;
-    ix->refine_smem = ix->smem_block_kernel;
-    ix->rows_grid = 0;
-  }
-  ix->refine_smem_k = mode;
   return cudaSuccess;
 }
 
 // One query (device pointers), stream-ordered. ev_a / ev_m / ev_b, when given,
-// bracket the series filter and the row refinement.
+// bracket q_filter_series and the row refinement.
 // The DTW chain: q_prep (envelope), q_seed_dtw, [q_seed_select], q_leaf_filter,
 // q_front_dtw, [q_seed_select], q_filter_blocks, q_filter_series (the Euclidean
 // filters run unchanged on the envelope's tables), q_refine_dtw, q_final_pick,
@@ -1917,7 +1777,7 @@ static cudaError_t refine_config(msi_index* ix, int k) {
 static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const float* q_dev, int k, int64_t* ids_dev,
                                  float* dists_dev, double* d64_dev, cudaStream_t s, cudaEvent_t ev_a,
                                  cudaEvent_t ev_m, cudaEvent_t ev_b, int window) {
-  cudaError_t e = refine_config(ix, 1);  // the filters' grids
+  cudaError_t e = refine_config(ix);
   if (e != cudaSuccess) return e;
   qv.window = std::min(window, ix->len - 1);
   // fp32 DTW sums up to 2 len - 1 cells along a path: relative error below
@@ -1943,8 +1803,8 @@ static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const f
   q_front_dtw<<<(unsigned)std::min<int64_t>((ix->cap + kDtwWarps - 1) / kDtwWarps, 512), kDtwWarps * 32, dsm, s>>>(
       v, qv, nlf);
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);
-  if (ev_a) cudaEventRecord(ev_a, s);
   q_filter_blocks<<<blocks_grid, kBlkThreads, fsmem, s>>>(v, qv);
+  if (ev_a) cudaEventRecord(ev_a, s);
   q_filter_series<<<series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
   if (ev_m) cudaEventRecord(ev_m, s);
   if (k == 1) q_refine_dtw<true><<<dtw_grid, kDtwWarps * 32, dsm, s>>>(v, qv);
@@ -1967,20 +1827,18 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
     qv.ovf = ovf;
     return query_one_dtw(ix, qv, share, q_dev, k, ids_dev, dists_dev, d64_dev, s, ev_a, ev_m, ev_b, window);
   }
-  cudaError_t e = refine_config(ix, k);
+  cudaError_t e = refine_config(ix);
   if (e != cudaSuccess) return e;
   QueryView qv = ws;
   qv.k = k;
   qv.ovf = ovf;
   qv.window = -1;
-  const int refine_grid = std::max(1, ix->refine_grid / share);
-  const int rows_grid = std::max(1, ix->rows_grid / share);
-  const int blocks_grid = std::max(1, ix->blocks_grid / share);
-  const bool stream = k <= 32 || kStreamAllK;
-  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)refine_grid * (stream ? kFiltWarps : kThreads / 32),
-                                             kMaxRefineWarps);
-  qv.npartials_rows = stream ? (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps)
-                             : qv.npartials;
+  const int series_grid = std::max(1, ix->grid_series / share);
+  const int rows_grid = std::max(1, (k == 1 ? ix->grid_rows1 : ix->grid_rowsk) / share);
+  const int blocks_grid = std::max(1, ix->grid_blocks / share);
+  const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+  qv.npartials = (uint32_t)std::min<int64_t>((int64_t)series_grid * kFiltWarps, kMaxRefineWarps);
+  qv.npartials_rows = (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps);
   const IndexView v = ix->view();
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   q_prep<<<1, kThreads, qbytes, s>>>(v, q_dev, qv, k);
@@ -1991,24 +1849,18 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   q_leaf_filter<<<nlf, kThreads, 0, s>>>(v, qv);
   q_front<<<(unsigned)std::min<int64_t>((ix->cap + 7) / 8, 256), kThreads, qbytes, s>>>(v, qv, nlf);
   if (k > 1) q_seed_select<<<1, 1024, 0, s>>>(qv);  // the k-th best over seed and front
+  q_filter_blocks<<<blocks_grid, kBlkThreads, fsmem, s>>>(v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
-  if (stream) {
-    q_filter_blocks<<<blocks_grid, kBlkThreads, ix->refine_smem, s>>>(v, qv);
-    q_filter_series<<<refine_grid, kFiltWarps * 32, ix->refine_smem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
-    if (ev_m) cudaEventRecord(ev_m, s);
-    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
-    if (k == 1) q_refine_rows<true><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
-    else q_refine_rows<false><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
-  } else {
-    q_refine<false><<<refine_grid, kThreads, ix->refine_smem, s>>>(v, qv);
-    if (ev_m) cudaEventRecord(ev_m, s);
-  }
+  q_filter_series<<<series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s>>>(v, qv);
+  if (ev_m) cudaEventRecord(ev_m, s);
+  const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  if (k == 1) q_refine_rows<true><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
+  else q_refine_rows<false><<<rows_grid, kRowWarps * 32, rsmem, s>>>(v, qv);
   if (ev_b) cudaEventRecord(ev_b, s);
   q_finalize<<<1, 1024, 0, s>>>(v, qv, ids_dev, dists_dev, d64_dev);
-  // q_prep, q_seed, q_leaf_filter, q_front, q_finalize, the refinement (block filter,
-  // series filter and rows when streaming; one kernel otherwise) and q_seed_select
-  // twice for k > 1.
-  ix->kernel_launches += 5 + (stream ? 3 : 1) + (k > 1 ? 2 : 0);
+  // q_prep, q_seed, q_leaf_filter, q_front, q_filter_blocks, q_filter_series,
+  // q_refine_rows, q_finalize, and q_seed_select twice for k > 1.
+  ix->kernel_launches += 8 + (k > 1 ? 2 : 0);
   return cudaGetLastError();
 }
 

@@ -264,6 +264,8 @@ typedef struct msi_query_stats {
                                  /* row (or DTW) refinement (timing enabled only)   */
   double filter_ms;              /* the q_filter_series part of refine_ms           */
   int64_t kernel_launches;       /* kernels the query path launched (all queries)   */
+  int64_t survivors;             /* series whose SAX-word bound passed the series   */
+                                 /* filter (they are re-tested before refinement)   */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises

@@ -521,8 +521,9 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->refine_ms = ix->refine_ms;
   st->filter_ms = ix->filter_ms;
   st->kernel_launches = ix->kernel_launches.load();
+  st->survivors = (int64_t)c[msi::ST_SURVIVORS];
   if (reset) {
-    if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_BAD_QUERY)) != cudaSuccess)
+    if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_COUNT)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");
     ix->refine_ms = 0.0;
     ix->filter_ms = 0.0;

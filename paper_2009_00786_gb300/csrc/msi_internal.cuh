@@ -75,7 +75,7 @@ struct QState {
 // Device-wide work counters (u64), in msi_query_stats field order.
 enum StatSlot {
   ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_SURVIVED, ST_LEAVES_PROCESSED, ST_SERIES_LB,
-  ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_COUNT
+  ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_SURVIVORS, ST_COUNT
 };
 
 struct QueryView {

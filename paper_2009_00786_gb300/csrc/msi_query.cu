@@ -1174,6 +1174,7 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     atomicAdd(&c[ST_SEED], seed + st->series_refined);
     atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
     atomicAdd(&c[ST_RECHECKED], (unsigned long long)R);
+    atomicAdd(&c[ST_SURVIVORS], (unsigned long long)st->surv_count);
   }
 }
 

@@ -40,12 +40,17 @@ def gather_merge(ids, d64, k, group=None):
     return merge_topk([g.cpu().numpy() for g in gi], [g.cpu().numpy() for g in gd], k)
 
 
-def sharded_knn(index, queries, k, first_id, group=None):
+def sharded_knn(index, queries, k, first_id, group=None, window=None):
     """k-NN over the whole sharded collection: this rank's answer over its index
     (collection ids offset by first_id), gathered and merged across the group.
+    window=None: Euclidean (msi_knn_ex); an int: DTW with that warping window
+    (msi_knn_dtw), whose FP64 DTW^2 merges the same way.
     Returns (ids int64 [nq, k], dists float32 [nq, k], d64 [nq, k])."""
-    from . import msi_knn_ex
-    ids, _, d64 = msi_knn_ex(index, queries, k)
+    from . import msi_knn_dtw, msi_knn_ex
+    if window is None:
+        ids, _, d64 = msi_knn_ex(index, queries, k)
+    else:
+        ids, _, d64 = msi_knn_dtw(index, queries, k, window=window)
     if hasattr(ids, "cpu"):
         ids, d64 = ids.cpu().numpy(), d64.cpu().numpy()
     mi, md = gather_merge(ids + first_id, d64, k, group)

@@ -20,6 +20,53 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _rank_dtw(rank, world, port, out_path):
+    import torch.distributed as dist
+
+    from paper_2009_00786_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    X = datagen.walks(62, 0, 1200, 64)
+    X[1100] = X[20]  # a tie across the two shards
+    per = 1200 // world
+    first = rank * per
+    Z = oracle.summarise(X[first:first + per], 16, 256)[0]
+    Q = np.concatenate([datagen.paper_queries(1200, 64, count=4, data_seed=62), X[[20]]])
+    ids, d2 = [], []
+    for q in Q:
+        i, d = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], K, 6)
+        ids.append(i + first)
+        d2.append(d)
+    mi, md = shard.gather_merge(np.array(ids), np.array(d2), K)
+    if rank == 0:
+        np.savez(out_path, ids=mi, d2=md)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_merge_dtw_answers(tmp_path):
+    """The same exchange under DTW: per-rank FP64 DTW^2 answers merge into the
+    whole-collection DTW answer."""
+    try:
+        import __graft_entry__
+        __graft_entry__.build()
+    except Exception as e:
+        pytest.skip(f"library build unavailable: {e}")
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "merged_dtw.npz")
+    mp.start_processes(_rank_dtw, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    got = np.load(out)
+    X = datagen.walks(62, 0, 1200, 64)
+    X[1100] = X[20]
+    Z = oracle.summarise(X, 16, 256)[0]
+    Q = np.concatenate([datagen.paper_queries(1200, 64, count=4, data_seed=62), X[[20]]])
+    for i, q in enumerate(Q):
+        oid, od2 = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], K, 6)
+        assert np.array_equal(got["ids"][i], oid)
+        assert np.array_equal(got["d2"][i], od2)
+    assert list(got["ids"][-1][:2]) == [20, 1100]
+
+
 def _rank(rank, world, port, out_path):
     import torch.distributed as dist
 

@@ -1242,24 +1242,26 @@ __device__ V warp_dtw(const float* qs, const float* ys, V* edge, int n, int r, V
     const float x = row ? qs[i] : 0.0f;
     const int jlo = max(0, i - r), jhi = min(n - 1, i + r);
     const bool writer = lane == 31 && i0 + 32 < n;
-    V prev = inf, upd = inf, rowmin = inf;
+    V prev = inf, rowmin = inf;
+    // the diagonal predecessor is the value the lane took as "up" one step earlier;
+    // lane 0 starts from the edge entry left of jbeg (the origin in the first stripe)
+    V upd = lane == 0 ? (jbeg >= 1 ? edge[jbeg - 1] : (i0 == 0 ? (V)0 : inf)) : inf;
+    const int jl = row ? jlo : 0x3fffffff;  // an empty band for rows past the end
+    const unsigned span = (unsigned)(jhi - jlo);
+    const int j0 = jbeg - lane;
     for (int t = 0; t < steps; ++t) {
-      const int j = jbeg + t - lane;
-      V up = __shfl_up_sync(kFull, prev, 1);
-      V diag = upd;
-      if (lane == 0) {
-        up = j < n ? edge[j] : inf;  // j >= 0 for lane 0
-        diag = j >= 1 && j <= n ? edge[j - 1] : (i0 == 0 && j == 0 ? (V)0 : inf);
-      }
+      const int j = j0 + t;
+      const V sh = __shfl_up_sync(kFull, prev, 1);
+      const V up = lane == 0 ? (j < n ? edge[j] : inf) : sh;  // j >= 0 for lane 0
       V cur = inf;
-      if (row && j >= jlo && j <= jhi) {
-        V m = diag < up ? diag : up;
+      if ((unsigned)(j - jl) <= span) {
+        V m = upd < up ? upd : up;
         m = prev < m ? prev : m;
         cur = dtw_cell<V>(x, ys[j], m);
         rowmin = cur < rowmin ? cur : rowmin;
-        if (i == n - 1 && j == n - 1) result = cur;
+        if (j == n - 1) result = cur;  // kept from the last stripe's row n - 1
       }
-      if (writer && j >= 0 && j < n) edge[j] = cur;
+      if (writer && (unsigned)j < (unsigned)n) edge[j] = cur;
       prev = cur;
       upd = up;
     }

@@ -505,43 +505,39 @@ q_leaf_filter(IndexView ix, QueryView qv) {
 // count, the same in every thread.
 __device__ int front_leaves(const IndexView& ix, const QueryView& qv, uint32_t nblockmin, int m, uint32_t* s_leaf,
                             uint32_t* s_beg, uint32_t* s_pre) {
-  __shared__ unsigned long long s_best;
-  __shared__ unsigned s_thr;
-  if (threadIdx.x == 0) {
-    s_thr = *(volatile unsigned*)&qv.st->thr_bits;
-    s_pre[0] = 0;
-  }
-  unsigned long long last = 0;
-  int count = 0;
-  for (int round = 0; round < m; ++round) {
-    unsigned long long best = ~0ull;
-    for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
-      const unsigned long long v = qv.blockmin[i];
-      if ((round == 0 || v > last) && v < best) best = v;
-    }
+  __shared__ int s_count;
+  if (threadIdx.x < 32) {  // warp 0 selects (shuffles only); the block waits once
+    const int lane = threadIdx.x;
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&qv.st->thr_bits : 0u, 0);
+    const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
+    if (lane == 0) s_pre[0] = 0;
+    unsigned long long last = 0;
+    int count = 0;
+    for (int round = 0; round < m; ++round) {
+      unsigned long long best = ~0ull;
+      for (uint32_t i = lane; i < nblockmin; i += 32) {
+        const unsigned long long v = qv.blockmin[i];
+        if ((round == 0 || v > last) && v < best) best = v;
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(kFull, best, o);
-      best = other < best ? other : best;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+        best = other < best ? other : best;
+      }
+      if (best == ~0ull || __uint_as_float((uint32_t)(best >> 32)) > bound2) break;
+      if (lane == 0) {
+        const uint32_t l = (uint32_t)best;
+        s_leaf[count] = l;
+        s_beg[count] = ix.leaf_begin[l];
+        s_pre[count + 1] = s_pre[count] + (ix.leaf_begin[l + 1] - ix.leaf_begin[l]);
+      }
+      last = best;
+      ++count;
     }
-    if (threadIdx.x == 0) s_best = ~0ull;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicMin(&s_best, best);
-    __syncthreads();
-    best = s_best;
-    __syncthreads();  // every thread has read s_best before the next round resets it
-    if (best == ~0ull || __uint_as_float((uint32_t)(best >> 32)) > lb_bound2(s_thr, qv.eps, qv.tau)) break;
-    if (threadIdx.x == 0) {
-      const uint32_t l = (uint32_t)best;
-      s_leaf[count] = l;
-      s_beg[count] = ix.leaf_begin[l];
-      s_pre[count + 1] = s_pre[count] + (ix.leaf_begin[l + 1] - ix.leaf_begin[l]);
-    }
-    last = best;
-    ++count;
+    if (lane == 0) s_count = count;
   }
   __syncthreads();
-  return count;
+  return s_count;
 }
 
 // Leaves refined early, by how many neighbours are wanted: k = 1 tightens its BSF
@@ -966,8 +962,20 @@ q_refine_rows(IndexView ix, QueryView qv) {
 __device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel) {
   const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
   const unsigned long long* c = qv.cand;
-  const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
-                                        (uint32_t)qv.k, hist, sel);
+  uint32_t kth;
+  if (qv.k == 1) {  // the smallest: one block-wide minimum
+    if (threadIdx.x == 0) sel[0] = 0xffffffffu;
+    __syncthreads();
+    uint32_t mn = 0xffffffffu;
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) mn = min(mn, (uint32_t)(c[i] >> 32));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&sel[0], mn);
+    __syncthreads();
+    kth = sel[0];
+  } else {
+    kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count, (uint32_t)qv.k, hist, sel);
+  }
   if (threadIdx.x == 0) qv.st->final_bits = __float_as_uint(__fmul_ru(__uint_as_float(kth), 1.0f + qv.eps));
 }
 

@@ -442,7 +442,12 @@ def main():
         h = hashlib.sha256(src).hexdigest()[:16]
         kv = dict(l.split(":", 1) for l in open(tpath).read().splitlines() if ":" in l and not l.startswith("#"))
         if kv.get("source_sha256_16", "").strip() == h:
-            traffic = float(kv["dram_bytes_per_launch"])
+            # a capture on a smaller collection, scaled to this launch by its units
+            # (the algorithmic bytes) when the file gives the ratio
+            if "dram_bytes_per_alg_byte" in kv:
+                traffic = float(kv["dram_bytes_per_alg_byte"]) * alg_bytes
+            else:
+                traffic = float(kv["dram_bytes_per_launch"])
 
     line = {
         "metric": METRIC,
@@ -463,6 +468,12 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},
         "refine_kernels": kernels,
+        # every kernel of the chain together, over the timed batched steps: leaves (40 B
+        # each), block envelopes and tasks (40 B per block bounded), SAX words (16 B),
+        # rows of the seed, front leaves and survivors (4 len + 12 B), candidates (8 B)
+        "step_alg_gbs": (40 * st["leaves_total"] + 40 * st["blocks_examined"] + 16 * st["series_lower_bounded"]
+                         + (4 * length + 12) * st["series_refined"] + 8 * st["candidates"])
+                        / max(1, st["queries"]) * qps / 1e9,
         "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if not kk.endswith("_ms")},
         "clocks": clocks.summary(),
     }

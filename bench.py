@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=10)
     p.add_argument("--serving", action="store_true", help="Poisson-arrival serving sweep over three collections")
     p.add_argument("--dtw", action="store_true", help="exact k-NN under DTW (window 10%%) on the same workload")
-    p.add_argument("--query-slots", type=int, default=0, help="concurrent query slots of the index (0: default 8)")
+    p.add_argument("--query-slots", type=int, default=0, help="concurrent query slots of the index (0: default 16)")
     p.add_argument("--window", type=int, default=-1, help="DTW half-width (default len / 10)")
     p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
@@ -457,7 +457,7 @@ def main():
         "config": {"workload": workload(n * world, length, nq, k, args.leaf),
                    "n_series": n * world, "len": length, "queries_per_step": nq, "k": k,
                    "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)",
-                   "query_slots": args.query_slots or 8},
+                   "query_slots": args.query_slots or 16},
         "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
         "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq},
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},

@@ -71,7 +71,7 @@ typedef struct msi_build_opts {
   int32_t leaf_capacity; /* most series per leaf; 0 selects MSI_DEFAULT_LEAF_CAPACITY */
   uint32_t flags;        /* MSI_BUILD_* bits                                          */
   void* stream;          /* cudaStream_t or NULL                                       */
-  int32_t query_slots;   /* Euclidean queries msi_knn runs at once; 0 selects 8, 1 runs */
+  int32_t query_slots;   /* Euclidean queries msi_knn runs at once; 0 selects 16, 1 runs*/
                          /* them one after another                                     */
   int32_t slot_capacity; /* candidates / survivors a concurrent slot holds; 0 selects  */
                          /* max(65536, leaf_capacity + MSI_MAX_K) and 2^20; a query     */
@@ -289,7 +289,7 @@ typedef struct msi_server msi_server;
 
 typedef struct msi_server_opts {
   int32_t slots_per_index;  /* query slots per index, the first with room for any query; */
-                            /* 0 selects 8                                              */
+                            /* 0 selects 8; each divides the grids by at most 3       */
   int64_t workspace_bytes;  /* device bytes the bounded slots may use (admission by     */
                             /* memory: slots beyond it are not created); 0 selects 8 GiB */
   int32_t max_inflight;     /* most queries on the GPU at once; 0: no cap, 1: one at a time */

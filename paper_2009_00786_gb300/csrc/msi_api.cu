@@ -163,7 +163,7 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
   if (cap < 1 || cap > (1 << 24)) return fail(MSI_EINVAL, "leaf_capacity = %d outside [1, 2^24]", cap);
   const uint32_t flags = opts ? opts->flags : 0u;
   if (flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT)) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
-  const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : 8;
+  const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : msi::kDefaultQuerySlots;
   if (slots < 1 || slots > 64) return fail(MSI_EINVAL, "query_slots = %d outside [1, 64]", slots);
   const int32_t slot_cap = opts ? opts->slot_capacity : 0;
   if (slot_cap < 0) return fail(MSI_EINVAL, "slot_capacity = %d is negative", slot_cap);
@@ -314,7 +314,7 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
       }
       if (batched) {
         const int sl = (int)(i % ix->nslots);
-        e = msi::query_one(ix, ix->slots[sl], ix->nslots, qd + i * ix->len, k, id_base + i * k,
+        e = msi::query_one(ix, ix->slots[sl], std::min(ix->nslots, msi::kSlotGridShare), qd + i * ix->len, k, id_base + i * k,
                            d_base ? d_base + i * k : nullptr, d64_base ? d64_base + i * k : nullptr, ix->ws_ovf + i,
                            ix->slot_streams[sl], ea, em, eb, window);
       } else {

@@ -17,6 +17,13 @@ constexpr int kWarp = 32;
 constexpr int kItem = 256;  // leaf positions per refinement work item
 constexpr int kMaxRefineWarps = 1 << 16;
 constexpr int kMaxFront = 8;  // leaves refined before the filters, at most
+// Concurrent queries divide the persistent grids of their kernels by at most this:
+// the queries then oversubscribe the GPU and the hardware interleaves their blocks,
+// where dividing by the number of queries would leave SMs idle whenever the queries'
+// phases do not line up (100M x 256: 16 queries at 1/3 of the grid each 31.6K q/s,
+// 8 queries at 1/8 each 24.0K).
+constexpr int kSlotGridShare = 3;
+constexpr int kDefaultQuerySlots = 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ index
@@ -288,7 +295,7 @@ struct msi_index {
   std::vector<cudaEvent_t> slot_events;
   cudaEvent_t fork_event = nullptr;
   uint32_t* ws_ovf = nullptr;   // [kQueryChunk]
-  int nslots = 8;
+  int nslots = msi::kDefaultQuerySlots;
   int slot_cap = 0;
   int64_t overflow_reruns = 0;
   float* ws_qraw = nullptr;     // staging for host queries [kQueryChunk][len]

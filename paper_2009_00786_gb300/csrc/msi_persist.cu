@@ -217,7 +217,7 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
     if (got < 0 || (size_t)got != want) return fail(MSI_EINVAL, "truncated or oversized index file");
     if (fseek(in.f, sizeof(FileHeader), SEEK_SET) != 0) return fail(MSI_EINTERNAL, "seeking the index file");
   }
-  const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : 8;
+  const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : msi::kDefaultQuerySlots;
   if (slots < 1 || slots > 64) return fail(MSI_EINVAL, "query_slots outside [1, 64]");
   const int32_t slot_cap = opts ? opts->slot_capacity : 0;
   if (slot_cap < 0) return fail(MSI_EINVAL, "slot_capacity is negative");

@@ -278,7 +278,7 @@ msi_status msi_server_create(msi_index* const* indexes, int32_t n_indexes, const
   msi_server* sv = new msi_server();
   sv->device = dev;
   sv->max_inflight = max_inflight;
-  sv->share = std::max(1, per_index);
+  sv->share = std::max(1, std::min(per_index, msi::kSlotGridShare));
   sv->waiting.resize(n_indexes);
   sv->rerun.resize(n_indexes);
   cudaError_t e = cudaSuccess;

@@ -146,3 +146,19 @@ def test_dtw_launch_count(msi):
     msi.msi_knn_dtw(ix, Q[:1], 4, window=6)
     assert msi.msi_query_stats_get(ix)["kernel_launches"] == 2 * 10 + 12
     ix.close()
+
+
+@pytest.mark.parametrize("n,length,segs,card,cap", [(4000, 256, 8, 16, 30), (1500, 60, 4, 4, 20)])
+def test_dtw_small_cardinalities(msi, n, length, segs, card, cap):
+    """Cardinalities below 32 (the coarse 5-bit tables then hold every symbol) and few
+    segments, under DTW."""
+    X = datagen.walks(310, 0, n, length)
+    Z = oracle.summarise(X, segs, card)[0]
+    ix = msi.msi_build(X, segments=segs, cardinality=card, leaf_capacity=cap)
+    Q = np.concatenate([datagen.paper_queries(n, length, count=4, data_seed=310), X[[11]]])
+    for k in (1, 6):
+        ids, dists, d64 = msi.msi_knn_dtw(ix, Q, k, window=length // 10)
+        for i, q in enumerate(Q):
+            oid, od2 = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], k, length // 10)
+            assert np.array_equal(ids[i], oid) and np.array_equal(d64[i], od2), (k, i)
+    ix.close()

@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--window", type=int, default=-1, help="DTW half-width (default len / 10)")
     p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
+    p.add_argument("--serve-slots", type=int, default=8, help="query slots per collection (serving mode)")
     p.add_argument("--serve-requests", type=int, default=3000, help="most requests per rate")
     return p.parse_args()
 
@@ -191,7 +192,7 @@ def serving(args):
            "config": {"workload": " + ".join(f"{n // 1_000_000}M x {l}" for n, l in shapes) +
                       " fp32 random walks, k uniform in 1..100, uniform collection per request"},
            "rates": []}
-    for name, opts in (("continuous", dict(slots_per_index=8)), ("one_at_a_time", dict(slots_per_index=1,
+    for name, opts in (("continuous", dict(slots_per_index=args.serve_slots)), ("one_at_a_time", dict(slots_per_index=1,
                                                                                         max_inflight=1))):
         srv = msi.Server(indexes, **opts)
         for rate in rates:

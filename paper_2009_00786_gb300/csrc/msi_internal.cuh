@@ -67,6 +67,8 @@ struct QState {
   unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int blk_count;       // leaf blocks whose envelope bound passed
   unsigned int overflow;        // a candidate or survivor list ran out of room
+  float kbase;                  // k > 1: the k-th best after the seed and front leaves; the
+                                // range [0, kbase) of the candidate histogram (0: none yet)
   uint32_t nfront;              // leaves refined early (the lowest-bound survivors)
   uint32_t front_leaf[8];       // their ids; the filters skip them
   unsigned int next_leaf;       // work counter of the refinement kernel
@@ -107,6 +109,7 @@ struct QueryView {
   uint32_t surv_cap;            // entries of surv
   uint32_t* ovf;                // per-query overflow flag written by q_finalize (or nullptr)
   float* qenv;                  // [2][len]: LB_Keogh envelope of the query, upper then lower (DTW)
+  uint32_t* khist;              // [256]: k > 1, kept candidates per bucket of [0, kbase)
   int window = -1;              // DTW: Sakoe-Chiba half-width; -1: Euclidean distance
   int k;
   float eps;                    // relative margin on squared distances

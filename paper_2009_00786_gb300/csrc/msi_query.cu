@@ -254,6 +254,8 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
   }
   __syncthreads();
   for (int t = tid; t < ix.len; t += blockDim.x) qv.qz[t] = zs[t];
+  if (k > 1)
+    for (int b = tid; b < 256; b += blockDim.x) qv.khist[b] = 0u;
   // the interval each bound measures gaps to: the PAA value (Euclidean), or for DTW
   // the LB_Keogh envelope reduced per segment (Keogh's PAA envelope: the max of the
   // upper envelope and the min of the lower one over the segment, i.e. the max / min
@@ -386,6 +388,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->blk_count = 0;
     st->overflow = 0;
     st->nfront = 0;
+    st->kbase = 0.0f;
     st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
@@ -394,6 +397,50 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->series_lb = 0;
     st->series_refined = 0;
   }
+}
+
+// ------------------------------------------------------------ k-th histogram
+// For k > 1 the candidates kept below kbase (the k-th best of the seed and front
+// leaves) are counted in 256 equal buckets of [0, kbase). If the buckets up to b hold
+// k candidates, at least k computed distances lie below the upper edge of bucket b;
+// the bound read off the counts is the upper edge of bucket b + 1, one bucket of room
+// for the rounding of the bucket index, so it bounds the k-th computed distance from
+// above like any k-th best seen so far.
+__device__ __forceinline__ int khist_bucket(float d2, float kbase) {
+  return min(255, (int)__fmul_rz(d2, __fdiv_rn(256.0f, kbase)));
+}
+// One warp: the bound (fp32 bits) from the counts, or 0x7f800000 while fewer than k.
+__device__ __forceinline__ unsigned khist_bound(const uint32_t* khist, float kbase, int k) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v[8], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[j] = *(volatile const uint32_t*)(khist + 8 * lane + j);
+    sum += v[j];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t before = incl - sum;
+  int b = 256;
+  if (before < (uint32_t)k && incl >= (uint32_t)k) {
+    uint32_t run = before;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      run += v[j];
+      if (run >= (uint32_t)k) {
+        b = 8 * lane + j;
+        break;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
+  if (b >= 254) return 0x7f800000u;
+  return __float_as_uint(__fmul_ru(kbase, (float)(b + 2) * 0.00390625f));
 }
 
 // ------------------------------------------------------------------ q_seed
@@ -427,7 +474,7 @@ q_seed(IndexView ix, QueryView qv) {
 }
 
 __global__ void __launch_bounds__(1024)
-q_seed_select(QueryView qv) {
+q_seed_select(QueryView qv, int base) {
   pdl_begin();
   __shared__ uint32_t hist[256], sel[2];
   const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
@@ -435,6 +482,21 @@ q_seed_select(QueryView qv) {
   const uint32_t kth = block_select_u32([&](uint32_t i) { return (uint32_t)(c[i] >> 32); }, count,
                                         (uint32_t)qv.k, hist, sel);
   if (threadIdx.x == 0) qv.st->thr_bits = kth;
+  if (!base) return;
+  // the candidates so far, counted in 256 buckets of [0, kth): the row refinement adds
+  // its own and reads a tighter k-th bound off the counts (see khist_bound)
+  const float kb = __uint_as_float(kth);
+  if (!(kb > 0.0f && kb < INFINITY)) return;
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const float d2 = __uint_as_float((uint32_t)(c[i] >> 32));
+    if (d2 < kb) atomicAdd(&hist[khist_bucket(d2, kb)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) qv.khist[b] = hist[b];
+  if (threadIdx.x == 0) qv.st->kbase = kb;
 }
 
 // ------------------------------------------------------------------ q_leaf_filter
@@ -844,6 +906,8 @@ q_refine_rows(IndexView ix, QueryView qv) {
   uint32_t n_ref = 0;
   const uint32_t gw = blockIdx.x * kRowWarps + warp;
   const uint32_t step = gridDim.x * kRowWarps * kRows;
+  const float kbase = KONE ? 0.0f : st->kbase;  // k > 1: the candidate histogram's range
+  uint32_t hist_round = 0;
   // three-stage pipeline over this warp's groups of kRows survivors (lanes < kRows
   // hold one survivor each): the survivor entry of group g + 2 step and the perm /
   // moments of group g + step are in flight while the rows of group g are read
@@ -956,9 +1020,14 @@ q_refine_rows(IndexView ix, QueryView qv) {
         else st->overflow = 1u;
       }
     }
+    if (!KONE && keep && kbase > 0.0f && d2 < kbase) atomicAdd(&qv.khist[khist_bucket(d2, kbase)], 1u);
+    if (!KONE && kbase > 0.0f && ((++hist_round & 15) == 0)) {  // every 16 groups: the shared bound
+      const unsigned hb = khist_bound(qv.khist, kbase, k);
+      if (lane == 0 && hb < thr2) atomicMin(&st->thr_bits, hb);
+    }
     if (KONE) {
       if (mine_live && __float_as_uint(d2) < thr2) atomicMin(&st->thr_bits, __float_as_uint(d2));
-    } else if (k <= 32) {  // above 32 the k-th best of the seed and front leaves stays the bound
+    } else if (k <= 32) {  // the warp's own k best as well
       const unsigned kth_old = __shfl_sync(kFull, mine, k - 1);
       for (int j = 0; j < kRows; ++j) {
         if (!((rm >> j) & 1u)) continue;
@@ -1671,6 +1740,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   if ((e = dalloc(&qv.rc_id, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.surv, (size_t)surv_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.qenv, 2 * (size_t)ix->len)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.khist, 256)) != cudaSuccess) return e;
   qv.window = -1;
   qv.cand_cap = cand_cap;
   qv.surv_cap = surv_cap;
@@ -1684,13 +1754,13 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
 // Device bytes of one query workspace (alloc_workspace).
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap) {
   const int64_t items = ix->n / kItem + 2 * ix->L + 2;
-  return (int64_t)(3 * ix->len + 4) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
+  return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
          items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
 
 void free_workspace(QueryView& qv) {
   void* ptrs[] = {qv.qz, qv.T, qv.T5, qv.st, qv.leaf_list, qv.leaf_lb2, qv.items, qv.blks, qv.partials,
-                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv, qv.qenv};
+                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv, qv.qenv, qv.khist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   qv = QueryView{};
@@ -1862,11 +1932,11 @@ static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const f
   MSI_LAUNCH(q_prep, 1, kThreads, qbytes, s, v, q_dev, qv, k);
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);
   MSI_LAUNCH(q_seed_dtw, (unsigned)std::min<int64_t>((seed_max + kDtwWarps - 1) / kDtwWarps, 1024), kDtwWarps * 32, dsm, s, v, qv);
-  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv);
+  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 0);
   const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
   MSI_LAUNCH(q_leaf_filter, nlf, kThreads, 0, s, v, qv);
   MSI_LAUNCH(q_front_dtw, (unsigned)std::min<int64_t>((ix->cap + kDtwWarps - 1) / kDtwWarps, 512), kDtwWarps * 32, dsm, s, v, qv, nlf);
-  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv);
+  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);
   MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s, v, qv);
@@ -1909,11 +1979,11 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   MSI_LAUNCH(q_prep, 1, kThreads, qbytes, s, v, q_dev, qv, k);
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);
   MSI_LAUNCH(q_seed, (unsigned)std::min<int64_t>((seed_max + 7) / 8, 1024), kThreads, qbytes, s, v, qv);
-  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv);
+  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 0);
   const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
   MSI_LAUNCH(q_leaf_filter, nlf, kThreads, 0, s, v, qv);
   MSI_LAUNCH(q_front, (unsigned)std::min<int64_t>((ix->cap + 7) / 8, 256), kThreads, qbytes, s, v, qv, nlf);
-  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv);  // the k-th best over seed and front
+  if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);  // the k-th best over seed and front
   MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s, v, qv);

@@ -74,7 +74,7 @@ typedef struct msi_build_opts {
   int32_t query_slots;   /* Euclidean queries msi_knn runs at once; 0 selects 16, 1 runs*/
                          /* them one after another                                     */
   int32_t slot_capacity; /* candidates / survivors a concurrent slot holds; 0 selects  */
-                         /* max(65536, leaf_capacity + MSI_MAX_K) and 2^20; a query     */
+                         /* max(2^18, leaf_capacity + MSI_MAX_K) and 2^22; a query     */
                          /* that needs more is run again with room for all n          */
 } msi_build_opts;
 

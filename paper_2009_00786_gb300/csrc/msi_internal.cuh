@@ -63,7 +63,6 @@ struct QState {
   unsigned int thr_bits;        // fp32 bits of the current k-th best squared distance
   unsigned int leaf_count;      // leaves that passed the leaf filter
   unsigned int item_count;      // refinement work items (<= kItem positions of one leaf)
-  unsigned int next_item;       // (unused)
   unsigned int surv_count;      // series whose bound passed the series filter
   unsigned int blk_count;       // leaf blocks whose envelope bound passed
   unsigned int overflow;        // a candidate or survivor list ran out of room
@@ -71,12 +70,9 @@ struct QState {
                                 // range [0, kbase) of the candidate histogram (0: none yet)
   uint32_t nfront;              // leaves refined early (the lowest-bound survivors)
   uint32_t front_leaf[8];       // their ids; the filters skip them
-  unsigned int next_leaf;       // work counter of the refinement kernel
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
   unsigned int final_bits;      // k-th smallest candidate squared distance (fp32 bits)
-  unsigned int leaves_processed;
-  unsigned int series_lb;
   unsigned int series_refined;
   int32_t flag;                 // 1 constant query, -1 non-finite query
 };
@@ -103,8 +99,8 @@ struct QueryView {
   uint32_t* rc_id;              // [n]
   unsigned long long* counters; // [ST_COUNT]
   uint32_t* partials;           // [kMaxRefineWarps][3]: per-warp work counters of the refinement
-  uint32_t npartials;           // warps of the series filter (or block refinement) launch
-  uint32_t npartials_rows;      // warps of the row refinement launch
+  uint32_t npartials;           // warps of the series filter launch
+  uint32_t npartials_rows;      // warps of the row (or DTW) refinement launch
   uint32_t cand_cap;            // entries of cand / rc_d / rc_id
   uint32_t surv_cap;            // entries of surv
   uint32_t* ovf;                // per-query overflow flag written by q_finalize (or nullptr)

@@ -383,18 +383,14 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->thr_bits = 0x7f800000u;
     st->leaf_count = 0;
     st->item_count = 0;
-    st->next_item = 0;
     st->surv_count = 0;
     st->blk_count = 0;
     st->overflow = 0;
     st->nfront = 0;
     st->kbase = 0.0f;
-    st->next_leaf = 0;
     st->cand_count = (uint32_t)(b - a);
     st->rc_count = 0;
     st->final_bits = 0;
-    st->leaves_processed = 0;
-    st->series_lb = 0;
     st->series_refined = 0;
   }
 }
@@ -1800,8 +1796,8 @@ cudaError_t query_setup(msi_index* ix) {
 void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap) {
   const int64_t seed_room = std::min<int64_t>(ix->n, (int64_t)ix->cap + MSI_MAX_K);
   *cand_cap = (uint32_t)std::min<int64_t>(
-      ix->n, std::max<int64_t>(seed_room, requested ? requested : std::max<int64_t>(65536, seed_room)));
-  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, requested ? requested : 1 << 20);
+      ix->n, std::max<int64_t>(seed_room, requested ? requested : std::max<int64_t>(1 << 18, seed_room)));
+  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, requested ? requested : 1 << 22);
 }
 
 // Allocates the concurrent query slots (bounded lists), their streams and events.

@@ -1503,6 +1503,8 @@ q_refine_dtw(IndexView ix, QueryView qv) {
   unsigned mine = 0x7f800000u;  // lanes < k: this warp's k best, ascending (1 < k <= 32)
   uint32_t n_ref = 0;
   const uint32_t gw = blockIdx.x * kDtwWarps + warp;
+  const float kbase = KONE ? 0.0f : st->kbase;
+  uint32_t hist_round = 0;
   const int r = qv.window, nstripes = (n + 31) >> 5;
   __shared__ float cb_s[kDtwWarps][MSI_MAX_LEN / 32], ec_s[kDtwWarps][MSI_MAX_LEN / 32];
   float* cb = cb_s[warp];
@@ -1610,6 +1612,13 @@ q_refine_dtw(IndexView ix, QueryView qv) {
       else st->overflow = 1u;
     }
     const unsigned v = __float_as_uint(d2);
+    if (!KONE && kbase > 0.0f) {  // k > 1: the shared candidate histogram (see khist_bound)
+      if (lane == 0 && d2 <= keep2 && d2 < kbase) atomicAdd(&qv.khist[khist_bucket(d2, kbase)], 1u);
+      if ((++hist_round & 15) == 0) {
+        const unsigned hb = khist_bound(qv.khist, kbase, k);
+        if (lane == 0 && hb < thr) atomicMin(&st->thr_bits, hb);
+      }
+    }
     if (KONE) {
       if (lane == 0 && v < thr) atomicMin(&st->thr_bits, v);
     } else if (k <= 32 && v < __shfl_sync(kFull, mine, k - 1)) {

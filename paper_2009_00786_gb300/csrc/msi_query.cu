@@ -619,12 +619,12 @@ __device__ int front_leaves(const IndexView& ix, const QueryView& qv, uint32_t n
 // list: the leaves it leaves out are pruned by that BSF.)
 __host__ __device__ inline int front_count(int k) { return k == 1 ? 4 : kMaxFront; }
 
-// The lowest-bound surviving leaf, refined before the block and series filters so
-// that they run against a tighter BSF (the priority order of ProcessQueue,
-// Algorithm 8: the most promising leaf first). Every block finds the same leaf from
-// the leaf filter's per-block minima; warps take its positions in a stride. A leaf
-// whose bound already exceeds the BSF is skipped; its positions are excluded from
-// the later passes like the seed's.
+// The lowest-bound surviving leaves (front_count(k) of them), refined before the
+// block and series filters so that those run against a tighter BSF (the priority
+// order of ProcessQueue, Algorithm 8: the most promising leaves first). Every block
+// picks them from the leaf filter's per-block minima (front_leaves); warps take their
+// positions in a stride, skipping the seed range. Block 0 records the leaves, which
+// the block filter then skips.
 __global__ void __launch_bounds__(kThreads)
 q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   pdl_begin();
@@ -680,21 +680,24 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   }
 }
 
-// ------------------------------------------------------------------ k <= 32
-// Refinement for k <= 32 in two streaming kernels (ProcessQueue and
-// CalculateRealDistance, Algorithms 8-9, with the per-series filter and the real
-// distances decoupled so that each kernel keeps many loads in flight):
+// ------------------------------------------------------------ refinement
+// The refinement in three streaming kernels (ProcessQueue and CalculateRealDistance,
+// Algorithms 8-9, with the block filter, the per-series filter and the real distances
+// decoupled so that each kernel keeps many loads in flight):
 //
-// q_filter_series: one warp per aligned block of 32 leaf positions of a work item
-//   (items are the positions of one surviving leaf inside an aligned tile of kItem
-//   positions). The warp re-tests the leaf's bound against the current BSF, bounds
-//   the block by its symbol envelope, and bounds every position by its SAX word;
-//   survivors {position, bound} go to a per-warp buffer flushed 32 at a time to the
-//   survivor list. kUnroll blocks are in flight per warp.
+// q_filter_blocks: a thread per aligned block of 32 positions of a work item (items
+//   are the positions of one surviving leaf inside an aligned tile of kItem
+//   positions): re-tests the leaf's bound against the current BSF and bounds the
+//   block by its symbol envelope; surviving blocks become tasks.
+// q_filter_series: a warp per task bounds every position by its SAX word (a coarse
+//   bound first, then the full one); survivors {position, bound} go to a per-warp
+//   buffer flushed 32 at a time to the survivor list. kUnroll tasks are in flight per
+//   warp.
 // q_refine_rows: real distances of the survivors whose bound still passes the
 //   current BSF, kRows rows per warp at a time. k = 1: the BSF is an atomicMin taken
-//   only by a distance below the current BSF. 1 < k <= 32: each warp keeps its k
-//   best in registers (lane i holds the i-th) and publishes its k-th once it has k.
+//   only by a distance below the current BSF. k > 1: the shared candidate histogram
+//   (khist_bound), and for k <= 32 each warp's own k best in registers (lane i holds
+//   the i-th), published once it has k.
 constexpr int kFiltWarps = 8;
 constexpr int kUnroll = 4;
 constexpr int kBlocksPerItem = kItem / 32;
@@ -1477,10 +1480,10 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
 }
 
 // One warp per survivor of the series filter: re-test its bound against the current
-// BSF, stage its row, screen it by LB_Keogh against the envelope, then its DTW
-// distance (abandoned above the keep bound). The BSF: an atomicMin for k = 1; for
-// k <= 32 the warp keeps its k best in registers and publishes its k-th; above 32 the
-// seed's k-th stays the bound.
+// BSF, stage its row, screen it by LB_Keogh against the envelope and by LB_Keogh with
+// the roles exchanged, then its DTW distance (abandoned above the keep bound, with
+// the cumulative bounds). The BSF: an atomicMin for k = 1; for k > 1 the shared
+// candidate histogram, and for k <= 32 the warp's own k best in registers.
 template <bool KONE>
 __global__ void __launch_bounds__(kDtwWarps * 32)
 q_refine_dtw(IndexView ix, QueryView qv) {

@@ -869,15 +869,25 @@ q_filter_series(IndexView ix, QueryView qv) {
     drain32(c);
     nq = c > 32 ? c - 32 : 0;
   }
+  // the last partial buffers of the CTA's warps: one atomic for the whole CTA
   __syncwarp();
-  if (nbuf) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&st->surv_count, nbuf);
-    base = __shfl_sync(kFull, base, 0);
-    if (lane < (int)nbuf) {
-      if (base + lane < qv.surv_cap) qv.surv[base + lane] = buf[lane];
-      else st->overflow = 1u;
+  __shared__ uint32_t wbase_s[kFiltWarps], cbase_s;
+  if (lane == 0) wbase_s[warp] = nbuf;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w2 = 0; w2 < kFiltWarps; ++w2) {
+      const uint32_t c = wbase_s[w2];
+      wbase_s[w2] = tot;
+      tot += c;
     }
+    cbase_s = tot ? atomicAdd(&st->surv_count, tot) : 0u;
+  }
+  __syncthreads();
+  if (lane < (int)nbuf) {
+    const uint32_t pos = cbase_s + wbase_s[warp] + lane;
+    if (pos < qv.surv_cap) qv.surv[pos] = buf[lane];
+    else st->overflow = 1u;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_lb += __shfl_xor_sync(kFull, n_lb, o);

@@ -162,3 +162,17 @@ def test_dtw_small_cardinalities(msi, n, length, segs, card, cap):
             oid, od2 = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], k, length // 10)
             assert np.array_equal(ids[i], oid) and np.array_equal(d64[i], od2), (k, i)
     ix.close()
+
+
+@pytest.mark.parametrize("n,length,cap", [(1200, 1024, 100), (2000, 512, 80)])
+def test_dtw_long_series(msi, n, length, cap):
+    """Long rows (screened from registers up to 1024 points) against the oracle."""
+    X = datagen.walks(311, 0, n, length)
+    Z = oracle.summarise(X, 16, 256)[0]
+    ix = msi.msi_build(X, segments=16, leaf_capacity=cap)
+    Q = np.concatenate([datagen.paper_queries(n, length, count=2, data_seed=311), X[[5]]])
+    ids, _, d64 = msi.msi_knn_dtw(ix, Q, 3, window=length // 10)
+    for i, q in enumerate(Q):
+        oid, od2 = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], 3, length // 10)
+        assert np.array_equal(ids[i], oid) and np.array_equal(d64[i], od2), i
+    ix.close()

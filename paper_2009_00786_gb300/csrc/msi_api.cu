@@ -113,6 +113,10 @@ void free_index(msi_index* ix) {
   for (cudaStream_t st : ix->slot_streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : ix->slot_events) cudaEventDestroy(ev);
   if (ix->fork_event) cudaEventDestroy(ix->fork_event);
+  for (auto& g : ix->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (ix->call_dev) cudaFree(ix->call_dev);
+  if (ix->call_host) cudaFreeHost(ix->call_host);
   for (cudaEvent_t ev : ix->events)
     if (ev) cudaEventDestroy(ev);
   if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
@@ -252,6 +256,61 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
 }
 
 // window < 0: Euclidean k-NN (msi_knn_ex); window >= 0: DTW k-NN (msi_knn_dtw).
+// Enqueues `cnt` Euclidean queries on the concurrent query slots (query i on slot
+// i mod nslots) between a fork from and a join back into stream s. With `call`, the
+// kernels take the queries and outputs from that descriptor (graph capture); else
+// from the pointers given.
+static cudaError_t enqueue_batch(msi_index* ix, cudaStream_t s, int64_t cnt, int32_t k, const float* qd,
+                                 int64_t* id_base, float* d_base, double* d64_base, const msi::CallDesc* call) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(ix->fork_event, s)) != cudaSuccess) return e;
+  for (int sl = 0; sl < ix->nslots; ++sl)
+    if ((e = cudaStreamWaitEvent(ix->slot_streams[sl], ix->fork_event, 0)) != cudaSuccess) return e;
+  const int share = std::min(ix->nslots, msi::kSlotGridShare);
+  for (int64_t i = 0; i < cnt; ++i) {
+    const int sl = (int)(i % ix->nslots);
+    if (call)
+      e = msi::query_one(ix, ix->slots[sl], share, nullptr, k, nullptr, nullptr, nullptr, ix->ws_ovf + i,
+                         ix->slot_streams[sl], nullptr, nullptr, nullptr, -1, call, (int)i);
+    else
+      e = msi::query_one(ix, ix->slots[sl], share, qd + i * ix->len, k, id_base + i * k,
+                         d_base ? d_base + i * k : nullptr, d64_base ? d64_base + i * k : nullptr, ix->ws_ovf + i,
+                         ix->slot_streams[sl], nullptr, nullptr, nullptr, -1);
+    if (e != cudaSuccess) return e;
+  }
+  for (int sl = 0; sl < ix->nslots; ++sl)
+    if ((e = cudaEventRecord(ix->slot_events[sl], ix->slot_streams[sl])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, ix->slot_events[sl], 0)) != cudaSuccess)
+      return e;
+  return cudaSuccess;
+}
+
+constexpr int kMaxBatchGraphs = 8;  // query shapes remembered per index
+
+// Records enqueue_batch for `cnt` queries as a CUDA graph whose queries and outputs
+// come from ix->call_dev; *launches = the kernels it holds.
+static cudaError_t capture_batch(msi_index* ix, cudaStream_t s, int64_t cnt, int32_t k, cudaGraphExec_t* exec,
+                                 int64_t* launches) {
+  cudaError_t e;
+  if (!ix->call_dev && (e = cudaMalloc(&ix->call_dev, sizeof(msi::CallDesc))) != cudaSuccess) return e;
+  if (!ix->call_host && (e = cudaMallocHost(&ix->call_host, sizeof(msi::CallDesc))) != cudaSuccess) return e;
+  if ((e = msi::grids_setup(ix)) != cudaSuccess) return e;
+  const int64_t before = ix->kernel_launches.load();
+  if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  const cudaError_t le = enqueue_batch(ix, s, cnt, k, nullptr, nullptr, nullptr, nullptr, ix->call_dev);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(s, &graph);
+  *launches = ix->kernel_launches.load() - before;
+  ix->kernel_launches -= *launches;  // counted when the graph runs
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return le != cudaSuccess ? le : e;
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
 static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t window, int64_t* ids,
                            float* dists, double* sqdists64, void* stream) {
   g_err.clear();
@@ -300,37 +359,45 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
     float* d_base = dists ? (d_dev ? dists + c0 * k : ix->ws_dists) : nullptr;
     double* d64_base = sqdists64 ? (d64_dev ? sqdists64 + c0 * k : ix->ws_d64) : nullptr;
     if (batched) {
-      if ((e = cudaEventRecord(ix->fork_event, s)) != cudaSuccess) return cuda_fail(e, "forking query streams");
-      for (int sl = 0; sl < ix->nslots; ++sl)
-        if ((e = cudaStreamWaitEvent(ix->slot_streams[sl], ix->fork_event, 0)) != cudaSuccess)
-          return cuda_fail(e, "forking query streams");
+      // A (queries, k) shape seen before runs as one CUDA graph, replayed with this
+      // call's pointers; a new shape launches its kernels directly (and is remembered).
+      msi_index::BatchGraph* g = nullptr;
+      for (auto& h : ix->graphs)
+        if (h.nq == cnt && h.k == k) g = &h;
+      if (ix->use_graphs && !g) {
+        if (ix->graphs.size() >= (size_t)kMaxBatchGraphs) {  // forget the oldest shape
+          if (ix->graphs.front().exec) cudaGraphExecDestroy(ix->graphs.front().exec);
+          ix->graphs.erase(ix->graphs.begin());
+        }
+        ix->graphs.push_back({cnt, k, nullptr, 0});
+      } else if (ix->use_graphs && !g->exec &&
+                 (e = capture_batch(ix, s, cnt, k, &g->exec, &g->launches)) != cudaSuccess) {
+        return cuda_fail(e, "capturing the batched query graph");
+      }
+      if (g && g->exec) {
+        *ix->call_host = msi::CallDesc{qd, id_base, d_base, d64_base};
+        if ((e = cudaMemcpyAsync(ix->call_dev, ix->call_host, sizeof(msi::CallDesc), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaGraphLaunch(g->exec, s)) != cudaSuccess)
+          return cuda_fail(e, "launching the batched query graph");
+        ix->kernel_launches += g->launches;
+      } else if ((e = enqueue_batch(ix, s, cnt, k, qd, id_base, d_base, d64_base, nullptr)) != cudaSuccess) {
+        return cuda_fail(e, "launching the query kernels");
+      }
     }
-    for (int64_t i = 0; i < cnt; ++i) {
+    for (int64_t i = 0; !batched && i < cnt; ++i) {
       cudaEvent_t ea = nullptr, em = nullptr, eb = nullptr;
       if (ix->timing) {
         ea = ix->events[3 * i];
         em = ix->events[3 * i + 1];
         eb = ix->events[3 * i + 2];
       }
-      if (batched) {
-        const int sl = (int)(i % ix->nslots);
-        e = msi::query_one(ix, ix->slots[sl], std::min(ix->nslots, msi::kSlotGridShare), qd + i * ix->len, k, id_base + i * k,
-                           d_base ? d_base + i * k : nullptr, d64_base ? d64_base + i * k : nullptr, ix->ws_ovf + i,
-                           ix->slot_streams[sl], ea, em, eb, window);
-      } else {
-        e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
-                           d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb, window);
-      }
+      e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
+                         d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb, window);
       if (e != cudaSuccess) return cuda_fail(e, "launching the query kernels");
     }
     if (batched) {
-      // join the slot streams back into the caller's stream, then run any query
-      // that overflowed a slot's bounded lists again on slot 0
-      for (int sl = 0; sl < ix->nslots; ++sl) {
-        if ((e = cudaEventRecord(ix->slot_events[sl], ix->slot_streams[sl])) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s, ix->slot_events[sl], 0)) != cudaSuccess)
-          return cuda_fail(e, "joining query streams");
-      }
+      // run any query that overflowed a slot's bounded lists again on slot 0
       std::vector<uint32_t> ovf(cnt);
       if ((e = cudaMemcpyAsync(ovf.data(), ix->ws_ovf, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost, s)) !=
               cudaSuccess ||

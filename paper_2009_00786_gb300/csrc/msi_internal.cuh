@@ -83,6 +83,16 @@ enum StatSlot {
   ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_SURVIVORS, ST_COUNT
 };
 
+// Base pointers of one batched call. A query launched from a cached CUDA graph finds
+// its input and outputs here (query qi of the call) instead of in kernel arguments, so
+// one graph serves every call of the same shape.
+struct CallDesc {
+  const float* queries;  // [nq][len]
+  int64_t* ids;          // [nq][k]
+  float* dists;          // [nq][k], or nullptr
+  double* d64;           // [nq][k], or nullptr
+};
+
 struct QueryView {
   float* qz;                    // [len]
   float* T;                     // [w][card] squared per-segment gap, query PAA to each symbol
@@ -107,6 +117,8 @@ struct QueryView {
   float* qenv;                  // [2][len]: LB_Keogh envelope of the query, upper then lower (DTW)
   uint32_t* khist;              // [256]: k > 1, kept candidates per bucket of [0, kbase)
   int window = -1;              // DTW: Sakoe-Chiba half-width; -1: Euclidean distance
+  const CallDesc* call = nullptr; // graph replay: the call's pointers (query qi of it)
+  int qi = 0;
   int k;
   float eps;                    // relative margin on squared distances
   float tau;                    // absolute margin on lower bounds (distance units)
@@ -294,6 +306,18 @@ struct msi_index {
   std::vector<cudaEvent_t> slot_events;
   cudaEvent_t fork_event = nullptr;
   uint32_t* ws_ovf = nullptr;   // [kQueryChunk]
+  // batched calls replay one CUDA graph per (queries, k); the call's pointers go to
+  // call_dev (from pinned call_host) before each replay
+  struct BatchGraph {
+    int64_t nq;
+    int32_t k;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<BatchGraph> graphs;
+  msi::CallDesc* call_dev = nullptr;
+  msi::CallDesc* call_host = nullptr;
+  bool use_graphs = true;
   int nslots = msi::kDefaultQuerySlots;
   int slot_cap = 0;
   int64_t overflow_reruns = 0;
@@ -355,9 +379,14 @@ void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap,
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
 void free_workspace(QueryView& qv);
 // window < 0: Euclidean distance; window >= 0: DTW with that Sakoe-Chiba half-width.
+// call != nullptr: q_dev / ids_dev / dists_dev / d64_dev are ignored and query qi of
+// the call descriptor is searched instead (Euclidean only).
 cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
                       float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
-                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window = -1);
+                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window = -1, const CallDesc* call = nullptr,
+                      int qi = 0);
+// Persistent grid sizes of the query kernels, computed once per index.
+cudaError_t grids_setup(msi_index* ix);
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);

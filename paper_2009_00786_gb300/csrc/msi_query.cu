@@ -220,6 +220,7 @@ __device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ 
 __global__ void __launch_bounds__(kThreads)
 q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
   pdl_begin();
+  if (qv.call) q = qv.call->queries + (size_t)qv.qi * ix.len;
   extern __shared__ float zs[];  // [len]
   __shared__ float thr_up_s[257], thr_lo_s[257];
   __shared__ float paa_s[16];
@@ -1151,6 +1152,13 @@ __global__ void __launch_bounds__(1024)
 q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out,
            double* __restrict__ d64_out) {
   pdl_begin();
+  if (qv.call) {
+    const CallDesc c = *qv.call;
+    const size_t off = (size_t)qv.qi * qv.k;
+    ids_out = c.ids + off;
+    dists_out = c.dists ? c.dists + off : nullptr;
+    d64_out = c.d64 ? c.d64 + off : nullptr;
+  }
   __shared__ unsigned long long sk[kSortCap];
   __shared__ uint32_t si[kSortCap];
   __shared__ uint32_t hist[256], sel[2], s_cnt;
@@ -1969,9 +1977,11 @@ static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const f
   return cudaGetLastError();
 }
 
+cudaError_t grids_setup(msi_index* ix) { return refine_config(ix); }
+
 cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float* q_dev, int k, int64_t* ids_dev,
                       float* dists_dev, double* d64_dev, uint32_t* ovf, cudaStream_t s, cudaEvent_t ev_a,
-                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window) {
+                      cudaEvent_t ev_m, cudaEvent_t ev_b, int window, const CallDesc* call, int qi) {
   share = std::max(1, share);
   if (window >= 0) {
     QueryView qv = ws;
@@ -1986,6 +1996,8 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   qv.k = k;
   qv.ovf = ovf;
   qv.window = -1;
+  qv.call = call;
+  qv.qi = qi;
   const int series_grid = std::max(1, ix->grid_series / share);
   const int rows_grid = std::max(1, (k == 1 ? ix->grid_rows1 : ix->grid_rowsk) / share);
   const int blocks_grid = std::max(1, ix->grid_blocks / share);

@@ -252,6 +252,40 @@ def test_batched_slots_match_single_queries_and_oracle(msi):
         assert ids_b[-2][0] == 999 and list(ids_b[-1][:min(k, 3)]) == [999, 1000, 1001][:min(k, 3)]
 
 
+def test_repeated_batched_shape_replays_with_new_pointers(msi):
+    """A batched call shape (queries, k) seen before runs as a captured CUDA graph that
+    takes its queries and outputs from a per-call descriptor: calls of the same shape
+    with other query sets and other output buffers (host, device, with and without the
+    FP64 distances) each give the oracle's answers, and every kernel is counted."""
+    import torch
+    n, length, nq, k = 6000, 256, 9, 5
+    X = datagen.walks(211, 0, n, length)
+    Z = oracle.summarise(X, 16, 256)[0]
+    sets = [datagen.paper_queries(n, length, count=nq, data_seed=211, fresh_seed=30 + j, pick_seed=40 + j)
+            for j in range(3)]
+    want = [[oracle.knn_scan(Z, oracle.znorm(q)[0], k)[0] for q in Q] for Q in sets]
+    ix = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=4)
+    msi.msi_query_stats_get(ix, reset=True)
+    calls = 0
+    for rep in range(2):
+        for j, Q in enumerate(sets):
+            ids, d = msi.msi_knn(ix, Q, k)  # host buffers
+            Qd = torch.from_numpy(Q).cuda()
+            ids_d, d_d = msi.msi_knn(ix, Qd, k)  # fresh device buffers
+            ids_x, d_x, d64_x = msi.msi_knn_ex(ix, Qd, k)
+            calls += 3
+            for i in range(nq):
+                assert np.array_equal(ids[i], want[j][i]), (rep, j, i)
+                assert np.array_equal(ids_d[i].cpu().numpy(), want[j][i]), (rep, j, i)
+                assert np.array_equal(ids_x[i].cpu().numpy(), want[j][i]), (rep, j, i)
+            assert np.array_equal(d, d_d.cpu().numpy()) and np.array_equal(d, d_x.cpu().numpy())
+            assert np.all(d64_x.cpu().numpy() >= 0)
+    st = msi.msi_query_stats_get(ix)
+    assert st["queries"] == calls * nq
+    assert st["kernel_launches"] == calls * nq * 10
+    ix.close()
+
+
 @pytest.mark.parametrize("k", [1, 10])
 def test_mixed_shapes_match_oracle(msi, k):
     """The harder value distributions (noisy sinusoids, Laplace-step walks with spike

@@ -39,7 +39,7 @@ extern "C" {
 #define MSI_API
 #endif
 
-#define MSI_ABI_VERSION 1
+#define MSI_ABI_VERSION 2
 #define MSI_MAX_SEGMENTS 16          /* one SAX word fits 16 bytes                    */
 #define MSI_MAX_CARDINALITY 256      /* 8-bit symbols (Section II-B)                  */
 #define MSI_MAX_LEN 4096             /* longest series                                */
@@ -66,6 +66,14 @@ typedef struct msi_index msi_index; /* opaque; owns all the device memory it use
                                  evenly (Section II-B), and route the approximate search
                                  down that tree; default: one bit per level, segments in
                                  turn (both give exact answers)                        */
+#define MSI_BUILD_NO_FINE_BOUND 0x4u /* keep no fine PAA. By default the index also stores
+                                 each series' means over wf equal segments (wf = the
+                                 largest of 64, 32, 16, 8 above `segments` that splits
+                                 len into power-of-two lengths; none if no such wf) as
+                                 fp16, 2 wf bytes per series, and the search bounds every
+                                 series that passes the iSAX bound by them before it
+                                 reads the series (a PAA lower bound, Section II-B, over
+                                 finer segments; answers are the same either way)      */
 
 typedef struct msi_build_opts {
   int32_t leaf_capacity; /* most series per leaf; 0 selects MSI_DEFAULT_LEAF_CAPACITY */
@@ -209,6 +217,7 @@ typedef struct msi_index_info {
   int64_t device_bytes;   /* device memory the index holds            */
   uint32_t flags;         /* MSI_BUILD_* flags it was built with      */
   int32_t device;         /* CUDA device ordinal                      */
+  int32_t fine_segments;  /* segments of the fine PAA (0: none kept)  */
 } msi_index_info;
 
 /* Shape and size of an index. `info` is a host pointer. */
@@ -224,6 +233,8 @@ MSI_API msi_status msi_index_info_get(const msi_index* index, msi_index_info* in
  *   thresholds  float[cardinality-1]: the fp32 quantisation thresholds in use (the
  *               smallest float at or above each N(0,1) breakpoint).
  *   znorm       float[n][len]: z-normalised collection (collection order).
+ *   fine        uint16[n][fine_segments]: the fine PAA, fp16 bit patterns, collection
+ *               order (ignored when the index keeps none).
  */
 typedef struct msi_export {
   uint8_t* words;
@@ -233,6 +244,7 @@ typedef struct msi_export {
   uint8_t* env_hi;
   float* thresholds;
   float* znorm;
+  uint16_t* fine;
 } msi_export;
 MSI_API msi_status msi_index_export(const msi_index* index, const msi_export* out);
 
@@ -264,8 +276,9 @@ typedef struct msi_query_stats {
                                  /* row (or DTW) refinement (timing enabled only)   */
   double filter_ms;              /* the q_filter_series part of refine_ms           */
   int64_t kernel_launches;       /* kernels the query path launched (all queries)   */
-  int64_t survivors;             /* series whose SAX-word bound passed the series   */
-                                 /* filter (they are re-tested before refinement)   */
+  int64_t survivors;             /* series that passed the series filter (the SAX-  */
+                                 /* word bound, then the fine PAA bound when the    */
+                                 /* index keeps one; re-tested before refinement)   */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises

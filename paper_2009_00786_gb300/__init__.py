@@ -22,6 +22,7 @@ __all__ = [
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
 MSI_BUILD_BORROW = 0x1
 MSI_BUILD_BALANCED_SPLIT = 0x2
+MSI_BUILD_NO_FINE_BOUND = 0x4
 MSI_MAX_K = 1024
 MSI_MAX_LEN = 4096
 
@@ -45,11 +46,13 @@ class _BuildOpts(ctypes.Structure):
 class _IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("len", ctypes.c_int32), ("segments", ctypes.c_int32),
                 ("cardinality", ctypes.c_int32), ("leaf_capacity", ctypes.c_int32), ("leaves", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("flags", ctypes.c_uint32), ("device", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("flags", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("fine_segments", ctypes.c_int32)]
 
 
 class _Export(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_void_p) for f in ("words", "perm", "leaf_begin", "env_lo", "env_hi", "thresholds", "znorm")]
+    _fields_ = [(f, ctypes.c_void_p) for f in ("words", "perm", "leaf_begin", "env_lo", "env_hi", "thresholds", "znorm",
+                                                "fine")]
 
 
 class _QueryStats(ctypes.Structure):
@@ -280,10 +283,14 @@ def msi_index_info_get(index):
     return {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
 
 
-def msi_index_export(index, words=True, perm=True, leaves=True, thresholds=True, znorm=False):
-    """msi_index_export into fresh numpy arrays (a dict)."""
+def msi_index_export(index, words=True, perm=True, leaves=True, thresholds=True, znorm=False, fine=False):
+    """msi_index_export into fresh numpy arrays (a dict); `fine` gives the fine PAA as
+    float16 [n, fine_segments] in collection order (absent when the index keeps none)."""
     n, w, L = index.n, index.segments, index.leaves
     out = {}
+    wf = msi_index_info_get(index)["fine_segments"]
+    if fine and wf:
+        out["fine"] = np.empty((n, wf), dtype=np.float16)
     if words:
         out["words"] = np.empty((n, w), dtype=np.uint8)
     if perm:

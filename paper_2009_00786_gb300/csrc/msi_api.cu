@@ -105,7 +105,7 @@ void free_index(msi_index* ix) {
   void* ptrs[] = {ix->data_owned, ix->words,     ix->perm,         ix->stats,   ix->leaf_begin, ix->env,
                   ix->benv,       ix->leaf_key,  ix->thr_up,       ix->thr_lo,  ix->qv.counters, ix->ws_qraw,
                   ix->ws_ids,     ix->ws_dists,  ix->ws_ovf,       ix->ws_d64,  ix->root_child,  ix->tree_child,
-                  ix->tree_seg};
+                  ix->tree_seg,   ix->fine};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   msi::free_workspace(ix->qv);
@@ -166,7 +166,7 @@ msi_status msi_build(const float* series, int64_t n, int32_t len, int32_t segmen
   const int32_t cap = (opts && opts->leaf_capacity) ? opts->leaf_capacity : MSI_DEFAULT_LEAF_CAPACITY;
   if (cap < 1 || cap > (1 << 24)) return fail(MSI_EINVAL, "leaf_capacity = %d outside [1, 2^24]", cap);
   const uint32_t flags = opts ? opts->flags : 0u;
-  if (flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT)) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
+  if (flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT | MSI_BUILD_NO_FINE_BOUND)) return fail(MSI_EINVAL, "unknown build flags 0x%x", flags);
   const int32_t slots = (opts && opts->query_slots) ? opts->query_slots : msi::kDefaultQuerySlots;
   if (slots < 1 || slots > 64) return fail(MSI_EINVAL, "query_slots = %d outside [1, 64]", slots);
   const int32_t slot_cap = opts ? opts->slot_capacity : 0;
@@ -475,6 +475,7 @@ msi_status msi_index_info_get(const msi_index* ix, msi_index_info* info) {
   info->device_bytes = ix->device_bytes;
   info->flags = ix->flags;
   info->device = ix->device;
+  info->fine_segments = ix->wf;
   return MSI_OK;
 }
 
@@ -513,6 +514,19 @@ msi_status msi_index_export(const msi_index* cix, const msi_export* ex) {
     }
   }
   if (ex->thresholds) std::memcpy(ex->thresholds, ix->h_thr_up + 1, sizeof(float) * (ix->card - 1));
+  if (ex->fine && ix->fine) {
+    const size_t per = (size_t)ix->wf;
+    std::vector<uint16_t> fl((size_t)n * per);
+    if (perm.empty()) {
+      perm.resize(n);
+      if ((e = cudaMemcpy(perm.data(), ix->perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "export");
+    }
+    if ((e = cudaMemcpy(fl.data(), ix->fine, sizeof(uint16_t) * fl.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "export");
+    for (int64_t p = 0; p < n; ++p)
+      std::memcpy(ex->fine + (size_t)perm[p] * per, fl.data() + (size_t)p * per, sizeof(uint16_t) * per);
+  }
   if (ex->znorm) {
     const size_t bytes = sizeof(float) * (size_t)n * ix->len;
     if (ix->data_is_z) {

@@ -36,7 +36,16 @@ struct SumOut {
   float2* stats;                // [n] collection order (mu, 1/sigma)
   float* z_out;                 // [n][len] or nullptr (borrowed data)
   unsigned long long* first_bad;  // min id of a non-finite series
+  uint4* fine;                  // [n][wf / 8] collection order: fine PAA (fp16), or nullptr
+  int wf, sf;                   // its segments and their length
 };
+
+// Writes the warp's fine PAA (fp16, staged in shared memory) as wf / 8 uint4 values.
+__device__ __forceinline__ void emit_fine(const __half* fs, int64_t i, const SumOut& o) {
+  const int lane = threadIdx.x & 31, chunks = o.wf / 8;
+  __syncwarp();
+  if (lane < chunks) o.fine[i * chunks + lane] = reinterpret_cast<const uint4*>(fs)[lane];
+}
 
 // Writes the word (symbols in a per-warp byte buffer) and the key.
 __device__ __forceinline__ void emit_word(uint8_t* sw, int sym_lane, int w, int bits, int64_t i,
@@ -61,6 +70,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
                const float* __restrict__ thr_up_g, SumOut o) {
   __shared__ float thr_s[257];
   __shared__ __align__(16) uint8_t sw_s[kSumWarps][16];
+  __shared__ __align__(16) __half fs_s[kSumWarps][kMaxFine];
   for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -68,6 +78,8 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
   const int s = 4 * G;
   const int segs_per_chunk = 128 / s;
   uint8_t* sw = sw_s[warp];
+  __half* fs = fs_s[warp];
+  const int sf = o.sf;  // fine segment length: 1, 2, or 4 Gf (Gf lanes per segment)
   for (int64_t i = (int64_t)blockIdx.x * kSumWarps + warp; i < n; i += (int64_t)gridDim.x * kSumWarps) {
     const float4* row = reinterpret_cast<const float4*>(src + i * len);
     float4 v[NC];
@@ -105,6 +117,22 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
       z.z = cst ? 0.0f : znorm_value(v[c].z, m.mu, m.rsig);
       z.w = cst ? 0.0f : znorm_value(v[c].w, m.mu, m.rsig);
       if (o.z_out) __stcs(reinterpret_cast<float4*>(o.z_out + i * len) + c * 32 + lane, z);
+      if (o.fine) {  // this lane's points are 4 (32 c + lane) .. + 3
+        const int t0 = 4 * (32 * c + lane);
+        if (sf == 1) {
+          fs[t0] = __float2half_rn(z.x);
+          fs[t0 + 1] = __float2half_rn(z.y);
+          fs[t0 + 2] = __float2half_rn(z.z);
+          fs[t0 + 3] = __float2half_rn(z.w);
+        } else if (sf == 2) {
+          fs[t0 / 2] = __float2half_rn(__fmul_rn(__fadd_rn(z.x, z.y), 0.5f));
+          fs[t0 / 2 + 1] = __float2half_rn(__fmul_rn(__fadd_rn(z.z, z.w), 0.5f));
+        } else {
+          float gf = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
+          for (int off = 1; off < sf / 4; off <<= 1) gf = __fadd_rn(gf, __shfl_xor_sync(kFull, gf, off));
+          if ((lane & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(__fdiv_rn(gf, (float)sf));
+        }
+      }
       float g = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
       for (int off = 1; off < G; off <<= 1) g = __fadd_rn(g, __shfl_xor_sync(kFull, g, off));
       if ((lane & (G - 1)) == 0) {
@@ -117,6 +145,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
     const int sym = lane < w ? sw[lane] : 0;
     if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
     emit_word(sw, sym, w, bits, i, o);
+    if (o.fine) emit_fine(fs, i, o);
     __syncwarp();
   }
 }
@@ -131,6 +160,7 @@ summarise_generic(const float* __restrict__ src, int64_t n, int len, int w, int 
   extern __shared__ float zs_all[];  // [kGenWarps][len]
   __shared__ float thr_s[257];
   __shared__ __align__(16) uint8_t sw_s[kGenWarps][16];
+  __shared__ __align__(16) __half fs_s[kGenWarps][kMaxFine];
   for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -155,6 +185,14 @@ summarise_generic(const float* __restrict__ src, int64_t n, int len, int w, int 
     __syncwarp();
     if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
     emit_word(sw, sym, w, bits, i, o);
+    if (o.fine) {
+      for (int j = lane; j < o.wf; j += 32) {
+        float g = 0.0f;
+        for (int t = j * o.sf; t < (j + 1) * o.sf; ++t) g = __fadd_rn(g, zs[t]);
+        fs_s[warp][j] = __float2half_rn(__fdiv_rn(g, (float)o.sf));
+      }
+      emit_fine(fs_s[warp], i, o);
+    }
     __syncwarp();
   }
 }
@@ -581,6 +619,16 @@ __global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, 
   stats_out[p] = stats_in[id];
 }
 
+// The fine PAA into leaf order: one thread per uint4 (chunks per series).
+__global__ void gather_fine(const uint32_t* __restrict__ perm, int64_t n, int chunks, const uint4* __restrict__ in,
+                            uint4* __restrict__ out) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n * chunks) return;
+  const int64_t p = u / chunks;
+  const int c = (int)(u - p * chunks);
+  out[u] = in[(int64_t)perm[p] * chunks + c];
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
@@ -624,6 +672,10 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(tmp.get(&ids_alt, n));
   MSI_TRY(tmp.get(&o.first_bad, 1));
   o.z_out = ix->data_owned;  // nullptr when borrowed
+  o.fine = nullptr;
+  o.wf = (ix->flags & MSI_BUILD_NO_FINE_BOUND) ? 0 : fine_segments(len, w);
+  o.sf = o.wf ? len / o.wf : 0;
+  if (o.wf) MSI_TRY(tmp.get(&o.fine, (size_t)n * (o.wf / 8)));
   MSI_TRY(cudaMemsetAsync(o.first_bad, 0xff, sizeof(unsigned long long), s));
 
   // 1. summarise
@@ -801,6 +853,13 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(cudaMemcpyAsync(ix->leaf_begin + ix->L, &nn, sizeof nn, cudaMemcpyHostToDevice, s));
   MSI_TRY(cudaMemcpyAsync(ix->perm, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
   gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.words, o.stats, ix->words, ix->stats);
+  if (o.wf) {
+    MSI_TRY(dalloc(&ix->fine, (size_t)n * (o.wf / 8)));
+    ix->wf = o.wf;
+    ix->sf = o.sf;
+    ix->device_bytes += (int64_t)n * 2 * o.wf;
+    gather_fine<<<grid_for(n * (o.wf / 8), 256), 256, 0, s>>>(ix->perm, n, o.wf / 8, o.fine, ix->fine);
+  }
   envelopes<<<grid_for(ix->L * 32, 256), 256, 0, s>>>(ix->words, ix->leaf_begin, ix->L, ka, ix->env, ix->leaf_key);
   block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, n, ix->benv);
   MSI_TRY(cudaGetLastError());

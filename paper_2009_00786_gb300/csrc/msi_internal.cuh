@@ -2,6 +2,7 @@
 // translation units (msi_api.cu, msi_build.cu, msi_query.cu).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,16 +48,32 @@ struct IndexView {
   const int32_t* root_child;
   const int32_t* tree_child;
   const int8_t* tree_seg;
+  // [n][wf / 8] leaf order: the series' means over wf equal segments of sf points
+  // (the fine PAA), fp16 rounded to nearest; null when wf = 0
+  const uint4* fine;
   int64_t n;
   int64_t L;
   int len, w, card, bits, seglen, root_bits;
+  int wf, sf;
 };
+
+constexpr int kMaxFine = 64;
+// Segments of the fine PAA: the largest of 64, 32, 16, 8 that divides len into
+// segments of a power-of-two length and exceeds the iSAX word's w; 0 when none does.
+__host__ __device__ inline int fine_segments(int len, int w) {
+  for (int wf = kMaxFine; wf >= 8; wf >>= 1) {
+    const int sf = len / wf;
+    if (len % wf == 0 && (sf & (sf - 1)) == 0 && wf > w) return wf;
+  }
+  return 0;
+}
 
 // Per-query device state (one instance per in-flight query).
 struct QState {
   float qpaa[16];
   float qup[16], qlo[16];       // per-segment interval the bounds measure gaps to: the PAA
                                 // value (Euclidean) or the envelope's [min, max] (DTW)
+  float fup[kMaxFine], flo[kMaxFine];  // the same over the fine PAA's segments
   int32_t qsym[16];             // a symbol inside that interval, per segment
   unsigned long long qkey;
   uint32_t seed_a, seed_b;      // leaf-order positions refined by the approximate search
@@ -291,6 +308,8 @@ struct msi_index {
   int32_t* tree_child = nullptr;
   int8_t* tree_seg = nullptr;
   int64_t tree_nodes = 0;
+  uint4* fine = nullptr;  // fine PAA (see IndexView); wf = 0: not kept
+  int wf = 0, sf = 0;
   int root_bits = 0;
   float h_thr_up[257];
   float h_thr_lo[257];
@@ -352,6 +371,9 @@ struct msi_index {
     v.tree_child = tree_child;
     v.tree_seg = tree_seg;
     v.root_bits = root_bits;
+    v.fine = fine;
+    v.wf = wf;
+    v.sf = sf;
     v.n = n;
     v.L = L;
     v.len = len;

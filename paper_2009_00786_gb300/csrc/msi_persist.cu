@@ -5,8 +5,8 @@
 // passes. The file holds a fixed header (parameters, array sizes and an FNV-1a
 // checksum of the index arrays) followed by the arrays in a fixed order: SAX words,
 // leaf order, per-series moments, leaf boundaries, leaf envelopes, block envelopes,
-// leaf keys, the balanced-split tree when there is one and, for an index that owns its
-// collection, the z-normalised collection.
+// leaf keys, the balanced-split tree when there is one, the fine PAA when there is one
+// and, for an index that owns its collection, the z-normalised collection.
 // A borrowed collection is not written; loading such an index takes the collection
 // again. Everything is little-endian, as both hosts that run this library are.
 #include <cuda_runtime.h>
@@ -21,7 +21,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'S', 'I', 'I', 'N', 'D', 'E', 'X'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr size_t kStage = size_t(64) << 20;  // pinned staging buffer
 
 struct FileHeader {
@@ -61,6 +61,7 @@ std::vector<Section> sections(msi_index* ix, int64_t nblk, bool with_data) {
     v.push_back({ix->tree_child, 2 * sizeof(int32_t) * (size_t)ix->tree_nodes});
     v.push_back({ix->tree_seg, sizeof(int8_t) * (size_t)ix->tree_nodes});
   }
+  if (ix->fine) v.push_back({ix->fine, sizeof(uint16_t) * (size_t)ix->n * ix->wf});
   if (with_data) v.push_back({ix->data_owned, sizeof(float) * (size_t)ix->n * ix->len});
   return v;
 }
@@ -195,13 +196,15 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
                         h.w <= MSI_MAX_SEGMENTS && h.len % h.w == 0 && h.seglen == h.len / h.w && h.card >= 2 &&
                         h.card <= MSI_MAX_CARDINALITY && (h.card & (h.card - 1)) == 0 && (1 << h.bits) == h.card &&
                         h.cap >= 1 && h.L >= 1 && h.L <= h.n && h.nblk == (h.n + 31) / 32 &&
-                        (h.flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT)) == 0 &&
+                        (h.flags & ~(MSI_BUILD_BORROW | MSI_BUILD_BALANCED_SPLIT | MSI_BUILD_NO_FINE_BOUND)) == 0 &&
                         h.data_is_z == ((h.flags & MSI_BUILD_BORROW) ? 0 : 1);
   const bool tree = (h.flags & MSI_BUILD_BALANCED_SPLIT) != 0;
   const bool tree_ok = tree ? (h.root_bits == h.w && h.tree_nodes >= 1 && h.tree_nodes <= 2 * h.n + (1ll << h.w))
                             : (h.root_bits == 0 && h.tree_nodes == 0);
   if (!shape_ok || !tree_ok) return fail(MSI_EINVAL, "inconsistent index file header");
   const bool borrow = (h.flags & MSI_BUILD_BORROW) != 0;
+  // the fine PAA's shape follows from the parameters, as in the build
+  const int wf = (h.flags & MSI_BUILD_NO_FINE_BOUND) ? 0 : msi::fine_segments(h.len, h.w);
   if (borrow && !series) return fail(MSI_EINVAL, "the index borrows its collection: pass the same collection");
   if (!borrow && series) return fail(MSI_EINVAL, "the index holds its collection: series must be NULL");
   // the file size must match the header before anything is allocated
@@ -210,8 +213,9 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
                              sizeof(uint32_t) * (size_t)(h.L + 1) + sizeof(uint4) * 2 * (size_t)h.L +
                              sizeof(uint4) * 2 * (size_t)h.nblk + sizeof(uint64_t) * (size_t)h.L;
     const size_t tree_bytes = tree ? (sizeof(int32_t) << h.root_bits) + 9 * (size_t)h.tree_nodes : 0;
-    const size_t want =
-        sizeof(FileHeader) + idx_bytes + tree_bytes + (borrow ? 0 : sizeof(float) * (size_t)h.n * h.len);
+    const size_t fine_bytes = sizeof(uint16_t) * (size_t)h.n * wf;
+    const size_t want = sizeof(FileHeader) + idx_bytes + tree_bytes + fine_bytes +
+                        (borrow ? 0 : sizeof(float) * (size_t)h.n * h.len);
     if (fseek(in.f, 0, SEEK_END) != 0) return fail(MSI_EINTERNAL, "seeking the index file");
     const long long got = ftell(in.f);
     if (got < 0 || (size_t)got != want) return fail(MSI_EINVAL, "truncated or oversized index file");
@@ -268,13 +272,16 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
       (tree && (e = cudaMalloc(&ix->root_child, sizeof(int32_t) << h.root_bits)) != cudaSuccess) ||
       (tree && (e = cudaMalloc(&ix->tree_child, 2 * sizeof(int32_t) * (size_t)h.tree_nodes)) != cudaSuccess) ||
       (tree && (e = cudaMalloc(&ix->tree_seg, (size_t)h.tree_nodes)) != cudaSuccess) ||
+      (wf && (e = cudaMalloc(&ix->fine, sizeof(uint16_t) * (size_t)h.n * wf)) != cudaSuccess) ||
       (!borrow && (e = cudaMalloc(&ix->data_owned, sizeof(float) * (size_t)h.n * h.len)) != cudaSuccess) ||
       (e = cudaMallocHost(&stage.p, kStage)) != cudaSuccess) {
     st = cuda_fail(e, "allocating the index");
     goto fail_out;
   }
   ix->data = borrow ? series : ix->data_owned;
-  ix->device_bytes = (int64_t)(sizeof(uint4) + sizeof(uint32_t) + sizeof(float2)) * h.n +
+  ix->wf = wf;
+  ix->sf = wf ? h.len / wf : 0;
+  ix->device_bytes = (int64_t)2 * wf * h.n + (int64_t)(sizeof(uint4) + sizeof(uint32_t) + sizeof(float2)) * h.n +
                      (int64_t)(4 + 32 + 8) * h.L + 32 * h.nblk + (borrow ? 0 : 4 * h.n * h.len);
   secs = sections(ix, h.nblk, !borrow);
   for (size_t si = 0; si < secs.size(); ++si) {

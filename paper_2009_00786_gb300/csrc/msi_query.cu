@@ -12,7 +12,9 @@
 //   q_front         the lowest-bound surviving leaves refined first (the head of the
 //                   priority order of ProcessQueue, Algorithm 8);
 //   q_filter_blocks bounds of 32-position blocks of the surviving leaves;
-//   q_filter_series per-series bounds from the SAX words (Algorithm 9's lower bound);
+//   q_filter_series per-series bounds from the SAX words (Algorithm 9's lower bound),
+//                   then, for those that pass, from the fine PAA (64 fp16 segment means
+//                   at most) before any row is read;
 //   q_refine_rows   real distances of the survivors (CalculateRealDistance,
 //                   Algorithm 9); the BSF is an atomicMin on the bits of a
 //                   non-negative float, each item re-tested against it (Algorithm 8);
@@ -216,6 +218,34 @@ __device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ 
   for (int i = 4 * n4 + threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
+// Lower bound^2 of position p from the fine PAA: sf times the sum over the fine
+// segments of the squared gap between the series' mean and the query's interval
+// [lo_j, up_j]. The stored mean h is fp16, within e = |h| 2^-11 + 2^-25 of the fp32
+// mean (half an fp16 ulp), so each gap is taken e short; every step rounds down.
+__device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t p) {
+  const int chunks = ix.wf >> 3;
+  const uint4* src = ix.fine + (size_t)p * chunks;
+  float acc = 0.0f;
+  for (int c = 0; c < chunks; ++c) {
+    const uint4 v = __ldg(src + c);
+    const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int h2 = 0; h2 < 4; ++h2) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&parts[h2]));
+      const float hv[2] = {f.x, f.y};
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2) {
+        const int j = 8 * c + 2 * h2 + e2;
+        const float h = hv[e2];
+        const float e = __fmaf_ru(fabsf(h), 4.8828125e-4f, 2.98023223876953125e-8f);
+        const float g = fmaxf(0.0f, fmaxf(__fsub_rd(__fsub_rd(h, fup[j]), e), __fsub_rd(__fsub_rd(flo[j], h), e)));
+        acc = __fmaf_rd(g, g, acc);
+      }
+    }
+  }
+  return __fmul_rd(acc, (float)ix.sf);
+}
+
 // ------------------------------------------------------------------ q_prep
 __global__ void __launch_bounds__(kThreads)
 q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
@@ -320,6 +350,25 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
       }
       qv.T5[e] = __fmul_rn(d, d);
     }
+  }
+  // the same intervals over the fine PAA's segments
+  for (int j = tid; j < ix.wf; j += blockDim.x) {
+    float u, l;
+    if (qv.window >= 0) {
+      const int a = max(0, j * ix.sf - qv.window), b = min(ix.len - 1, (j + 1) * ix.sf - 1 + qv.window);
+      u = -INFINITY;
+      l = INFINITY;
+      for (int x = a; x <= b; ++x) {
+        u = fmaxf(u, zs[x]);
+        l = fminf(l, zs[x]);
+      }
+    } else {
+      float g = 0.0f;
+      for (int t = j * ix.sf; t < (j + 1) * ix.sf; ++t) g = __fadd_rn(g, zs[t]);
+      u = l = __fdiv_rn(g, (float)ix.sf);
+    }
+    qv.st->fup[j] = u;
+    qv.st->flo[j] = l;
   }
   if (tid < ix.w) {
     qv.st->qpaa[tid] = paa_s[tid];
@@ -632,7 +681,12 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   extern __shared__ __align__(16) float qs[];
   __shared__ unsigned s_min;
   __shared__ uint32_t s_leaf[kMaxFront], s_beg[kMaxFront], s_pre[kMaxFront + 1];
+  __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(qs, qv.qz, ix.len);
+  for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
+    fup_s[j] = qv.st->fup[j];
+    flo_s[j] = qv.st->flo[j];
+  }
   if (threadIdx.x == 0) s_min = 0x7f800000u;
   const int nf = front_leaves(ix, qv, nblockmin, front_count(qv.k), s_leaf, s_beg, s_pre);
   QState* st = qv.st;
@@ -646,14 +700,16 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   const unsigned thr = *(volatile unsigned*)&st->thr_bits;
   const float keep2 = keep_bound2(thr, qv.eps);
   const uint32_t warps = gridDim.x * (kThreads / 32);
+  const uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   unsigned bestd = 0x7f800000u;
   uint32_t n_front = 0;
-  for (uint32_t g = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); g < total; g += warps) {
+  auto position = [&](uint32_t g) {
     int f = 0;
     while (g >= s_pre[f + 1]) ++f;
-    const uint32_t pos = s_beg[f] + (g - s_pre[f]);
-    if (pos >= sa && pos < sb) continue;  // already refined by the seed
+    return s_beg[f] + (g - s_pre[f]);
+  };
+  auto refine = [&](uint32_t pos) {
     const uint32_t id = ix.perm[pos];
     const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
     const float d2 = warp_sqdist(ix, id, ms, qs);
@@ -666,6 +722,23 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
       }
     }
     bestd = min(bestd, __float_as_uint(d2));
+  };
+  const float lbb = lb_bound2(thr, qv.eps, qv.tau);
+  if (ix.wf && lbb < INFINITY) {
+    // a warp takes 32 rows: each lane bounds one by the fine PAA (against the seed's
+    // BSF), and only the rows that pass are read
+    for (uint32_t g0 = gw * 32; g0 < total; g0 += warps * 32) {
+      const uint32_t g = g0 + lane;
+      const uint32_t pos = g < total ? position(g) : 0u;
+      const bool want = g < total && !(pos >= sa && pos < sb) && fine_lb2(ix, fup_s, flo_s, pos) <= lbb;
+      for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
+    }
+  } else {
+    for (uint32_t g = gw; g < total; g += warps) {
+      const uint32_t pos = position(g);
+      if (pos >= sa && pos < sb) continue;  // already refined by the seed
+      refine(pos);
+    }
   }
   __shared__ unsigned s_n;
   if (threadIdx.x == 0) s_n = 0;
@@ -691,9 +764,9 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
 //   positions): re-tests the leaf's bound against the current BSF and bounds the
 //   block by its symbol envelope; surviving blocks become tasks.
 // q_filter_series: a warp per task bounds every position by its SAX word (a coarse
-//   bound first, then the full one); survivors {position, bound} go to a per-warp
-//   buffer flushed 32 at a time to the survivor list. kUnroll tasks are in flight per
-//   warp.
+//   bound first, then the full one, then the fine PAA's when the index keeps one);
+//   survivors {position, bound} go to a per-warp buffer flushed 32 at a time to the
+//   survivor list. kUnroll tasks are in flight per warp.
 // q_refine_rows: real distances of the survivors whose bound still passes the
 //   current BSF, kRows rows per warp at a time. k = 1: the BSF is an atomicMin taken
 //   only by a distance below the current BSF. k > 1: the shared candidate histogram
@@ -784,8 +857,13 @@ q_filter_series(IndexView ix, QueryView qv) {
   __shared__ uint2 buf_s[kFiltWarps][64];
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
+  __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   smem_fill(T5s, qv.T5, ix.w * 32);
+  for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
+    fup_s[j] = qv.st->fup[j];
+    flo_s[j] = qv.st->flo[j];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
@@ -806,8 +884,12 @@ q_filter_series(IndexView ix, QueryView qv) {
   auto drain32 = [&](uint32_t count) {
     const bool have = lane < (int)count;
     const uint32_t p = have ? qp[lane] : 0u;
-    const float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
-    const bool pass = have && lb2 <= bound2;
+    float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
+    bool pass = have && lb2 <= bound2;
+    if (pass && ix.wf) {  // the fine PAA's bound, before the series is read
+      lb2 = fmaxf(lb2, fine_lb2(ix, fup_s, flo_s, p));
+      pass = lb2 <= bound2;
+    }
     __syncwarp();
     if (count > 32 && lane < (int)count - 32) {  // move the rest of the queue down
       qw[lane] = qw[32 + lane];

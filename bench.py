@@ -417,11 +417,13 @@ def main():
     launches = max(1, st["refine_launches"])
     main_refined = st["series_refined"] - st["seed_series"]
     # algorithmic bytes per launch:
-    # q_filter_series: 16 per SAX word bounded + 8 per block task read + 8 per survivor
-    # written (survivors counted by the rows they became); row refinement: 8 per
-    # survivor read + 4 len + 4 + 8 per refined series (row, perm, moments) + 8 per kept
-    # candidate
-    filt_bytes = (16 * st["series_lower_bounded"] + 8 * st["blocks_examined"] + 8 * main_refined) / launches
+    # q_filter_series: 16 per SAX word bounded + 8 per block task read + 2 wf per fine
+    # PAA read (wf fp16 means) + 8 per survivor written (survivors counted by the rows
+    # they became); row refinement: 8 per survivor read + 4 len + 4 + 8 per refined
+    # series (row, perm, moments) + 8 per kept candidate
+    wf = msi.msi_index_info_get(index)["fine_segments"]
+    filt_bytes = (16 * st["series_lower_bounded"] + 8 * st["blocks_examined"] + 2 * wf * st["fine_bounded"]
+                  + 8 * main_refined) / launches
     rows_bytes = ((8 + 4 * length + 4 + 8) * main_refined + 8 * st["candidates"]) / launches
     filt_s = st["filter_ms"] / launches / 1e3
     rows_s = (st["refine_ms"] - st["filter_ms"]) / launches / 1e3
@@ -471,8 +473,10 @@ def main():
         "refine_kernels": kernels,
         # every kernel of the chain together, over the timed batched steps: leaves (40 B
         # each), block envelopes and tasks (40 B per block bounded), SAX words (16 B),
-        # rows of the seed, front leaves and survivors (4 len + 12 B), candidates (8 B)
+        # fine PAA means (2 wf B per series or front row bounded by them), rows of the
+        # seed, front leaves and survivors (4 len + 12 B), candidates (8 B)
         "step_alg_gbs": (40 * st["leaves_total"] + 40 * st["blocks_examined"] + 16 * st["series_lower_bounded"]
+                         + 2 * wf * (st["fine_bounded"] + st["front_fine_bounded"])
                          + (4 * length + 12) * st["series_refined"] + 8 * st["candidates"])
                         / max(1, st["queries"]) * qps / 1e9,
         "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if not kk.endswith("_ms")},

@@ -279,6 +279,8 @@ typedef struct msi_query_stats {
   int64_t survivors;             /* series that passed the series filter (the SAX-  */
                                  /* word bound, then the fine PAA bound when the    */
                                  /* index keeps one; re-tested before refinement)   */
+  int64_t fine_bounded;          /* series the series filter bounded by the fine PAA */
+  int64_t front_fine_bounded;    /* front-leaf rows bounded by the fine PAA         */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises

@@ -603,6 +603,8 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->filter_ms = ix->filter_ms;
   st->kernel_launches = ix->kernel_launches.load();
   st->survivors = (int64_t)c[msi::ST_SURVIVORS];
+  st->fine_bounded = (int64_t)c[msi::ST_FINE];
+  st->front_fine_bounded = (int64_t)c[msi::ST_FINE_FRONT];
   if (reset) {
     if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_COUNT)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");

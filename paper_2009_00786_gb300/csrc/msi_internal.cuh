@@ -91,13 +91,15 @@ struct QState {
   unsigned int rc_count;        // FP64 re-checks appended
   unsigned int final_bits;      // k-th smallest candidate squared distance (fp32 bits)
   unsigned int series_refined;
+  unsigned int fine_front;      // front-leaf rows bounded by the fine PAA
   int32_t flag;                 // 1 constant query, -1 non-finite query
 };
 
 // Device-wide work counters (u64), in msi_query_stats field order.
 enum StatSlot {
   ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_SURVIVED, ST_LEAVES_PROCESSED, ST_SERIES_LB,
-  ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_SURVIVORS, ST_COUNT
+  ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_SURVIVORS, ST_FINE, ST_FINE_FRONT,
+  ST_COUNT
 };
 
 // Base pointers of one batched call. A query launched from a cached CUDA graph finds
@@ -125,7 +127,7 @@ struct QueryView {
   double* rc_d;                 // [n]
   uint32_t* rc_id;              // [n]
   unsigned long long* counters; // [ST_COUNT]
-  uint32_t* partials;           // [kMaxRefineWarps][3]: per-warp work counters of the refinement
+  uint32_t* partials;           // [4][kMaxRefineWarps]: per-warp work counters of the refinement
   uint32_t npartials;           // warps of the series filter launch
   uint32_t npartials_rows;      // warps of the row (or DTW) refinement launch
   uint32_t cand_cap;            // entries of cand / rc_d / rc_id

@@ -246,6 +246,23 @@ __device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup,
   return __fmul_rd(acc, (float)ix.sf);
 }
 
+// The same bound computed by a whole warp for one position (lane l takes segments l,
+// l + 32, ...); every lane returns lane 0's sum.
+__device__ __forceinline__ float warp_fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t p) {
+  const int lane = threadIdx.x & 31;
+  const __half* src = reinterpret_cast<const __half*>(ix.fine) + (size_t)p * ix.wf;
+  float acc = 0.0f;
+  for (int j = lane; j < ix.wf; j += 32) {
+    const float h = __half2float(src[j]);
+    const float e = __fmaf_ru(fabsf(h), 4.8828125e-4f, 2.98023223876953125e-8f);
+    const float g = fmaxf(0.0f, fmaxf(__fsub_rd(__fsub_rd(h, fup[j]), e), __fsub_rd(__fsub_rd(flo[j], h), e)));
+    acc = __fmaf_rd(g, g, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = __fadd_rd(acc, __shfl_xor_sync(kFull, acc, o));
+  return __shfl_sync(kFull, __fmul_rd(acc, (float)ix.sf), 0);
+}
+
 // ------------------------------------------------------------------ q_prep
 __global__ void __launch_bounds__(kThreads)
 q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
@@ -442,6 +459,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->rc_count = 0;
     st->final_bits = 0;
     st->series_refined = 0;
+    st->fine_front = 0;
   }
 }
 
@@ -703,7 +721,7 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   const uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   unsigned bestd = 0x7f800000u;
-  uint32_t n_front = 0;
+  uint32_t n_front = 0, n_fine = 0;
   auto position = [&](uint32_t g) {
     int f = 0;
     while (g >= s_pre[f + 1]) ++f;
@@ -730,7 +748,9 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
     for (uint32_t g0 = gw * 32; g0 < total; g0 += warps * 32) {
       const uint32_t g = g0 + lane;
       const uint32_t pos = g < total ? position(g) : 0u;
-      const bool want = g < total && !(pos >= sa && pos < sb) && fine_lb2(ix, fup_s, flo_s, pos) <= lbb;
+      const bool screen = g < total && !(pos >= sa && pos < sb);
+      n_fine += __popc(__ballot_sync(kFull, screen));
+      const bool want = screen && fine_lb2(ix, fup_s, flo_s, pos) <= lbb;
       for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
     }
   } else {
@@ -740,16 +760,18 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
       refine(pos);
     }
   }
-  __shared__ unsigned s_n;
-  if (threadIdx.x == 0) s_n = 0;
+  __shared__ unsigned s_n, s_nf;
+  if (threadIdx.x == 0) s_n = s_nf = 0;
   __syncthreads();
   if (lane == 0) {
     if (bestd < 0x7f800000u) atomicMin(&s_min, bestd);
     if (n_front) atomicAdd(&s_n, n_front);
+    if (n_fine) atomicAdd(&s_nf, n_fine);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_n) atomicAdd(&st->series_refined, s_n);  // one global atomic per block
+    if (s_nf) atomicAdd(&st->fine_front, s_nf);
     if (qv.k == 1 && s_min < thr) atomicMin(&st->thr_bits, s_min);
   }
 }
@@ -877,7 +899,7 @@ q_filter_series(IndexView ix, QueryView qv) {
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
-  uint32_t nbuf = 0, nq = 0, n_lb = 0;
+  uint32_t nbuf = 0, nq = 0, n_lb = 0, n_fine = 0;
   float bound2 = 0.0f;
 
   // full bounds of the first 32 queued words (one per lane); survivors to the buffer
@@ -887,6 +909,7 @@ q_filter_series(IndexView ix, QueryView qv) {
     float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
     bool pass = have && lb2 <= bound2;
     if (pass && ix.wf) {  // the fine PAA's bound, before the series is read
+      ++n_fine;
       lb2 = fmaxf(lb2, fine_lb2(ix, fup_s, flo_s, p));
       pass = lb2 <= bound2;
     }
@@ -973,10 +996,14 @@ q_filter_series(IndexView ix, QueryView qv) {
     else st->overflow = 1u;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) n_lb += __shfl_xor_sync(kFull, n_lb, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    n_lb += __shfl_xor_sync(kFull, n_lb, o);
+    n_fine += __shfl_xor_sync(kFull, n_fine, o);
+  }
   if (lane == 0 && gw < kMaxRefineWarps) {
     qv.partials[gw] = n_lb;
     qv.partials[2 * kMaxRefineWarps + gw] = gw == 0 ? ntask : 0u;
+    qv.partials[3 * kMaxRefineWarps + gw] = n_fine;
   }
 }
 
@@ -1334,14 +1361,15 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     if (d64_out) d64_out[r] = __longlong_as_double((long long)sk[r]);
   }
   // sum the refinement's per-warp work counters
-  __shared__ unsigned long long s_part[3];
-  if (threadIdx.x < 3) s_part[threadIdx.x] = 0;
+  __shared__ unsigned long long s_part[4];
+  if (threadIdx.x < 4) s_part[threadIdx.x] = 0;
   __syncthreads();
   {
-    unsigned long long a = 0, b = 0, cc = 0;
+    unsigned long long a = 0, b = 0, cc = 0, fc = 0;
     for (uint32_t i = threadIdx.x; i < qv.npartials; i += blockDim.x) {
       a += qv.partials[i];
       cc += qv.partials[2 * kMaxRefineWarps + i];
+      fc += qv.partials[3 * kMaxRefineWarps + i];
     }
     for (uint32_t i = threadIdx.x; i < qv.npartials_rows; i += blockDim.x) b += qv.partials[kMaxRefineWarps + i];
 #pragma unroll
@@ -1349,11 +1377,13 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
       a += __shfl_xor_sync(kFull, a, o);
       b += __shfl_xor_sync(kFull, b, o);
       cc += __shfl_xor_sync(kFull, cc, o);
+      fc += __shfl_xor_sync(kFull, fc, o);
     }
     if ((threadIdx.x & 31) == 0) {  // one shared atomic per warp
       atomicAdd(&s_part[0], a);
       atomicAdd(&s_part[1], b);
       atomicAdd(&s_part[2], cc);
+      atomicAdd(&s_part[3], fc);
     }
   }
   __syncthreads();
@@ -1371,6 +1401,8 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
     atomicAdd(&c[ST_RECHECKED], (unsigned long long)R);
     atomicAdd(&c[ST_SURVIVORS], (unsigned long long)st->surv_count);
+    atomicAdd(&c[ST_FINE], s_part[3]);
+    atomicAdd(&c[ST_FINE_FRONT], (unsigned long long)st->fine_front);
   }
 }
 
@@ -1540,6 +1572,11 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
   float* edge = ys + n4;
   smem_fill(qs, qv.qz, ix.len);
   __shared__ uint32_t s_leaf[kMaxFront], s_beg[kMaxFront], s_pre[kMaxFront + 1];
+  __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
+  for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
+    fup_s[j] = qv.st->fup[j];
+    flo_s[j] = qv.st->flo[j];
+  }
   const int nf = front_leaves(ix, qv, nblockmin, front_count(qv.k), s_leaf, s_beg, s_pre);
   QState* st = qv.st;
   if (nf == 0) return;  // the same in every thread of the block
@@ -1550,15 +1587,20 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
   }
   const uint32_t total = s_pre[nf];
   const uint32_t sa = st->seed_a, sb = st->seed_b;
-  __shared__ unsigned s_n;
-  if (threadIdx.x == 0) s_n = 0;
+  __shared__ unsigned s_n, s_nf;
+  if (threadIdx.x == 0) s_n = s_nf = 0;
   __syncthreads();
-  uint32_t n_front = 0;
+  uint32_t n_front = 0, n_fine = 0;
   for (uint32_t g = blockIdx.x * kDtwWarps + warp; g < total; g += gridDim.x * kDtwWarps) {
     int f = 0;
     while (g >= s_pre[f + 1]) ++f;
     const uint32_t pos = s_beg[f] + (g - s_pre[f]);
     if (pos >= sa && pos < sb) continue;  // already refined by the seed
+    if (ix.wf) {  // the fine PAA's bound against the envelope, before the row is read
+      const unsigned thr0 = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
+      ++n_fine;
+      if (warp_fine_lb2(ix, fup_s, flo_s, pos) > lb_bound2(thr0, qv.eps, qv.tau)) continue;
+    }
     stage_row(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
     const float keep2 = keep_bound2(thr, qv.eps);
@@ -1575,8 +1617,10 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
     __syncwarp();
   }
   if (lane == 0 && n_front) atomicAdd(&s_n, n_front);
+  if (lane == 0 && n_fine) atomicAdd(&s_nf, n_fine);
   __syncthreads();
   if (threadIdx.x == 0 && s_n) atomicAdd(&st->series_refined, s_n);
+  if (threadIdx.x == 0 && s_nf) atomicAdd(&st->fine_front, s_nf);
 }
 
 // One warp per survivor of the series filter: re-test its bound against the current
@@ -1841,7 +1885,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.items, items)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * items)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.partials, (size_t)3 * kMaxRefineWarps)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.partials, (size_t)4 * kMaxRefineWarps)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.blockmin, (size_t)(ix->L / kThreads + 2))) != cudaSuccess) return e;
   if ((e = dalloc(&qv.cand, (size_t)cand_cap)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.rc_d, (size_t)cand_cap)) != cudaSuccess) return e;

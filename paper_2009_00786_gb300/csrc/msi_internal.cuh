@@ -92,6 +92,7 @@ struct QState {
   unsigned int final_bits;      // k-th smallest candidate squared distance (fp32 bits)
   unsigned int series_refined;
   unsigned int fine_front;      // front-leaf rows bounded by the fine PAA
+  unsigned int seed_done;       // seed rows whose distance was computed
   int32_t flag;                 // 1 constant query, -1 non-finite query
 };
 

@@ -36,6 +36,8 @@ namespace msi {
 namespace {
 
 constexpr int kThreads = 256;
+// Seed rows a warp takes at once when their fine PAA bounds order them (k = 1).
+constexpr int kSeedGroup = 8;
 
 // Programmatic dependent launch (sm_90 and later): the query kernels are launched so
 // that one may start while the previous kernel of its stream is finishing (its launch
@@ -460,6 +462,7 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
     st->final_bits = 0;
     st->series_refined = 0;
     st->fine_front = 0;
+    st->seed_done = (uint32_t)(b - a);
   }
 }
 
@@ -512,29 +515,75 @@ __global__ void __launch_bounds__(kThreads)
 q_seed(IndexView ix, QueryView qv) {
   pdl_begin();
   extern __shared__ __align__(16) float qs[];
+  __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(qs, qv.qz, ix.len);
+  for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
+    fup_s[j] = qv.st->fup[j];
+    flo_s[j] = qv.st->flo[j];
+  }
   __syncthreads();
   __shared__ unsigned s_min;
   if (threadIdx.x == 0) s_min = 0x7f800000u;
   const uint32_t a = qv.st->seed_a, b = qv.st->seed_b;
   const uint32_t warps = gridDim.x * (kThreads / 32);
+  const int lane = threadIdx.x & 31;
   unsigned best = 0x7f800000u;
-  for (uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); gw < b - a; gw += warps) {
-    const uint32_t pos = a + gw;
-    const uint32_t id = ix.perm[pos];
-    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
-    const float d2 = warp_sqdist(ix, id, ms, qs);
-    if ((threadIdx.x & 31) == 0) {
-      if (gw < qv.cand_cap) qv.cand[gw] = pack(d2, pos);
+  uint32_t n_skip = 0;  // seed rows the fine bound ruled out (counted by every lane)
+  auto refine = [&](uint32_t g) {  // row g of the seed: a candidate, and the BSF for k = 1
+    const uint32_t pos = a + g;
+    const float d2 = warp_sqdist(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], qs);
+    if (lane == 0) {
+      if (g < qv.cand_cap) qv.cand[g] = pack(d2, pos);
       else qv.st->overflow = 1u;
+      if (qv.k == 1 && ix.wf) atomicMin(&qv.st->thr_bits, __float_as_uint(d2));  // the screens read it
     }
     best = min(best, __float_as_uint(d2));
+  };
+  if (qv.k == 1 && ix.wf) {
+    // k = 1 with the fine PAA: a warp takes kSeedGroup rows, refines the one with the
+    // smallest fine bound (its distance joins the BSF at once), then only the others
+    // whose fine bound still passes the BSF; the rest become +inf candidates
+    const uint32_t nrow = b - a;
+    for (uint32_t g0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * kSeedGroup; g0 < nrow;
+         g0 += warps * kSeedGroup) {
+      const uint32_t g = g0 + lane;
+      const bool have = lane < kSeedGroup && g < nrow;
+      const float lb = have ? fine_lb2(ix, fup_s, flo_s, a + g) : INFINITY;
+      float m = lb;
+      int mi = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float om = __shfl_xor_sync(kFull, m, o);
+        const int oi = __shfl_xor_sync(kFull, mi, o);
+        if (om < m || (om == m && oi < mi)) {
+          m = om;
+          mi = oi;
+        }
+      }
+      if (!(m < INFINITY)) mi = 0;
+      refine(g0 + mi);
+      const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&qv.st->thr_bits : 0u, 0);
+      const bool rest = have && lane != mi;
+      const bool pass = rest && lb <= lb_bound2(thr, qv.eps, qv.tau);
+      if (rest && !pass) {
+        if (g < qv.cand_cap) qv.cand[g] = pack(INFINITY, a + g);
+        else qv.st->overflow = 1u;
+      }
+      n_skip += __popc(__ballot_sync(kFull, rest && !pass));
+      for (unsigned mk = __ballot_sync(kFull, pass); mk; mk &= mk - 1) refine(g0 + __ffs(mk) - 1);
+    }
+  } else {
+    for (uint32_t gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); gw < b - a; gw += warps) refine(gw);
   }
   // k = 1: one atomicMin per block, on the block's smallest distance
+  __shared__ unsigned s_skip;
+  if (threadIdx.x == 0) s_skip = 0;
   __syncthreads();
   if ((threadIdx.x & 31) == 0 && best < 0x7f800000u) atomicMin(&s_min, best);
+  if ((threadIdx.x & 31) == 0 && n_skip) atomicAdd(&s_skip, n_skip);
   __syncthreads();
   if (threadIdx.x == 0 && qv.k == 1 && s_min < 0x7f800000u) atomicMin(&qv.st->thr_bits, s_min);
+  if (threadIdx.x == 0 && s_skip) atomicSub(&qv.st->seed_done, s_skip);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -805,6 +854,22 @@ constexpr int kBlkThreads = 256;
 // leaf bound against the current BSF, bounds the block by its symbol envelope
 // (T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range),
 // and lists the surviving blocks; the list is compacted per CTA (one atomic per CTA).
+// Squared iSAX bound of a symbol envelope (per-segment min / max symbols lo, hi):
+// T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range.
+__device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
+                                         float seglen) {
+  const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j < w) {
+      const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
+      acc = __fadd_rn(acc, Ts[j * card + min(max(qsym[j], sl), sh)]);
+    }
+  }
+  return __fmul_rn(acc, seglen);
+}
+
 __global__ void __launch_bounds__(kBlkThreads)
 q_filter_blocks(IndexView ix, QueryView qv) {
   pdl_begin();
@@ -830,17 +895,8 @@ q_filter_blocks(IndexView ix, QueryView qv) {
       bool front = false;  // a leaf refined early
       for (uint32_t f = 0; f < nfront; ++f) front |= fl_s[f] == item.w;
       if (!front && __uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
-        const uint4 lo = __ldg(ix.benv + 2 * blk), hi = __ldg(ix.benv + 2 * blk + 1);
-        const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
-        float acc = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (j < ix.w) {
-            const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
-            acc = __fadd_rn(acc, Ts[j * ix.card + min(max(qsym_s[j], sl), sh)]);
-          }
-        }
-        if (__fmul_rn(acc, seglen) <= bound2) {
+        if (env_lb2(__ldg(ix.benv + 2 * blk), __ldg(ix.benv + 2 * blk + 1), Ts, qsym_s, ix.w, ix.card, seglen) <=
+            bound2) {
           // task: block index, and the block's positions inside the item: [lo, hi) offsets
           const uint32_t lo_off = max(item.x, blk * 32) - blk * 32, hi_off = min(item.y, blk * 32 + 32) - blk * 32;
           s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, lo_off | (hi_off << 8));
@@ -1395,7 +1451,7 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     atomicAdd(&c[ST_LEAVES_SURVIVED], (unsigned long long)st->leaf_count);
     atomicAdd(&c[ST_LEAVES_PROCESSED], s_part[2]);
     atomicAdd(&c[ST_SERIES_LB], s_part[0]);
-    const unsigned long long seed = st->seed_b - st->seed_a;
+    const unsigned long long seed = st->seed_done;
     atomicAdd(&c[ST_SERIES_REFINED], s_part[1] + seed + st->series_refined);
     atomicAdd(&c[ST_SEED], seed + st->series_refined);
     atomicAdd(&c[ST_CANDIDATES], (unsigned long long)st->cand_count);
@@ -2134,7 +2190,10 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   MSI_LAUNCH(q_prep, 1, kThreads, qbytes, s, v, q_dev, qv, k);
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);
-  MSI_LAUNCH(q_seed, (unsigned)std::min<int64_t>((seed_max + 7) / 8, 1024), kThreads, qbytes, s, v, qv);
+  // a warp per seed row; k = 1 with the fine PAA: a warp per kSeedGroup rows
+  const int64_t seed_per_block = (k == 1 && ix->wf) ? 8 * kSeedGroup : 8;
+  MSI_LAUNCH(q_seed, (unsigned)std::min<int64_t>((seed_max + seed_per_block - 1) / seed_per_block, 1024), kThreads,
+             qbytes, s, v, qv);
   if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 0);
   const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
   MSI_LAUNCH(q_leaf_filter, nlf, kThreads, 0, s, v, qv);

@@ -86,7 +86,15 @@ def test_answers_match_oracle_and_fewer_rows_are_read(msi, length):
             for i, q in enumerate(Q):
                 oid, _ = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
                 assert np.array_equal(ids[i], oid), (name, k, i)
-        refined[name] = msi.msi_query_stats_get(ix)["series_refined"]
+        st = msi.msi_query_stats_get(ix)
+        refined[name] = st["series_refined"]
+        # the fine bound runs only on the index that keeps the fine PAA, and only on
+        # series whose iSAX bound passed (so never more often than the words bounded)
+        if name == "on":
+            assert 0 < st["fine_bounded"] <= st["series_lower_bounded"]
+            assert st["survivors"] <= st["fine_bounded"]
+        else:
+            assert st["fine_bounded"] == 0 and st["front_fine_bounded"] == 0
     assert refined["on"] < refined["off"], refined
     for name, ix in (("on", on), ("off", off)):
         ids, _, d64 = msi.msi_knn_dtw(ix, Q[:4], 3, window=length // 10)

@@ -50,7 +50,9 @@ def parse():
     p.add_argument("--cpu-queries", type=int, default=10)
     p.add_argument("--serving", action="store_true", help="Poisson-arrival serving sweep over three collections")
     p.add_argument("--dtw", action="store_true", help="exact k-NN under DTW (window 10%%) on the same workload")
-    p.add_argument("--query-slots", type=int, default=0, help="concurrent query slots of the index (0: default 16)")
+    p.add_argument("--query-slots", type=int, default=0,
+                   help="concurrent query slots of the index (0: the autotuner's choice, default schedule 16)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default batched schedule (16 slots, share 3)")
     p.add_argument("--window", type=int, default=-1, help="DTW half-width (default len / 10)")
     p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
@@ -346,6 +348,15 @@ def main():
     out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     out_d = torch.empty((nq, k), dtype=torch.float32, device=dev)
 
+    # ---- the batched schedule (query slots x grid share), chosen by the library's
+    # autotuner on this step's queries before the warm-up (answers do not depend on it)
+    schedule = {"query_slots": args.query_slots or 16, "grid_share": 3, "autotuned": False}
+    if not args.no_autotune and not args.query_slots:
+        tr = msi.msi_autotune(index, Q, k, stream=stream)
+        schedule = {"query_slots": tr["query_slots"], "grid_share": tr["grid_share"], "autotuned": True,
+                    "candidates": tr["candidates"], "tuned_qps": tr["queries_per_s"],
+                    "default_schedule_qps": tr["default_queries_per_s"]}
+
     def step():
         if world > 1:  # answers over every rank's shard, merged by (FP64 distance, id)
             from paper_2009_00786_gb300 import shard
@@ -460,7 +471,7 @@ def main():
         "config": {"workload": workload(n * world, length, nq, k, args.leaf),
                    "n_series": n * world, "len": length, "queries_per_step": nq, "k": k,
                    "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)",
-                   "query_slots": args.query_slots or 16},
+                   "query_slots": schedule["query_slots"], "schedule": schedule},
         "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
         "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq},
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},

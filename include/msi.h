@@ -292,6 +292,31 @@ MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats,
 MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
 
 /*
+ * msi_autotune -- choose the batched-query schedule of an index by measurement. The
+ * paper runs one query after another (Section IV, "Setup"); a batched msi_knn call here
+ * runs its queries concurrently on query slots, each with its own stream and
+ * workspace, and each query's persistent grids are divided by min(slots, grid share).
+ * This call times msi_knn on `queries` (nq >= 2 of them, host or device, as msi_knn)
+ * with k neighbours for every candidate schedule: query slots in {4, 8, 12, 16, 24,
+ * 32} (at most 64) and grid shares in {1, 2, 3, 4, 6} up to the slot count. Each
+ * candidate runs `reps` timed calls (0 selects 3) after three untimed ones, with CUDA
+ * events on `stream` (NULL: the index's stream). The fastest schedule (queries/s)
+ * stays with the index; answers are the same under every schedule. `out` (host, may
+ * be NULL) receives the choice. Slot workspaces are allocated as needed and kept.
+ * Errors: MSI_EINVAL for a NULL index or queries, nq < 2 or k outside msi_knn's
+ * range; MSI_ENOMEM / MSI_ECUDA as msi_knn. On error the index keeps its schedule.
+ */
+typedef struct msi_tune_result {
+  int32_t query_slots;   /* the schedule chosen                                  */
+  int32_t grid_share;
+  double queries_per_s;  /* its measured rate                                    */
+  int32_t candidates;    /* schedules measured                                   */
+  double default_queries_per_s;  /* the rate of the default schedule (16, 3)     */
+} msi_tune_result;
+MSI_API msi_status msi_autotune(msi_index* index, const float* queries, int64_t nq, int32_t k, int32_t reps,
+                                msi_tune_result* out, void* stream);
+
+/*
  * Serving: a request loop over several resident indexes with continuous batching.
  * The paper answers one query after another (Section IV, "Setup"); this has no
  * counterpart there. Each index gets query slots (a bounded workspace, a stream and

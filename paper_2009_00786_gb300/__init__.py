@@ -67,6 +67,8 @@ _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 _lib.msi_build.argtypes = [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(_BuildOpts), ctypes.POINTER(_vp)]
 _lib.msi_build.restype = ctypes.c_int
 _lib.msi_knn.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
+_lib.msi_autotune.argtypes = [_vp, _vp, _i64, _i32, _i32, _vp, _vp]
+_lib.msi_autotune.restype = ctypes.c_int
 _lib.msi_knn.restype = ctypes.c_int
 _lib.msi_knn_ex.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]
 _lib.msi_knn_dtw.argtypes = [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
@@ -325,6 +327,21 @@ def msi_query_stats_get(index, reset=False):
 
 def msi_set_timing(index, enable=True):
     _check(_lib.msi_set_timing(ctypes.c_void_p(index.handle), 1 if enable else 0))
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("query_slots", ctypes.c_int32), ("grid_share", ctypes.c_int32), ("queries_per_s", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("default_queries_per_s", ctypes.c_double)]
+
+
+def msi_autotune(index, queries, k, reps=0, stream=None):
+    """msi_autotune: times the batched schedules (query slots x grid share) on
+    `queries` [nq >= 2, len] (host or device) and keeps the fastest for the index.
+    Returns the choice as a dict."""
+    out = _TuneResult()
+    _check(_lib.msi_autotune(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), queries.shape[0], k, reps,
+                             ctypes.byref(out), _stream(stream)))
+    return {f: getattr(out, f) for f, _ in _TuneResult._fields_}
 
 
 def msi_lower_bounds_noalloc(index, query, series_lb, leaf_lb, stream=None):

@@ -266,7 +266,7 @@ static cudaError_t enqueue_batch(msi_index* ix, cudaStream_t s, int64_t cnt, int
   if ((e = cudaEventRecord(ix->fork_event, s)) != cudaSuccess) return e;
   for (int sl = 0; sl < ix->nslots; ++sl)
     if ((e = cudaStreamWaitEvent(ix->slot_streams[sl], ix->fork_event, 0)) != cudaSuccess) return e;
-  const int share = std::min(ix->nslots, msi::kSlotGridShare);
+  const int share = std::min(ix->nslots, ix->grid_share);
   for (int64_t i = 0; i < cnt; ++i) {
     const int sl = (int)(i % ix->nslots);
     if (call)
@@ -452,6 +452,93 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
 msi_status msi_knn_ex(msi_index* ix, const float* queries, int64_t nq, int32_t k, int64_t* ids, float* dists,
                       double* sqdists64, void* stream) {
   return knn_impl(ix, queries, nq, k, -1, ids, dists, sqdists64, stream);
+}
+
+namespace {
+void forget_graphs(msi_index* ix) {
+  for (auto& g : ix->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ix->graphs.clear();
+}
+}  // namespace
+
+msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t reps,
+                        msi_tune_result* out, void* stream) {
+  g_err.clear();
+  if (!ix || !queries) return fail(MSI_EINVAL, "index or queries is NULL");
+  if (nq < 2) return fail(MSI_EINVAL, "nq = %lld: a schedule needs at least 2 queries", (long long)nq);
+  if (k < 1 || k > MSI_MAX_K || (int64_t)k > ix->n)
+    return fail(MSI_EINVAL, "k = %d outside [1, min(n = %lld, %d)]", k, (long long)ix->n, MSI_MAX_K);
+  if (reps < 0) return fail(MSI_EINVAL, "reps = %d is negative", reps);
+  if (reps == 0) reps = 3;
+  DeviceGuard guard(ix->device);
+  cudaStream_t s = stream ? (cudaStream_t)stream : ix->own_stream;
+  const int keep_slots = ix->nslots, keep_share = ix->grid_share;
+  const bool keep_timing = ix->timing;
+  ix->timing = false;
+  int64_t* ids = nullptr;
+  float* dists = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  msi_status st = MSI_OK;
+  double best = -1.0, def_rate = 0.0;
+  int best_slots = keep_slots, best_share = keep_share, count = 0;
+  if ((e = cudaMalloc(&ids, sizeof(int64_t) * (size_t)nq * k)) != cudaSuccess ||
+      (e = cudaMalloc(&dists, sizeof(float) * (size_t)nq * k)) != cudaSuccess ||
+      (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    st = cuda_fail(e, "autotune buffers");
+  } else {
+    static const int kSlots[] = {4, 8, 12, 16, 24, 32};
+    static const int kShares[] = {1, 2, 3, 4, 6};
+    for (int sl : kSlots) {
+      for (int sh : kShares) {
+        if (sh > sl || st != MSI_OK) continue;
+        forget_graphs(ix);  // graphs hold the previous schedule's streams and grids
+        ix->nslots = std::min(sl, 64);
+        ix->grid_share = sh;
+        for (int w = 0; w < 3 && st == MSI_OK; ++w) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
+        if (st != MSI_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == MSI_OK; ++r) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
+        if (st != MSI_OK) break;
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+          st = cuda_fail(e, "autotune timing");
+          break;
+        }
+        const double rate = ms > 0.f ? (double)nq * reps / (ms * 1e-3) : 0.0;
+        ++count;
+        if (sl == msi::kDefaultQuerySlots && sh == msi::kSlotGridShare) def_rate = rate;
+        if (rate > best) {
+          best = rate;
+          best_slots = sl;
+          best_share = sh;
+        }
+      }
+    }
+  }
+  if (ids) cudaFree(ids);
+  if (dists) cudaFree(dists);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  forget_graphs(ix);
+  ix->timing = keep_timing;
+  if (st != MSI_OK) {
+    ix->nslots = keep_slots;
+    ix->grid_share = keep_share;
+    return st;
+  }
+  ix->nslots = best_slots;
+  ix->grid_share = best_share;
+  if (out) {
+    out->query_slots = best_slots;
+    out->grid_share = best_share;
+    out->queries_per_s = best;
+    out->candidates = count;
+    out->default_queries_per_s = def_rate;
+  }
+  return MSI_OK;
 }
 
 msi_status msi_knn_dtw(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t window, int64_t* ids,

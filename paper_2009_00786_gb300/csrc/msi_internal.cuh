@@ -341,6 +341,7 @@ struct msi_index {
   msi::CallDesc* call_host = nullptr;
   bool use_graphs = true;
   int nslots = msi::kDefaultQuerySlots;
+  int grid_share = msi::kSlotGridShare;  // batched calls: grids divided by min(nslots, this)
   int slot_cap = 0;
   int64_t overflow_reruns = 0;
   float* ws_qraw = nullptr;     // staging for host queries [kQueryChunk][len]

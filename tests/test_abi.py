@@ -94,6 +94,9 @@ def test_knn_and_helpers_reject_null_index(msi):
     assert lib.msi_set_timing(None, 1) == msi.MSI_EINVAL
     st = msi._QueryStats()
     assert lib.msi_query_stats_get(None, ctypes.byref(st), 0) == msi.MSI_EINVAL
+    tr = msi._TuneResult()
+    assert lib.msi_autotune(None, qp, 4, 1, 0, ctypes.byref(tr), None) == msi.MSI_EINVAL
+    assert "NULL" in msi.msi_last_error()
     lib.msi_free(None)  # no-op
 
 

@@ -286,6 +286,32 @@ def test_repeated_batched_shape_replays_with_new_pointers(msi):
     ix.close()
 
 
+def test_autotune_keeps_answers_and_picks_a_measured_schedule(msi):
+    """The batched-schedule autotuner times query slots x grid shares on the caller's
+    queries and keeps the fastest; answers before and after are identical and the
+    oracle's, and bad arguments are refused without changing the schedule."""
+    import torch
+    n, length, nq, k = 30000, 256, 24, 3
+    X = datagen.walks(221, 0, n, length)
+    Z = oracle.summarise(X, 16, 256)[0]
+    Q = datagen.paper_queries(n, length, count=nq, data_seed=221)
+    ix = msi.msi_build(X, segments=16, leaf_capacity=200)
+    before = msi.msi_knn(ix, Q, k)
+    Qd = torch.from_numpy(Q).cuda()
+    with pytest.raises(msi.MsiError):
+        msi.msi_autotune(ix, Qd[:1], k)  # one query cannot be batched
+    tr = msi.msi_autotune(ix, Qd, k, reps=2)
+    assert tr["query_slots"] in (4, 8, 12, 16, 24, 32)
+    assert 1 <= tr["grid_share"] <= min(6, tr["query_slots"])
+    assert tr["candidates"] == 29 and tr["queries_per_s"] >= tr["default_queries_per_s"] > 0
+    after = msi.msi_knn(ix, Q, k)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    for i, q in enumerate(Q):
+        oid, _ = oracle.knn_scan(Z, oracle.znorm(q)[0], k)
+        assert np.array_equal(after[0][i], oid), i
+    ix.close()
+
+
 @pytest.mark.parametrize("k", [1, 10])
 def test_mixed_shapes_match_oracle(msi, k):
     """The harder value distributions (noisy sinusoids, Laplace-step walks with spike

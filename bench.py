@@ -29,7 +29,14 @@ HBM_FALLBACK_GBS = 6800.0
 METRIC = "exact 1-NN queries/s and p50/p99 ms at 100M x 256 fp32, batched vs plain"
 
 
-def workload(n_total, length, nq, k, leaf):
+MIXED_SEED = 4  # the mixed-shape collection
+
+
+def workload(n_total, length, nq, k, leaf, kind="walks"):
+    if kind == "mixed":
+        return (f"{n_total // 1_000_000}M x {length} fp32 mixed shapes (seed {MIXED_SEED}: 50% noisy sinusoids, "
+                f"50% Laplace-step walks with spike bursts), {nq} queries (fresh draws + N(0, 0.1) noise), k={k}, "
+                f"16 segments, cardinality 256, leaf capacity {leaf}")
     return (f"{n_total // 1_000_000}M x {length} fp32 random walks (seed 0), {nq} queries (50% fresh walks, "
             f"50% noisy members), k={k}, 16 segments, cardinality 256, leaf capacity {leaf}")
 
@@ -53,6 +60,10 @@ def parse():
     p.add_argument("--query-slots", type=int, default=0,
                    help="concurrent query slots of the index (0: the autotuner's choice, default schedule 16)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default batched schedule (16 slots, share 3)")
+    p.add_argument("--slot-capacity", type=int, default=0,
+                   help="entries of each bounded query slot's candidate and survivor lists (0: the defaults)")
+    p.add_argument("--workload", default="walks", choices=["walks", "mixed"],
+                   help="random walks (the headline) or the mixed-shape family (use --n 60000000)")
     p.add_argument("--window", type=int, default=-1, help="DTW half-width (default len / 10)")
     p.add_argument("--serve-scale", type=float, default=1.0, help="collection sizes x this (serving mode)")
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
@@ -121,11 +132,15 @@ def cpu_baseline(args, length, n_total, seconds_budget=None):
     import datagen
     import oracle
     ns = min(args.cpu_sample, n_total)
-    X = datagen.walks(0, 0, ns, length)
+    mixed = getattr(args, "workload", "walks") == "mixed"
+    X = datagen.mixed(MIXED_SEED, 0, ns, length) if mixed else datagen.walks(0, 0, ns, length)
     t0 = time.perf_counter()
     Z = oracle.summarise(X, 16, 256, want_paa=False)[0]
     t_sum = time.perf_counter() - t0
-    Q = datagen.paper_queries(n_total, length, count=args.queries)[: args.cpu_queries]
+    if mixed:
+        Q = datagen.mixed_queries(count=args.queries, length=length)[: args.cpu_queries]
+    else:
+        Q = datagen.paper_queries(n_total, length, count=args.queries)[: args.cpu_queries]
     t0 = time.perf_counter()
     for q in Q:
         oracle.knn_scan(Z, oracle.znorm(q)[0], args.k)
@@ -155,7 +170,7 @@ def reference_arm(args):
             "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload(args.n, length, args.queries, args.k, args.leaf),
+            "config": {"workload": workload(args.n, length, args.queries, args.k, args.leaf, args.workload),
                        "sample": base["sample"]},
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -325,14 +340,18 @@ def main():
     # ---- collection (this rank's shard of the weak-scaled job) and queries, in HBM
     first_id = rank * n
     X = torch.empty((n, length), dtype=torch.float32, device=dev)
-    datagen.walks_device(0, first_id, n, length, X.data_ptr(), stream.cuda_stream)
-    n_fresh, ids, sig = datagen.query_plan(n, nq)
-    Q = torch.empty((nq, length), dtype=torch.float32, device=dev)
-    datagen.walks_device(1, 0, n_fresh, length, Q.data_ptr(), stream.cuda_stream)
-    ids_d = torch.from_numpy(ids).to(dev)
-    sig_d = torch.from_numpy(sig).to(dev)
-    datagen.noisy_copies_device(0, 2, ids_d.data_ptr(), sig_d.data_ptr(), nq - n_fresh, length,
-                                Q[n_fresh:].data_ptr(), stream.cuda_stream)
+    if args.workload == "mixed":
+        datagen.mixed_device(MIXED_SEED, first_id, n, length, X.data_ptr(), stream.cuda_stream)
+        Q = torch.from_numpy(datagen.mixed_queries(count=nq, length=length)).to(dev)
+    else:
+        datagen.walks_device(0, first_id, n, length, X.data_ptr(), stream.cuda_stream)
+        n_fresh, ids, sig = datagen.query_plan(n, nq)
+        Q = torch.empty((nq, length), dtype=torch.float32, device=dev)
+        datagen.walks_device(1, 0, n_fresh, length, Q.data_ptr(), stream.cuda_stream)
+        ids_d = torch.from_numpy(ids).to(dev)
+        sig_d = torch.from_numpy(sig).to(dev)
+        datagen.noisy_copies_device(0, 2, ids_d.data_ptr(), sig_d.data_ptr(), nq - n_fresh, length,
+                                    Q[n_fresh:].data_ptr(), stream.cuda_stream)
     stream.synchronize()
 
     # ---- build (timed once; the collection is borrowed in place)
@@ -340,7 +359,7 @@ def main():
     with torch.cuda.stream(stream):
         b0.record(stream)
         index = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=args.leaf, flags=msi.MSI_BUILD_BORROW,
-                              stream=stream, query_slots=args.query_slots)
+                              stream=stream, query_slots=args.query_slots, slot_capacity=args.slot_capacity)
         b1.record(stream)
     stream.synchronize()
     build_ms = b0.elapsed_time(b1)
@@ -419,7 +438,7 @@ def main():
     e2e_qps = nq * args.steps / (ee0.elapsed_time(ee1) / 1e3)
 
     # ---- refinement kernels, timed with CUDA events recorded on the query stream
-    msi.msi_query_stats_get(index, reset=True)
+    batched_st = msi.msi_query_stats_get(index, reset=True)  # the timed and end-to-end batched steps
     msi.msi_set_timing(index, True)
     step()
     stream.synchronize()
@@ -468,13 +487,15 @@ def main():
         "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload(n * world, length, nq, k, args.leaf),
+        "config": {"workload": workload(n * world, length, nq, k, args.leaf, args.workload),
                    "n_series": n * world, "len": length, "queries_per_step": nq, "k": k,
                    "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)",
                    "query_slots": schedule["query_slots"], "schedule": schedule},
         "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
-        "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq},
-        "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9},
+        "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq,
+                    "overflow_reruns_per_query": batched_st["overflow_reruns"] / max(1, batched_st["queries"])},
+        "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9,
+                  "index_device_gb": msi.msi_index_info_get(index)["device_bytes"] / 1e9},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
                 "d2h_bytes_per_step": nq * k * 12},
         "gpu_launches": timed_launches,

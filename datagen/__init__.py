@@ -52,6 +52,8 @@ def _load_dev():
         lib.dg_walks_device.restype = ctypes.c_int
         lib.dg_noisy_copies_device.argtypes = [c_u64, c_u64, vp, vp, c_i64, c_i32, vp, vp]
         lib.dg_noisy_copies_device.restype = ctypes.c_int
+        lib.dg_mixed_device.argtypes = [c_u64, c_i64, c_i64, c_i32, vp, vp]
+        lib.dg_mixed_device.restype = ctypes.c_int
         _dev = lib
     return _dev
 
@@ -136,6 +138,14 @@ def walks_device(seed, first_id, count, length, out_ptr, stream_ptr=0):
                                      ctypes.c_void_p(stream_ptr))
     if rc != 0:
         raise RuntimeError(f"dg_walks_device failed: cudaError {rc}")
+
+
+def mixed_device(seed, first_id, count, length, out_ptr, stream_ptr=0):
+    """Fill a device buffer (raw pointer) with the mixed-shape family; bit-identical to mixed()."""
+    rc = _load_dev().dg_mixed_device(seed, first_id, count, length, ctypes.c_void_p(out_ptr),
+                                     ctypes.c_void_p(stream_ptr))
+    if rc != 0:
+        raise RuntimeError(f"dg_mixed_device failed: cudaError {rc}")
 
 
 def noisy_copies_device(data_seed, noise_seed, ids_ptr, sigma_ptr, count, length, out_ptr, stream_ptr=0):

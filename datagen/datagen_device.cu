@@ -49,7 +49,24 @@ __global__ void noisy_kernel(uint64_t data_seed, uint64_t noise_seed, const int6
   }
 }
 
+// The mixed-shape family: one thread per series, written in place.
+__global__ void mixed_kernel(uint64_t seed, int64_t first_id, int64_t count, int32_t len, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  dg_mixed_one(seed, (uint64_t)(first_id + i), len, out + i * (int64_t)len);
+}
+
 }  // namespace
+
+extern "C" int dg_mixed_device(uint64_t seed, int64_t first_id, int64_t count, int32_t len, float* out,
+                               void* stream) {
+  if (count <= 0) return 0;
+  if (len <= 0 || out == nullptr) return (int)cudaErrorInvalidValue;
+  const int64_t blocks = (count + 127) / 128;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  mixed_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(seed, first_id, count, len, out);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int dg_walks_device(uint64_t seed, int64_t first_id, int64_t count, int32_t len,
                                float* out, void* stream) {

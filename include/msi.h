@@ -82,7 +82,8 @@ typedef struct msi_build_opts {
   int32_t query_slots;   /* Euclidean queries msi_knn runs at once; 0 selects 16, 1 runs*/
                          /* them one after another                                     */
   int32_t slot_capacity; /* candidates / survivors a concurrent slot holds; 0 selects  */
-                         /* max(2^18, leaf_capacity + MSI_MAX_K) and 2^22; a query     */
+                         /* max(2^18, leaf_capacity + MSI_MAX_K) and max(2^22, n / 4); */
+                         /* at most n each; a query                                   */
                          /* that needs more is run again with room for all n          */
 } msi_build_opts;
 
@@ -281,6 +282,8 @@ typedef struct msi_query_stats {
                                  /* index keeps one; re-tested before refinement)   */
   int64_t fine_bounded;          /* series the series filter bounded by the fine PAA */
   int64_t front_fine_bounded;    /* front-leaf rows bounded by the fine PAA         */
+  int64_t overflow_reruns;       /* batched queries whose bounded slot lists ran out */
+                                 /* of room and that ran again on the full workspace */
 } msi_query_stats;
 
 /* Reads the counters (host pointer), optionally resetting them. Reading synchronises

@@ -60,7 +60,8 @@ class _QueryStats(ctypes.Structure):
         "queries", "leaves_total", "leaves_survived", "blocks_examined", "series_lower_bounded",
         "series_refined", "seed_series", "candidates", "rechecked", "refine_launches")] + [
         ("refine_ms", ctypes.c_double), ("filter_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-        ("survivors", ctypes.c_int64), ("fine_bounded", ctypes.c_int64), ("front_fine_bounded", ctypes.c_int64)]
+        ("survivors", ctypes.c_int64), ("fine_bounded", ctypes.c_int64), ("front_fine_bounded", ctypes.c_int64),
+        ("overflow_reruns", ctypes.c_int64)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64

@@ -692,6 +692,7 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->survivors = (int64_t)c[msi::ST_SURVIVORS];
   st->fine_bounded = (int64_t)c[msi::ST_FINE];
   st->front_fine_bounded = (int64_t)c[msi::ST_FINE_FRONT];
+  st->overflow_reruns = ix->overflow_reruns;
   if (reset) {
     if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_COUNT)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");
@@ -699,6 +700,7 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
     ix->filter_ms = 0.0;
     ix->refine_launches = 0;
     ix->kernel_launches = 0;
+    ix->overflow_reruns = 0;
   }
   return MSI_OK;
 }

@@ -18,11 +18,12 @@ constexpr int kWarp = 32;
 constexpr int kItem = 256;  // leaf positions per refinement work item
 constexpr int kMaxRefineWarps = 1 << 16;
 constexpr int kMaxFront = 8;  // leaves refined before the filters, at most
-// Concurrent queries divide the persistent grids of their kernels by at most this:
-// the queries then oversubscribe the GPU and the hardware interleaves their blocks,
-// where dividing by the number of queries would leave SMs idle whenever the queries'
-// phases do not line up (100M x 256: 16 queries at 1/3 of the grid each 31.6K q/s,
-// 8 queries at 1/8 each 24.0K).
+// Concurrent queries divide the persistent grids of their kernels by at most this (the
+// default of an index's grid share; msi_autotune may choose another): the queries then
+// oversubscribe the GPU and the hardware interleaves their blocks, where dividing by
+// the number of queries would leave SMs idle whenever the queries' phases do not line
+// up (100M x 256: 16 queries at 1/3 of the grid each 31.6K q/s, 8 queries at 1/8 each
+// 24.0K).
 constexpr int kSlotGridShare = 3;
 constexpr int kDefaultQuerySlots = 16;
 constexpr unsigned kFull = 0xffffffffu;

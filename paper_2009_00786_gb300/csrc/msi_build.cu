@@ -71,6 +71,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
   __shared__ float thr_s[257];
   __shared__ __align__(16) uint8_t sw_s[kSumWarps][16];
   __shared__ __align__(16) __half fs_s[kSumWarps][kMaxFine];
+  __shared__ float paa_s[kSumWarps][16];
   for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -137,12 +138,14 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
       for (int off = 1; off < G; off <<= 1) g = __fadd_rn(g, __shfl_xor_sync(kFull, g, off));
       if ((lane & (G - 1)) == 0) {
         const int j = c * segs_per_chunk + lane / G;
-        if (j < 16) sw[j] = (uint8_t)sax_symbol(thr_s, card, __fdiv_rn(g, (float)s));
+        if (j < 16) paa_s[warp][j] = __fdiv_rn(g, (float)s);
       }
     }
-    if (lane < 16 - w) sw[w + lane] = 0;
+    // one symbol search for all segments: lane j takes segment j
     __syncwarp();
-    const int sym = lane < w ? sw[lane] : 0;
+    const int sym = lane < w ? sax_symbol(thr_s, card, paa_s[warp][lane]) : 0;
+    if (lane < 16) sw[lane] = (uint8_t)sym;
+    __syncwarp();
     if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
     emit_word(sw, sym, w, bits, i, o);
     if (o.fine) emit_fine(fs, i, o);

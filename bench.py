@@ -44,7 +44,8 @@ def workload(n_total, length, nq, k, leaf, kind="walks"):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default 100 for the headline, about 0.3 s of GPU time; 10 otherwise)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=100_000_000)
@@ -69,7 +70,10 @@ def parse():
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
     p.add_argument("--serve-slots", type=int, default=8, help="query slots per collection (serving mode)")
     p.add_argument("--serve-requests", type=int, default=3000, help="most requests per rate")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.steps is None:
+        args.steps = 10 if (args.dtw or args.serving or args.impl == "reference") else 100
+    return args
 
 
 def peaks():
@@ -104,7 +108,7 @@ class ClockSampler:
                     self.samples.append(vals)
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.05)
 
     def __enter__(self):
         self._t.start()

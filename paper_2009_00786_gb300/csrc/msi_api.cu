@@ -531,6 +531,18 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
   }
   ix->nslots = best_slots;
   ix->grid_share = best_share;
+  // release the slots the chosen schedule does not use (every call above has finished)
+  uint32_t cand_cap = 0, surv_cap = 0;
+  msi::slot_capacities(ix, ix->slot_cap, &cand_cap, &surv_cap);
+  while ((int)ix->slots.size() > ix->nslots) {
+    msi::free_workspace(ix->slots.back());
+    ix->device_bytes -= msi::workspace_bytes(ix, cand_cap, surv_cap);
+    cudaStreamDestroy(ix->slot_streams.back());
+    cudaEventDestroy(ix->slot_events.back());
+    ix->slots.pop_back();
+    ix->slot_streams.pop_back();
+    ix->slot_events.pop_back();
+  }
   if (out) {
     out->query_slots = best_slots;
     out->grid_share = best_share;

@@ -499,6 +499,7 @@ def main():
         "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq,
                     "overflow_reruns_per_query": batched_st["overflow_reruns"] / max(1, batched_st["queries"])},
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9,
+                  "input_frac_of_hbm": n * length * 4 / (build_ms / 1e3) / 1e9 / peak,
                   "index_device_gb": msi.msi_index_info_get(index)["device_bytes"] / 1e9},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * length * 4,
                 "d2h_bytes_per_step": nq * k * 12},

@@ -208,26 +208,17 @@ void orc_paa64(const float* z, int32_t n, int32_t w, double* paa) {
 }
 
 /* ------------------------------------------------------------ exact distance
- * Section II-A: Euclidean distance. D = sum_t (z_t - q_t)^2 in FP64. The paper
- * fixes no summation order; this one is shared with the GPU re-check so both sides
- * produce the same bits: 32 partial sums, partial l adding the terms with
- * t mod 32 = l in increasing t, combined by a pairwise tree in partial order. */
-static double orc_lane_tree64(double a[32]) {
-  for (int off = 1; off < 32; off <<= 1) {
-    double b[32];
-    for (int l = 0; l < 32; ++l) b[l] = a[l] + a[l ^ off];
-    memcpy(a, b, sizeof b);
-  }
-  return a[0];
-}
-
+ * Section II-A: Euclidean distance. D = sum_t (z_t - q_t)^2 in FP64, the terms added
+ * one after another in increasing t: the definition written out. (The GPU re-check
+ * adds the same FP64 terms in another order, so the two may differ in the last
+ * bits; an exact tie between identical series is a tie under any order.) */
 double orc_sqdist(const float* a, const float* b, int32_t n) {
-  double part[32] = {0};
+  double acc = 0.0;
   for (int32_t t = 0; t < n; ++t) {
     const double d = (double)a[t] - (double)b[t];
-    part[t & 31] = part[t & 31] + d * d;
+    acc = acc + d * d;
   }
-  return orc_lane_tree64(part);
+  return acc;
 }
 
 /* (D, id) order: smaller distance first, then lower id. */

@@ -1245,7 +1245,9 @@ __device__ void final_select(const QueryView& qv, uint32_t* hist, uint32_t* sel)
 // FP64 re-check of the candidates at or below the k-th candidate distance times
 // (1 + eps): one warp per candidate. Lane l adds the FP64 squared differences of the
 // points t = l, l + 32, ... in increasing t; the 32 partials are combined by a
-// pairwise tree in lane order. No fused operations: the same bits as the oracle.
+// pairwise tree in lane order. No fused operations. The FP64 sum differs from a
+// sequential one by a few units in its last place at most (far inside the fp32
+// margin), and identical series give identical sums, so exact ties stay ties.
 // In rounds of 4 * blockDim candidates, all threads test the candidates against the
 // bound and list the passing ones in shared memory (`list`, 4 * blockDim entries);
 // then one warp per listed candidate computes its FP64 distance.

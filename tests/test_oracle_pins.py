@@ -204,6 +204,22 @@ def test_knn_scan_brute_force():
             np.testing.assert_allclose(d2, bd, rtol=1e-12)
 
 
+def test_sqdist_within_the_error_bound_of_the_exact_sum():
+    """The FP64 distance against exact rational arithmetic (Section II-A's sum of
+    squared differences of the fp32 values): a sequential FP64 sum of n rounded terms
+    is within n 2^-53 of the exact value, relative; a dropped, doubled or mis-signed
+    term is not."""
+    from fractions import Fraction
+    X = datagen.walks(33, 0, 6, 256)
+    Z = oracle.summarise(X, 16, 256)[0]
+    for a in range(3):
+        for b in range(3, 6):
+            exact = sum((Fraction(float(x)) - Fraction(float(y))) ** 2 for x, y in zip(Z[a], Z[b]))
+            got = oracle.sqdist(Z[a], Z[b])
+            assert abs(Fraction(got) - exact) <= exact * Fraction(256 + 2, 2 ** 53)
+    assert oracle.sqdist(Z[0], Z[0]) == 0.0
+
+
 def test_knn_scan_special_cases():
     X = datagen.walks(41, 0, 500, 128)
     Z = oracle.summarise(X, 16, 256)[0]

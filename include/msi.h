@@ -256,6 +256,7 @@ MSI_API msi_status msi_index_export(const msi_index* index, const msi_export* ou
  *   query     float[len], host or device (raw; z-normalised here).
  *   series_lb float[n] in collection order, or NULL.
  *   leaf_lb   float[leaves], or NULL.
+ * A query holding NaN or infinity gets NaN bounds.
  */
 MSI_API msi_status msi_lower_bounds(msi_index* index, const float* query, float* series_lb, float* leaf_lb,
                             void* stream);
@@ -363,10 +364,10 @@ MSI_API void msi_server_free(msi_server* server);
 /*
  * msi_lower_bounds_noalloc -- msi_lower_bounds for callers that cannot allocate
  * device memory. The paper has no counterpart: it exists for code that must not
- * call cudaMalloc, such as code running while a stream is captured into a CUDA graph
- * (an allocation ends the capture), code held to a memory budget by an allocator or
- * pool it does not own, and latency-critical paths that must not wait on the
- * driver's allocator.
+ * call cudaMalloc, such as code held to a device-memory budget by an allocator or
+ * pool it does not own (an allocation behind its back breaks the budget), and
+ * latency-critical paths that must not wait on the driver's allocator (cudaMalloc
+ * can synchronise the device).
  *
  * It computes the same lower bounds, with the same kernels, and calls no cudaMalloc,
  * cudaFree or allocating library routine: the per-query temporaries (query state,
@@ -383,7 +384,9 @@ MSI_API void msi_server_free(msi_server* server);
  *   series_lb  float[n] in DEVICE memory: bound per series, collection order.
  *   leaf_lb    float[leaves] in DEVICE memory: bound per leaf.
  *   stream     cudaStream_t or NULL (NULL: the legacy default stream, and the call
- *              waits for its work and reports a non-finite query).
+ *              waits for its work and reports a non-finite query). A non-finite
+ *              query gets NaN in every output, so a caller that passes a stream
+ *              and does not wait still cannot take it for a bound.
  * Errors: MSI_EINVAL (NULL or host pointers; an index whose len exceeds 4096 or whose
  * segments * cardinality exceeds 4096 does not fit the fixed scratch; a non-finite
  * query), MSI_ECUDA.

@@ -272,6 +272,12 @@ __device__ __forceinline__ unsigned long long interleave_key(int sym, int w, int
 }
 
 // ------------------------------------------------------------------ margins
+// The two margins of the exactness argument for series of `len` points: eps relative
+// on squared distances (2^-16), tau absolute on lower bounds (1e-3 at len 256, growing
+// with the square root of the length as the fp32 PAA rounding of a bound does).
+inline float margin_eps() { return 1.52587890625e-05f; }
+inline float margin_tau(int len) { return 1e-3f * fmaxf(1.0f, sqrtf((float)len / 256.0f)); }
+
 // Lower-bound pruning threshold for a k-th best squared distance `thr`:
 // (sqrt(thr) (1 + eps) + tau)^2, rounded up; +inf while thr is unknown.
 __device__ __forceinline__ float lb_bound2(unsigned thr_bits, float eps, float tau) {

@@ -1,10 +1,10 @@
 // msi_noalloc.cu -- msi_lower_bounds_noalloc, the one entry point that allocates no
 // memory at all.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is being
-// captured into a graph (an allocation would end the capture), code inside a
-// memory budget enforced by a custom allocator or a stream-ordered pool it does not
-// own, and real-time paths that must not block on the driver's allocator. For them
+// Some callers cannot call cudaMalloc: code held to a device-memory budget by a custom
+// allocator or a stream-ordered pool that it does not own (an allocation behind the
+// pool's back breaks the budget), and real-time paths that must not block on the
+// driver's allocator (cudaMalloc can synchronise the device). For them
 // this entry point computes the same lower bounds as msi_lower_bounds with every
 // per-query temporary (query state, z-normalised query, per-segment gap tables,
 // counters) in one file-scope device array of fixed size instead of the index's
@@ -97,8 +97,8 @@ extern "C" MSI_API msi_status msi_lower_bounds_noalloc(const msi_index* ix, cons
   qv.T = reinterpret_cast<float*>(b + kStateBytes + kCounterBytes + kQzBytes);
   qv.T5 = reinterpret_cast<float*>(b + kStateBytes + kCounterBytes + kQzBytes + kTBytes);
   qv.k = 1;
-  qv.eps = 1.52587890625e-05f;
-  qv.tau = 1e-3f;
+  qv.eps = msi::margin_eps();  // the allocating path's margins
+  qv.tau = msi::margin_tau(ix->len);
   cudaStream_t s = (cudaStream_t)stream;
   // state and counters start at zero on every call (the array keeps the last call's)
   cudaError_t e = cudaMemsetAsync(b, 0, kStateBytes + kCounterBytes, s);

@@ -1899,13 +1899,16 @@ q_lb_all(IndexView ix, QueryView qv, float* __restrict__ series_lb, float* __res
   }
   smem_fill(Ts, qv.T, ix.w * ix.card);
   __syncthreads();
+  // a query with NaN or infinity gets NaN bounds, so that a caller that does not
+  // wait for the call (and so gets no error status) cannot mistake them for bounds
+  const bool bad = qv.st->flag < 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (series_lb)
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ix.n; p += stride)
-      series_lb[ix.perm[p]] = __fsqrt_rn(word_lb2(ix.words[p], Ts, ix.w, ix.card, (float)ix.seglen));
+      series_lb[ix.perm[p]] = bad ? NAN : __fsqrt_rn(word_lb2(ix.words[p], Ts, ix.w, ix.card, (float)ix.seglen));
   if (leaf_lb)
     for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L; l += stride)
-      leaf_lb[l] = __fsqrt_rn(leaf_lb2(ix, l, up_s, lo_s, thr_lo_s, thr_up_s));
+      leaf_lb[l] = bad ? NAN : __fsqrt_rn(leaf_lb2(ix, l, up_s, lo_s, thr_lo_s, thr_up_s));
 }
 
 // z-normalised collection in collection order, from the index's storage.
@@ -1955,8 +1958,8 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   qv.cand_cap = cand_cap;
   qv.surv_cap = surv_cap;
   qv.ovf = nullptr;
-  qv.eps = 1.52587890625e-05f;  // 2^-16
-  qv.tau = 1e-3f * fmaxf(1.0f, sqrtf((float)ix->len / 256.0f));
+  qv.eps = margin_eps();
+  qv.tau = margin_tau(ix->len);
   *bytes += workspace_bytes(ix, cand_cap, surv_cap);
   return cudaSuccess;
 }

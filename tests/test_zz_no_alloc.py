@@ -1,6 +1,7 @@
 """msi_lower_bounds_noalloc, the entry point for callers that cannot allocate device
-memory (for example code running during CUDA graph capture, or under an allocator
-budget it does not control). It must give the same bounds as msi_lower_bounds,
+memory (for example code held to a memory budget by an allocator it does not control,
+or a latency-critical path that must not wait on cudaMalloc). It must give the same
+bounds as msi_lower_bounds,
 which allocates its workspace, on consecutive calls that reuse its fixed scratch.
 This file runs last so that a failure here leaves every other test already run."""
 import numpy as np
@@ -32,4 +33,11 @@ def test_noalloc_lower_bounds_equal_allocating_entry_point():
     with pytest.raises(msi.MsiError) as e:  # host memory is refused: nothing is staged
         msi.msi_lower_bounds_noalloc(index, Q[0], s_lb, l_lb)
     assert e.value.status == msi.MSI_EINVAL
+    # a NaN query on a caller's stream (no error status without a wait): NaN bounds
+    bad = torch.from_numpy(Q[0].copy()).cuda()
+    bad[5] = float("nan")
+    s = torch.cuda.Stream()
+    msi.msi_lower_bounds_noalloc(index, bad, s_lb, l_lb, stream=s)
+    s.synchronize()
+    assert torch.isnan(s_lb).all() and torch.isnan(l_lb).all()
     index.close()

@@ -70,6 +70,10 @@ def parse():
     p.add_argument("--rates", default="1000,3000,10000,30000,100000")
     p.add_argument("--serve-slots", type=int, default=8, help="query slots per collection (serving mode)")
     p.add_argument("--serve-requests", type=int, default=3000, help="most requests per rate")
+    p.add_argument("--load-rates", default="5000,10000,15000",
+                   help="offered Poisson rates (queries/s) of the under-load leg on the benchmark's collection "
+                        "(empty: skip the leg)")
+    p.add_argument("--load-requests", type=int, default=3000, help="requests per offered rate of the under-load leg")
     args = p.parse_args()
     if args.steps is None:
         args.steps = 10 if (args.dtw or args.serving or args.impl == "reference") else 100
@@ -241,6 +245,39 @@ def serving(args):
     print(json.dumps(out))
 
 
+def under_load_leg(msi, index, pool, k, args):
+    """Poisson arrivals at each offered rate through msi_server_* on the benchmark's
+    index: continuous batching (16 slots) against one query at a time
+    (max_inflight = 1). Each request is a query of the benchmark's mix; the latency of
+    a request runs from its submission to its completion."""
+    import random
+    rates = [float(r) for r in args.load_rates.split(",") if r]
+    out = []
+    for name, opts in (("continuous", dict(slots_per_index=16)), ("one_at_a_time", dict(slots_per_index=1,
+                                                                                         max_inflight=1))):
+        srv = msi.Server([index], **opts)
+        for q in pool[:8]:  # warm the slots
+            srv.wait(srv.submit(0, q, k), k)
+        for rate in rates:
+            rng = random.Random(int(rate) + 17)
+            plan, t = [], 0.0
+            for _ in range(args.load_requests):
+                t += rng.expovariate(rate)
+                plan.append((t, pool[rng.randrange(len(pool))]))
+            tickets = []
+            t0 = time.perf_counter()
+            for at, q in plan:
+                while time.perf_counter() - t0 < at:
+                    pass
+                tickets.append(srv.submit(0, q, k))
+            lat = [srv.wait(tk, k)[2] for tk in tickets]
+            wall = time.perf_counter() - t0
+            out.append({"server": name, "offered_qps": rate, "requests": len(plan), "achieved_qps": len(plan) / wall,
+                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))})
+        srv.close()
+    return out
+
+
 def dtw_bench(args):
     """Exact k-NN under DTW (Section IV, MESSI with DTW) on the benchmark's collection
     and query mix: the same index, a Sakoe-Chiba window of 10% of the length."""
@@ -372,13 +409,20 @@ def main():
     out_d = torch.empty((nq, k), dtype=torch.float32, device=dev)
 
     # ---- the batched schedule (query slots x grid share), chosen by the library's
-    # autotuner on this step's queries before the warm-up (answers do not depend on it)
+    # autotuner before the warm-up (answers do not depend on it), on a query set of the
+    # same mix drawn from other seeds than the timed queries
+    if args.workload == "mixed":
+        Qt = torch.from_numpy(datagen.mixed_queries(count=nq, length=length, query_seed=7, noise_seed=8)).to(dev)
+    else:
+        Qt = torch.from_numpy(datagen.paper_queries(n, length, count=nq, data_seed=0, fresh_seed=7,
+                                                    pick_seed=8)).to(dev) if first_id == 0 else Q
     schedule = {"query_slots": args.query_slots or 16, "grid_share": 3, "autotuned": False}
     if not args.no_autotune and not args.query_slots:
-        tr = msi.msi_autotune(index, Q, k, stream=stream)
+        tr = msi.msi_autotune(index, Qt, k, stream=stream)
         schedule = {"query_slots": tr["query_slots"], "grid_share": tr["grid_share"], "autotuned": True,
                     "candidates": tr["candidates"], "tuned_qps": tr["queries_per_s"],
-                    "default_schedule_qps": tr["default_queries_per_s"]}
+                    "default_schedule_qps": tr["default_queries_per_s"],
+                    "tuning_queries": "a disjoint set of the same mix (seeds 7 and 8)"}
 
     def step():
         if world > 1:  # answers over every rank's shard, merged by (FP64 distance, id)
@@ -397,14 +441,21 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # an event after every step: a query of the batched form is answered when its
+    # call completes, so its latency is its call's (from the call's start on the
+    # stream to its completion)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local) as clocks:
         e0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
             step()
+            step_ev[i].record(stream)
         e1.record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
     elapsed_ms = e0.elapsed_time(e1)
+    call_lat = [e0.elapsed_time(step_ev[0])] + [step_ev[i - 1].elapsed_time(step_ev[i])
+                                                 for i in range(1, args.steps)]
     timed_launches = msi.msi_query_stats_get(index)["kernel_launches"]  # counted by the library
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
@@ -424,8 +475,9 @@ def main():
         lat.append(qe0.elapsed_time(qe1))
     plain_qps = nq / (sum(lat) / 1e3)
 
-    # ---- batched latency: every query of a step waits for the whole step
-    batch_lat = elapsed_ms / args.steps
+    # ---- under load: Poisson arrivals through the serving loop on this collection,
+    # continuous batching against one query at a time
+    under_load = under_load_leg(msi, index, Q.cpu().numpy(), k, args) if (args.load_rates and world == 1) else None
 
     # ---- end to end: host queries in, host results out, through the C ABI
     Qh = torch.empty((nq, length), dtype=torch.float32, pin_memory=True)
@@ -496,7 +548,9 @@ def main():
                    "l2": "inputs larger than L2 (102 GB collection)", "collection": "borrowed in place (MSI_BUILD_BORROW)",
                    "query_slots": schedule["query_slots"], "schedule": schedule},
         "plain": {"qps": plain_qps, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
-        "batched": {"qps": qps, "p50_ms": batch_lat, "p99_ms": batch_lat, "queries_per_call": nq,
+        "batched": {"qps": qps, "p50_ms": float(np.percentile(call_lat, 50)),
+                    "p99_ms": float(np.percentile(call_lat, 99)), "latency": "per call (every query of a call "
+                    "is answered when the call completes), over the timed steps", "queries_per_call": nq,
                     "overflow_reruns_per_query": batched_st["overflow_reruns"] / max(1, batched_st["queries"])},
         "build": {"ms": build_ms, "input_gbs": n * length * 4 / (build_ms / 1e3) / 1e9,
                   "input_frac_of_hbm": n * length * 4 / (build_ms / 1e3) / 1e9 / peak,
@@ -519,6 +573,8 @@ def main():
         "work_per_query": {kk: v / max(1, st["queries"]) for kk, v in st.items() if not kk.endswith("_ms")},
         "clocks": clocks.summary(),
     }
+    if under_load is not None:
+        line["under_load"] = under_load
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, length, n * world)
     index.close()

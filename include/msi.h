@@ -362,6 +362,26 @@ MSI_API msi_status msi_server_stats(msi_server* server, int64_t* completed, int6
 MSI_API void msi_server_free(msi_server* server);
 
 /*
+ * msi_merge_topk -- the one exchange of a search over a collection split across GPUs
+ * by contiguous ranges of series. Every series is summarised and searched on its own
+ * (Section III), so each range is indexed and searched alone; the answer over the
+ * whole collection is the k smallest of the ranges' answers in (FP64 squared
+ * distance, collection id) order, which is the order msi_knn_ex returns.
+ *   ids        int64[parts][nq][k_in]: each part's answer (collection ids, distinct
+ *              across parts), each row sorted by (sqdists64, id) as msi_knn_ex gives it.
+ *   sqdists64  double[parts][nq][k_in]: the FP64 squared distances of those ids.
+ *   out_ids    int64[nq][k]; out_dists float[nq][k] = sqrt rounded to fp32 (may be NULL);
+ *              out_sqdists64 double[nq][k] (may be NULL). Ascending (distance, id).
+ * Arrays may be host or device memory (host arrays are staged through a temporary
+ * device buffer). Stream as for every call (NULL: the call waits).
+ * Errors: MSI_EINVAL (NULL pointers; parts < 1; k_in or k outside [1, 1024]; k above
+ * parts * k_in), MSI_ENOMEM, MSI_ECUDA.
+ */
+MSI_API msi_status msi_merge_topk(const int64_t* ids, const double* sqdists64, int32_t parts, int64_t nq,
+                                  int32_t k_in, int32_t k, int64_t* out_ids, float* out_dists,
+                                  double* out_sqdists64, void* stream);
+
+/*
  * msi_lower_bounds_noalloc -- msi_lower_bounds for callers that cannot allocate
  * device memory. The paper has no counterpart: it exists for code that must not
  * call cudaMalloc, such as code held to a device-memory budget by an allocator or

@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "MsiError", "Index", "msi_build", "msi_knn", "msi_knn_ex", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
-    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "Server", "MSI_BUILD_BORROW", "MSI_BUILD_BALANCED_SPLIT", "MSI_MAX_K", "library_path",
+    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "msi_merge_topk", "Server", "MSI_BUILD_BORROW", "MSI_BUILD_BALANCED_SPLIT", "MSI_MAX_K", "library_path",
 ]
 
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
@@ -96,6 +96,8 @@ _lib.msi_set_timing.argtypes = [_vp, _i32]
 _lib.msi_set_timing.restype = ctypes.c_int
 _lib.msi_lower_bounds_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.msi_lower_bounds_noalloc.restype = ctypes.c_int
+_lib.msi_merge_topk.argtypes = [_vp, _vp, _i32, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
+_lib.msi_merge_topk.restype = ctypes.c_int
 
 
 class _ServerOpts(ctypes.Structure):
@@ -350,6 +352,31 @@ def msi_lower_bounds_noalloc(index, query, series_lb, leaf_lb, stream=None):
     float32 [n] and [leaves]); the library allocates nothing for this call."""
     _check(_lib.msi_lower_bounds_noalloc(ctypes.c_void_p(index.handle), _ptr(query, np.float32),
                                          _ptr(series_lb, np.float32), _ptr(leaf_lb, np.float32), _stream(stream)))
+
+
+def msi_merge_topk(ids, sqdists64, k, stream=None):
+    """msi_merge_topk: ids int64 [parts, nq, k_in] and sqdists64 float64 [parts, nq,
+    k_in] (each row sorted by (distance, id), ids distinct across parts), numpy or
+    torch. Returns (ids int64 [nq, k], dists float32 [nq, k], sqdists64 [nq, k]),
+    allocated like `ids` (numpy, or torch on its device)."""
+    parts, nq, kin = ids.shape
+    if _is_torch(ids):
+        import torch
+        if sqdists64.dtype != torch.float64 or not sqdists64.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor of distances")
+        oi = torch.empty((nq, k), dtype=torch.int64, device=ids.device)
+        od = torch.empty((nq, k), dtype=torch.float32, device=ids.device)
+        o64 = torch.empty((nq, k), dtype=torch.float64, device=ids.device)
+        dp, o64p = ctypes.c_void_p(sqdists64.data_ptr()), ctypes.c_void_p(o64.data_ptr())
+    else:
+        sqdists64 = np.ascontiguousarray(sqdists64, dtype=np.float64)
+        oi = np.empty((nq, k), dtype=np.int64)
+        od = np.empty((nq, k), dtype=np.float32)
+        o64 = np.empty((nq, k), dtype=np.float64)
+        dp, o64p = ctypes.c_void_p(sqdists64.ctypes.data), ctypes.c_void_p(o64.ctypes.data)
+    _check(_lib.msi_merge_topk(_ptr(ids, np.int64), dp, parts, nq, kin, k, _ptr(oi, np.int64), _ptr(od, np.float32),
+                               o64p, _stream(stream)))
+    return oi, od, o64
 
 
 class Server:

@@ -4,8 +4,9 @@ on outputs the oracle can compute one by one:
   - the SAX words of sampled blocks of series, bit-exact;
   - every returned distance equals the oracle's FP64 distance to the returned id;
   - for noisy members, the answer is no farther than the member itself;
-  - for a few queries, the full answer of the oracle's serial scan over the whole
-    collection, regenerated on the host chunk by chunk.
+  - for 24 queries (12 fresh walks, 4 noisy members at each sigma), the full k = 1
+    and k = 10 answers of the oracle's serial scan over the whole collection,
+    regenerated on the host chunk by chunk.
 MSI_FULLSIZE_N overrides the collection size (default 100M)."""
 import os
 
@@ -75,23 +76,43 @@ def test_every_answer_distance_and_member_bound(setup):
             assert dists[i, 0] <= np.sqrt(oracle.sqdist(zm, zq)) * (1 + 1e-6)
 
 
-def test_full_scan_of_sampled_queries(setup):
-    msi, index, ids, dists, Q, n_fresh, members = setup
-    picks = [0, n_fresh + 2, n_fresh]  # a fresh walk, a sigma = 1 copy, a sigma = 0.01 copy
-    zqs = [oracle.znorm(Q[i])[0] for i in picks]
-    best = [(np.inf, -1)] * len(picks)
-    chunk = 4_000_000
-    for c0 in range(0, N, chunk):
-        cnt = min(chunk, N - c0)
-        Z = oracle.summarise(datagen.walks(0, c0, cnt, LEN), 16, 256, want_paa=False)[0]
+def full_scan(gen, n, zqs, k, chunk=4_000_000):
+    """The oracle's exact answer over a whole collection for several queries at once:
+    the collection regenerated on the host chunk by chunk (gen(first, count)),
+    z-normalised by the oracle, every chunk scanned for every query, the per-chunk
+    top-k lists merged by (FP64 squared distance, id)."""
+    best = [[] for _ in zqs]
+    for c0 in range(0, n, chunk):
+        cnt = min(chunk, n - c0)
+        Z = oracle.summarise(gen(c0, cnt), 16, 256, want_paa=False)[0]
         for j, zq in enumerate(zqs):
-            oid, od2 = oracle.knn_scan(Z, zq, 1)
-            cand = (od2[0], int(oid[0]) + c0)
-            if cand < best[j]:
-                best[j] = cand
+            oid, od2 = oracle.knn_scan(Z, zq, k)
+            best[j] = sorted(best[j] + [(float(d), int(i) + c0) for d, i in zip(od2, oid)])[:k]
+    return best
+
+
+# 24 of the 100 queries: 12 fresh walks, and 12 noisy members, 4 each at sigma = 0.01,
+# 0.1 and 1 (the plan cycles sigma through the members in that order)
+PICKS_FRESH = list(range(12))
+
+
+def test_full_scan_of_24_queries_k1_and_k10(setup):
+    """24 of the benchmark's queries answered over the whole 100M collection by the
+    oracle's serial scan: the batched k = 1 answers of the benchmark call and a
+    batched k = 10 call must return exactly the oracle's ids (distances within 1e-4)."""
+    import torch
+    msi, index, ids, dists, Q, n_fresh, members = setup
+    picks = PICKS_FRESH + list(range(n_fresh, n_fresh + 12))
+    ids10, d10 = msi.msi_knn(index, torch.from_numpy(Q[picks]).cuda(), 10)
+    ids10, d10 = ids10.cpu().numpy(), d10.cpu().numpy()
+    best = full_scan(lambda c0, cnt: datagen.walks(0, c0, cnt, LEN), N, [oracle.znorm(Q[i])[0] for i in picks], 10)
     for j, i in enumerate(picks):
-        assert ids[i, 0] == best[j][1], f"query {i}: {ids[i, 0]} vs oracle {best[j][1]}"
-        np.testing.assert_allclose(dists[i, 0], np.sqrt(best[j][0]), rtol=1e-4)
+        o_d2 = np.array([b[0] for b in best[j]])
+        o_id = np.array([b[1] for b in best[j]])
+        assert ids[i, 0] == o_id[0], f"k=1 query {i}: {ids[i, 0]} vs oracle {o_id[0]}"
+        np.testing.assert_allclose(dists[i, 0], np.sqrt(o_d2[0]), rtol=1e-4)
+        assert np.array_equal(ids10[j], o_id), f"k=10 query {i}: {ids10[j]} vs oracle {o_id}"
+        np.testing.assert_allclose(d10[j], np.sqrt(o_d2), rtol=1e-4)
 
 
 def test_dtw_at_full_size_against_sampled_scans(setup):

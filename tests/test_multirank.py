@@ -1,7 +1,10 @@
-"""The multi-rank path on the CPU: two gloo ranks each answer the queries over their
-half of the collection (with the oracle, as a GPU rank answers with its index) and
-merge through paper_2009_00786_gb300.shard; the merged answer must equal the oracle's
-answer over the whole collection, ties included."""
+"""The multi-rank exchange on the CPU: two gloo ranks each answer the queries over
+their half of the collection (with the oracle, as a GPU rank answers with its index)
+and exchange them through paper_2009_00786_gb300.shard.gather_merge; the merged answer
+must equal the oracle's answer over the whole collection, ties included. The library
+merges on the GPU (msi_merge_topk, tested in test_gpu_multirank.py); here, with no
+GPU, the merge step is the definition written out: all candidates sorted by
+(distance, id), the first k kept."""
 import os
 import socket
 
@@ -12,6 +15,18 @@ import datagen
 import oracle
 
 N, LEN, K = 3000, 128, 7
+
+
+def host_merge(gi, gd, k):
+    """The k smallest of every part's candidates by (FP64 distance, id)."""
+    ids = np.concatenate(list(gi.numpy()), axis=1)
+    d64 = np.concatenate(list(gd.numpy()), axis=1)
+    out_i = np.empty((ids.shape[0], k), dtype=np.int64)
+    out_d = np.empty((ids.shape[0], k), dtype=np.float64)
+    for q in range(ids.shape[0]):
+        order = np.lexsort((ids[q], d64[q]))[:k]
+        out_i[q], out_d[q] = ids[q, order], d64[q, order]
+    return out_i, np.sqrt(out_d).astype(np.float32), out_d
 
 
 def _free_port():
@@ -38,7 +53,7 @@ def _rank_dtw(rank, world, port, out_path):
         i, d = oracle.knn_scan_dtw(Z, oracle.znorm(q)[0], K, 6)
         ids.append(i + first)
         d2.append(d)
-    mi, md = shard.gather_merge(np.array(ids), np.array(d2), K)
+    mi, _, md = shard.gather_merge(np.array(ids), np.array(d2), K, merge=host_merge)
     if rank == 0:
         np.savez(out_path, ids=mi, d2=md)
     dist.destroy_process_group()
@@ -85,7 +100,7 @@ def _rank(rank, world, port, out_path):
         i, d = oracle.knn_scan(Z, oracle.znorm(q)[0], K)
         ids.append(i + first)
         d2.append(d)
-    mi, md = shard.gather_merge(np.array(ids), np.array(d2), K)
+    mi, _, md = shard.gather_merge(np.array(ids), np.array(d2), K, merge=host_merge)
     if rank == 0:
         np.savez(out_path, ids=mi, d2=md)
     dist.destroy_process_group()
@@ -110,11 +125,3 @@ def test_two_gloo_ranks_merge_to_the_whole_answer(tmp_path):
         assert np.array_equal(got["ids"][i], oid)
         assert np.array_equal(got["d2"][i], od2)
     assert list(got["ids"][-1][:2]) == [10, 2500]
-
-
-def test_merge_orders_by_distance_then_id():
-    from paper_2009_00786_gb300.shard import merge_topk
-    a_ids, a_d = np.array([[5, 9]]), np.array([[1.0, 2.0]])
-    b_ids, b_d = np.array([[3, 7]]), np.array([[1.0, 1.5]])
-    mi, md = merge_topk([a_ids, b_ids], [a_d, b_d], 3)
-    assert list(mi[0]) == [3, 5, 7] and list(md[0]) == [1.0, 1.0, 1.5]

@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--dtw", action="store_true", help="exact k-NN under DTW (window 10%%) on the same workload")
     p.add_argument("--query-slots", type=int, default=0,
                    help="concurrent query slots of the index (0: the autotuner's choice, default schedule 16)")
-    p.add_argument("--no-autotune", action="store_true", help="keep the default batched schedule (16 slots, share 3)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default batched schedule (the batched chain, groups of 128, share 4)")
     p.add_argument("--slot-capacity", type=int, default=0,
                    help="entries of each bounded query slot's candidate and survivor lists (0: the defaults)")
     p.add_argument("--workload", default="walks", choices=["walks", "mixed"],
@@ -416,12 +417,16 @@ def main():
     else:
         Qt = torch.from_numpy(datagen.paper_queries(n, length, count=nq, data_seed=0, fresh_seed=7,
                                                     pick_seed=8)).to(dev) if first_id == 0 else Q
-    schedule = {"query_slots": args.query_slots or 16, "grid_share": 3, "autotuned": False}
+    if args.query_slots:
+        msi.msi_schedule_set(index, batch_chain=0)
+    schedule = dict(msi.msi_schedule_get(index), autotuned=False)
     if not args.no_autotune and not args.query_slots:
         tr = msi.msi_autotune(index, Qt, k, stream=stream)
-        schedule = {"query_slots": tr["query_slots"], "grid_share": tr["grid_share"], "autotuned": True,
+        schedule = {"batch_chain": tr["batch_chain"], "batch_group": tr["batch_group"],
+                    "batch_share": tr["batch_share"], "query_slots": tr["query_slots"],
+                    "grid_share": tr["grid_share"], "autotuned": True,
                     "candidates": tr["candidates"], "tuned_qps": tr["queries_per_s"],
-                    "default_schedule_qps": tr["default_queries_per_s"],
+                    "untuned_schedule_qps": tr["default_queries_per_s"],
                     "tuning_queries": "a disjoint set of the same mix (seeds 7 and 8)"}
 
     def step():

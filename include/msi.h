@@ -39,7 +39,7 @@ extern "C" {
 #define MSI_API
 #endif
 
-#define MSI_ABI_VERSION 2
+#define MSI_ABI_VERSION 3
 #define MSI_MAX_SEGMENTS 16          /* one SAX word fits 16 bytes                    */
 #define MSI_MAX_CARDINALITY 256      /* 8-bit symbols (Section II-B)                  */
 #define MSI_MAX_LEN 4096             /* longest series                                */
@@ -296,26 +296,50 @@ MSI_API msi_status msi_query_stats_get(msi_index* index, msi_query_stats* stats,
 MSI_API msi_status msi_set_timing(msi_index* index, int32_t enable);
 
 /*
- * msi_autotune -- choose the batched-query schedule of an index by measurement. The
- * paper runs one query after another (Section IV, "Setup"); a batched msi_knn call here
- * runs its queries concurrently on query slots, each with its own stream and
- * workspace, and each query's persistent grids are divided by min(slots, grid share).
+ * The schedule of batched msi_knn calls (nq > 1, Euclidean). The paper runs one
+ * query after another (Section IV, "Setup"); here a call's queries run together in
+ * one of two forms, with the same answers:
+ *  - the batched chain (batch_chain = 1, the default): one kernel launch per stage of
+ *    the search for a group of up to batch_group queries, each query with its own
+ *    workspace and 1/batch_share of each persistent grid;
+ *  - query slots (batch_chain = 0): each query runs its own chain of launches on one
+ *    of query_slots streams, its grids divided by min(query_slots, grid_share).
+ * msi_schedule_set changes it (MSI_EINVAL outside: query_slots 1..64, grid_share
+ * 1..64, batch_group 1..1024, batch_share 1..64); msi_schedule_get reads it.
+ */
+typedef struct msi_schedule {
+  int32_t batch_chain;
+  int32_t query_slots;
+  int32_t grid_share;
+  int32_t batch_group;
+  int32_t batch_share;
+} msi_schedule;
+MSI_API msi_status msi_schedule_set(msi_index* index, const msi_schedule* schedule);
+MSI_API msi_status msi_schedule_get(const msi_index* index, msi_schedule* schedule);
+
+/*
+ * msi_autotune -- choose the batched-query schedule of an index by measurement.
  * This call times msi_knn on `queries` (nq >= 2 of them, host or device, as msi_knn)
- * with k neighbours for every candidate schedule: query slots in {4, 8, 12, 16, 24,
- * 32} (at most 64) and grid shares in {1, 2, 3, 4, 6} up to the slot count. Each
- * candidate runs `reps` timed calls (0 selects 3) after three untimed ones, with CUDA
- * events on `stream` (NULL: the index's stream). The fastest schedule (queries/s)
- * stays with the index; answers are the same under every schedule. `out` (host, may
- * be NULL) receives the choice. Slot workspaces are allocated as needed and kept.
+ * with k neighbours for every candidate schedule: the batched chain with groups of
+ * {32, 64, 128} queries (at most nq) and batch shares {1, 2, 4, 8}; query slots
+ * {4, 8, 12, 16, 24, 32} with grid shares {1, 2, 3, 4, 6} up to the slot count.
+ * Each candidate runs `reps` timed calls (0 selects 3) after three untimed ones, with
+ * CUDA events on `stream` (NULL: the index's stream). The fastest schedule
+ * (queries/s) stays with the index; answers are the same under every schedule. `out`
+ * (host, may be NULL) receives the choice. Workspaces the choice does not use are
+ * released.
  * Errors: MSI_EINVAL for a NULL index or queries, nq < 2 or k outside msi_knn's
  * range; MSI_ENOMEM / MSI_ECUDA as msi_knn. On error the index keeps its schedule.
  */
 typedef struct msi_tune_result {
-  int32_t query_slots;   /* the schedule chosen                                  */
+  int32_t query_slots;   /* the schedule chosen (slots form)                     */
   int32_t grid_share;
   double queries_per_s;  /* its measured rate                                    */
   int32_t candidates;    /* schedules measured                                   */
-  double default_queries_per_s;  /* the rate of the default schedule (16, 3)     */
+  double default_queries_per_s;  /* the rate of the index's schedule before tuning */
+  int32_t batch_chain;   /* the form chosen, and its group and share (chain form) */
+  int32_t batch_group;
+  int32_t batch_share;
 } msi_tune_result;
 MSI_API msi_status msi_autotune(msi_index* index, const float* queries, int64_t nq, int32_t k, int32_t reps,
                                 msi_tune_result* out, void* stream);

@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "MsiError", "Index", "msi_build", "msi_knn", "msi_knn_ex", "msi_free", "msi_status_str", "msi_last_error",
     "msi_abi_version", "msi_index_info_get", "msi_index_export", "msi_lower_bounds",
-    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "msi_merge_topk", "Server", "MSI_BUILD_BORROW", "MSI_BUILD_BALANCED_SPLIT", "MSI_MAX_K", "library_path",
+    "msi_query_stats_get", "msi_set_timing", "msi_lower_bounds_noalloc", "msi_merge_topk", "msi_schedule_get", "msi_schedule_set", "Server", "MSI_BUILD_BORROW", "MSI_BUILD_BALANCED_SPLIT", "MSI_MAX_K", "library_path",
 ]
 
 MSI_OK, MSI_EINVAL, MSI_ENOMEM, MSI_ECUDA, MSI_ETIMEOUT, MSI_EINTERNAL = range(6)
@@ -96,6 +96,10 @@ _lib.msi_set_timing.argtypes = [_vp, _i32]
 _lib.msi_set_timing.restype = ctypes.c_int
 _lib.msi_lower_bounds_noalloc.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.msi_lower_bounds_noalloc.restype = ctypes.c_int
+_lib.msi_schedule_set.argtypes = [_vp, _vp]
+_lib.msi_schedule_set.restype = ctypes.c_int
+_lib.msi_schedule_get.argtypes = [_vp, _vp]
+_lib.msi_schedule_get.restype = ctypes.c_int
 _lib.msi_merge_topk.argtypes = [_vp, _vp, _i32, _i64, _i32, _i32, _vp, _vp, _vp, _vp]
 _lib.msi_merge_topk.restype = ctypes.c_int
 
@@ -334,17 +338,42 @@ def msi_set_timing(index, enable=True):
 
 class _TuneResult(ctypes.Structure):
     _fields_ = [("query_slots", ctypes.c_int32), ("grid_share", ctypes.c_int32), ("queries_per_s", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("default_queries_per_s", ctypes.c_double)]
+                ("candidates", ctypes.c_int32), ("default_queries_per_s", ctypes.c_double),
+                ("batch_chain", ctypes.c_int32), ("batch_group", ctypes.c_int32), ("batch_share", ctypes.c_int32)]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("batch_chain", "query_slots", "grid_share", "batch_group",
+                                              "batch_share")]
 
 
 def msi_autotune(index, queries, k, reps=0, stream=None):
-    """msi_autotune: times the batched schedules (query slots x grid share) on
+    """msi_autotune: times the batched schedules (batched chain and query slots) on
     `queries` [nq >= 2, len] (host or device) and keeps the fastest for the index.
     Returns the choice as a dict."""
     out = _TuneResult()
     _check(_lib.msi_autotune(ctypes.c_void_p(index.handle), _ptr(queries, np.float32), queries.shape[0], k, reps,
                              ctypes.byref(out), _stream(stream)))
     return {f: getattr(out, f) for f, _ in _TuneResult._fields_}
+
+
+def msi_schedule_get(index):
+    """msi_schedule_get: the index's batched schedule as a dict."""
+    sc = _Schedule()
+    _check(_lib.msi_schedule_get(ctypes.c_void_p(index.handle), ctypes.byref(sc)))
+    return {f: getattr(sc, f) for f, _ in _Schedule._fields_}
+
+
+def msi_schedule_set(index, **changes):
+    """msi_schedule_set: changes the named fields of the index's batched schedule
+    (batch_chain, query_slots, grid_share, batch_group, batch_share)."""
+    cur = msi_schedule_get(index)
+    unknown = set(changes) - set(cur)
+    if unknown:
+        raise TypeError(f"unknown schedule fields {sorted(unknown)}")
+    cur.update(changes)
+    sc = _Schedule(**{f: int(v) for f, v in cur.items()})
+    _check(_lib.msi_schedule_set(ctypes.c_void_p(index.handle), ctypes.byref(sc)))
 
 
 def msi_lower_bounds_noalloc(index, query, series_lb, leaf_lb, stream=None):

@@ -110,6 +110,8 @@ void free_index(msi_index* ix) {
     if (p) cudaFree(p);
   msi::free_workspace(ix->qv);
   for (auto& qv : ix->slots) msi::free_workspace(qv);
+  for (auto& qv : ix->bws) msi::free_workspace(qv);
+  if (ix->bws_dev) cudaFree(ix->bws_dev);
   for (cudaStream_t st : ix->slot_streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : ix->slot_events) cudaEventDestroy(ev);
   if (ix->fork_event) cudaEventDestroy(ix->fork_event);
@@ -260,9 +262,20 @@ msi_status msi_knn(msi_index* ix, const float* queries, int64_t nq, int32_t k, i
 // i mod nslots) between a fork from and a join back into stream s. With `call`, the
 // kernels take the queries and outputs from that descriptor (graph capture); else
 // from the pointers given.
+// With the batched chain (ix->batch_chain) the queries run in groups of at most
+// batch_group queries, one launch per stage per group, and `call` must be given.
 static cudaError_t enqueue_batch(msi_index* ix, cudaStream_t s, int64_t cnt, int32_t k, const float* qd,
                                  int64_t* id_base, float* d_base, double* d64_base, const msi::CallDesc* call) {
   cudaError_t e;
+  if (ix->batch_chain) {
+    if (!call) return cudaErrorInvalidValue;
+    const int64_t G = std::max(1, ix->batch_group);
+    for (int64_t g0 = 0; g0 < cnt; g0 += G)
+      if ((e = msi::query_batch(ix, (int)std::min<int64_t>(G, cnt - g0), k, call, (int)g0, ix->ws_ovf + g0, s,
+                                nullptr, nullptr, nullptr)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+  }
   if ((e = cudaEventRecord(ix->fork_event, s)) != cudaSuccess) return e;
   for (int sl = 0; sl < ix->nslots; ++sl)
     if ((e = cudaStreamWaitEvent(ix->slot_streams[sl], ix->fork_event, 0)) != cudaSuccess) return e;
@@ -295,6 +308,7 @@ static cudaError_t capture_batch(msi_index* ix, cudaStream_t s, int64_t cnt, int
   if (!ix->call_dev && (e = cudaMalloc(&ix->call_dev, sizeof(msi::CallDesc))) != cudaSuccess) return e;
   if (!ix->call_host && (e = cudaMallocHost(&ix->call_host, sizeof(msi::CallDesc))) != cudaSuccess) return e;
   if ((e = msi::grids_setup(ix)) != cudaSuccess) return e;
+  if (ix->batch_chain && (e = msi::batch_setup(ix)) != cudaSuccess) return e;
   const int64_t before = ix->kernel_launches.load();
   if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
   const cudaError_t le = enqueue_batch(ix, s, cnt, k, nullptr, nullptr, nullptr, nullptr, ix->call_dev);
@@ -344,8 +358,20 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
   const bool host_out = !ids_dev || !d_dev || !d64_dev;
   // several queries run concurrently on the query slots
   // (DTW queries use the full workspace: their survivor lists outgrow a slot's)
-  const bool batched = nq > 1 && ix->nslots > 1 && !ix->timing && window < 0;
-  if (batched && (e = msi::slots_setup(ix)) != cudaSuccess) return cuda_fail(e, "allocating query slots");
+  // timing: the batched chain records its events around each group's series filter
+  // and row kernel (launched directly, not from a graph); the slot form times queries
+  // one at a time instead
+  const bool batched = nq > 1 && (ix->batch_chain || (ix->nslots > 1 && !ix->timing)) && window < 0;
+  int64_t timed = 0;  // entries of ix->events used by this chunk (three each)
+  if (batched && !ix->batch_chain && (e = msi::slots_setup(ix)) != cudaSuccess)
+    return cuda_fail(e, "allocating query slots");
+  if (batched && ix->batch_chain) {
+    if ((e = msi::batch_setup(ix)) != cudaSuccess) return cuda_fail(e, "allocating the batch workspaces");
+    if (!ix->call_dev && (e = cudaMalloc(&ix->call_dev, sizeof(msi::CallDesc))) != cudaSuccess)
+      return cuda_fail(e, "allocating the call descriptor");
+    if (!ix->call_host && (e = cudaMallocHost(&ix->call_host, sizeof(msi::CallDesc))) != cudaSuccess)
+      return cuda_fail(e, "allocating the call descriptor");
+  }
   for (int64_t c0 = 0; c0 < nq; c0 += chunk) {
     const int64_t cnt = std::min<int64_t>(chunk, nq - c0);
     const float* qd = queries + c0 * ix->len;
@@ -358,7 +384,19 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
     int64_t* id_base = ids_dev ? ids + c0 * k : ix->ws_ids;
     float* d_base = dists ? (d_dev ? dists + c0 * k : ix->ws_dists) : nullptr;
     double* d64_base = sqdists64 ? (d64_dev ? sqdists64 + c0 * k : ix->ws_d64) : nullptr;
-    if (batched) {
+    timed = 0;
+    if (batched && ix->timing) {  // the batched chain, group by group, with events
+      *ix->call_host = msi::CallDesc{qd, id_base, d_base, d64_base};
+      if ((e = cudaMemcpyAsync(ix->call_dev, ix->call_host, sizeof(msi::CallDesc), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(e, "copying the call descriptor");
+      const int64_t G = std::max(1, ix->batch_group);
+      for (int64_t g0 = 0; g0 < cnt; g0 += G, ++timed)
+        if ((e = msi::query_batch(ix, (int)std::min<int64_t>(G, cnt - g0), k, ix->call_dev, (int)g0, ix->ws_ovf + g0,
+                                  s, ix->events[3 * timed], ix->events[3 * timed + 1], ix->events[3 * timed + 2])) !=
+            cudaSuccess)
+          return cuda_fail(e, "launching the batched query kernels");
+    } else if (batched) {
       // A (queries, k) shape seen before runs as one CUDA graph, replayed with this
       // call's pointers; a new shape launches its kernels directly (and is remembered).
       msi_index::BatchGraph* g = nullptr;
@@ -381,6 +419,12 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
             (e = cudaGraphLaunch(g->exec, s)) != cudaSuccess)
           return cuda_fail(e, "launching the batched query graph");
         ix->kernel_launches += g->launches;
+      } else if (ix->batch_chain) {
+        *ix->call_host = msi::CallDesc{qd, id_base, d_base, d64_base};
+        if ((e = cudaMemcpyAsync(ix->call_dev, ix->call_host, sizeof(msi::CallDesc), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = enqueue_batch(ix, s, cnt, k, nullptr, nullptr, nullptr, nullptr, ix->call_dev)) != cudaSuccess)
+          return cuda_fail(e, "launching the batched query kernels");
       } else if ((e = enqueue_batch(ix, s, cnt, k, qd, id_base, d_base, d64_base, nullptr)) != cudaSuccess) {
         return cuda_fail(e, "launching the query kernels");
       }
@@ -391,6 +435,7 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
         ea = ix->events[3 * i];
         em = ix->events[3 * i + 1];
         eb = ix->events[3 * i + 2];
+        timed = i + 1;
       }
       e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
                          d64_base ? d64_base + i * k : nullptr, nullptr, s, ea, em, eb, window);
@@ -427,7 +472,7 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "query execution");
     }
     if (ix->timing) {
-      for (int64_t i = 0; i < cnt; ++i) {
+      for (int64_t i = 0; i < timed; ++i) {
         float ms = 0.f;
         float fms = 0.f;
         if (cudaEventElapsedTime(&ms, ix->events[3 * i], ix->events[3 * i + 2]) == cudaSuccess &&
@@ -462,6 +507,68 @@ void forget_graphs(msi_index* ix) {
 }
 }  // namespace
 
+namespace {
+struct Sched {
+  bool chain;
+  int slots, share, group, bshare;
+};
+Sched get_sched(const msi_index* ix) {
+  return Sched{ix->batch_chain, ix->nslots, ix->grid_share, ix->batch_group, ix->batch_share};
+}
+void put_sched(msi_index* ix, const Sched& c) {
+  ix->batch_chain = c.chain;
+  ix->nslots = c.slots;
+  ix->grid_share = c.share;
+  ix->batch_group = c.group;
+  ix->batch_share = c.bshare;
+}
+// Releases the slot and batch workspaces the index's schedule does not use (no call
+// may be in flight).
+void release_unused(msi_index* ix) {
+  uint32_t cand_cap = 0, surv_cap = 0;
+  msi::slot_capacities(ix, ix->slot_cap, &cand_cap, &surv_cap);
+  const int keep = ix->batch_chain ? 0 : ix->nslots;
+  while ((int)ix->slots.size() > keep) {
+    msi::free_workspace(ix->slots.back());
+    ix->device_bytes -= msi::workspace_bytes(ix, cand_cap, surv_cap);
+    cudaStreamDestroy(ix->slot_streams.back());
+    cudaEventDestroy(ix->slot_events.back());
+    ix->slots.pop_back();
+    ix->slot_streams.pop_back();
+    ix->slot_events.pop_back();
+  }
+  msi::batch_release(ix, ix->batch_chain ? ix->batch_group : 0);
+}
+}  // namespace
+
+msi_status msi_schedule_set(msi_index* ix, const msi_schedule* sc) {
+  g_err.clear();
+  if (!ix || !sc) return fail(MSI_EINVAL, "index or schedule is NULL");
+  if (sc->query_slots < 1 || sc->query_slots > 64 || sc->grid_share < 1 || sc->grid_share > 64 ||
+      sc->batch_group < 1 || sc->batch_group > 1024 || sc->batch_share < 1 || sc->batch_share > 64)
+    return fail(MSI_EINVAL, "schedule outside query_slots 1..64, grid_share 1..64, batch_group 1..1024, "
+                            "batch_share 1..64");
+  DeviceGuard guard(ix->device);
+  cudaError_t e = cudaStreamSynchronize(ix->own_stream);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "msi_schedule_set");
+  forget_graphs(ix);  // graphs hold the previous schedule's launches
+  put_sched(ix, Sched{sc->batch_chain != 0, sc->query_slots, sc->grid_share, sc->batch_group, sc->batch_share});
+  release_unused(ix);
+  return MSI_OK;
+}
+
+msi_status msi_schedule_get(const msi_index* ix, msi_schedule* sc) {
+  g_err.clear();
+  if (!ix || !sc) return fail(MSI_EINVAL, "index or schedule is NULL");
+  sc->batch_chain = ix->batch_chain ? 1 : 0;
+  sc->query_slots = ix->nslots;
+  sc->grid_share = ix->grid_share;
+  sc->batch_group = ix->batch_group;
+  sc->batch_share = ix->batch_share;
+  return MSI_OK;
+}
+
 msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t k, int32_t reps,
                         msi_tune_result* out, void* stream) {
   g_err.clear();
@@ -473,7 +580,7 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
   if (reps == 0) reps = 3;
   DeviceGuard guard(ix->device);
   cudaStream_t s = stream ? (cudaStream_t)stream : ix->own_stream;
-  const int keep_slots = ix->nslots, keep_share = ix->grid_share;
+  const Sched keep = get_sched(ix);
   const bool keep_timing = ix->timing;
   ix->timing = false;
   int64_t* ids = nullptr;
@@ -482,39 +589,57 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
   cudaError_t e;
   msi_status st = MSI_OK;
   double best = -1.0, def_rate = 0.0;
-  int best_slots = keep_slots, best_share = keep_share, count = 0;
+  Sched best_s = keep;
+  int count = 0;
+  // the candidates: the index's own schedule first, then the batched chain, then slots
+  std::vector<Sched> cands{keep};
+  for (int g : {32, 64, 128}) {
+    const int gg = (int)std::min<int64_t>(g, nq);
+    for (int bs : {1, 2, 4, 8}) {
+      const Sched c{true, keep.slots, keep.share, gg, bs};
+      bool dup = false;
+      for (const Sched& o : cands)
+        dup |= o.chain && o.group == c.group && o.bshare == c.bshare;
+      if (!dup) cands.push_back(c);
+    }
+  }
+  for (int sl : {4, 8, 12, 16, 24, 32})
+    for (int sh : {1, 2, 3, 4, 6}) {
+      if (sh > sl) continue;
+      const Sched c{false, sl, sh, keep.group, keep.bshare};
+      if (!(!keep.chain && keep.slots == sl && keep.share == sh)) cands.push_back(c);
+    }
   if ((e = cudaMalloc(&ids, sizeof(int64_t) * (size_t)nq * k)) != cudaSuccess ||
       (e = cudaMalloc(&dists, sizeof(float) * (size_t)nq * k)) != cudaSuccess ||
       (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
     st = cuda_fail(e, "autotune buffers");
   } else {
-    static const int kSlots[] = {4, 8, 12, 16, 24, 32};
-    static const int kShares[] = {1, 2, 3, 4, 6};
-    for (int sl : kSlots) {
-      for (int sh : kShares) {
-        if (sh > sl || st != MSI_OK) continue;
-        forget_graphs(ix);  // graphs hold the previous schedule's streams and grids
-        ix->nslots = std::min(sl, 64);
-        ix->grid_share = sh;
-        for (int w = 0; w < 3 && st == MSI_OK; ++w) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
-        if (st != MSI_OK) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == MSI_OK; ++r) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
-        if (st != MSI_OK) break;
-        float ms = 0.f;
-        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
-            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
-          st = cuda_fail(e, "autotune timing");
-          break;
-        }
-        const double rate = ms > 0.f ? (double)nq * reps / (ms * 1e-3) : 0.0;
-        ++count;
-        if (sl == msi::kDefaultQuerySlots && sh == msi::kSlotGridShare) def_rate = rate;
-        if (rate > best) {
-          best = rate;
-          best_slots = sl;
-          best_share = sh;
-        }
+    bool batch_released = false;
+    for (const Sched& c : cands) {
+      if (st != MSI_OK) break;
+      forget_graphs(ix);  // graphs hold the previous schedule's streams and grids
+      if (!c.chain && !batch_released) {  // the slot candidates do not hold batch workspaces too
+        msi::batch_release(ix, 0);
+        batch_released = true;
+      }
+      put_sched(ix, c);
+      for (int w = 0; w < 3 && st == MSI_OK; ++w) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
+      if (st != MSI_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && st == MSI_OK; ++r) st = knn_impl(ix, queries, nq, k, -1, ids, dists, nullptr, s);
+      if (st != MSI_OK) break;
+      float ms = 0.f;
+      if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        st = cuda_fail(e, "autotune timing");
+        break;
+      }
+      const double rate = ms > 0.f ? (double)nq * reps / (ms * 1e-3) : 0.0;
+      if (count == 0) def_rate = rate;
+      ++count;
+      if (rate > best) {
+        best = rate;
+        best_s = c;
       }
     }
   }
@@ -524,31 +649,19 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
   if (e1) cudaEventDestroy(e1);
   forget_graphs(ix);
   ix->timing = keep_timing;
-  if (st != MSI_OK) {
-    ix->nslots = keep_slots;
-    ix->grid_share = keep_share;
-    return st;
-  }
-  ix->nslots = best_slots;
-  ix->grid_share = best_share;
-  // release the slots the chosen schedule does not use (every call above has finished)
-  uint32_t cand_cap = 0, surv_cap = 0;
-  msi::slot_capacities(ix, ix->slot_cap, &cand_cap, &surv_cap);
-  while ((int)ix->slots.size() > ix->nslots) {
-    msi::free_workspace(ix->slots.back());
-    ix->device_bytes -= msi::workspace_bytes(ix, cand_cap, surv_cap);
-    cudaStreamDestroy(ix->slot_streams.back());
-    cudaEventDestroy(ix->slot_events.back());
-    ix->slots.pop_back();
-    ix->slot_streams.pop_back();
-    ix->slot_events.pop_back();
-  }
+  put_sched(ix, st == MSI_OK ? best_s : keep);
+  cudaStreamSynchronize(s);
+  release_unused(ix);
+  if (st != MSI_OK) return st;
   if (out) {
-    out->query_slots = best_slots;
-    out->grid_share = best_share;
+    out->query_slots = best_s.slots;
+    out->grid_share = best_s.share;
     out->queries_per_s = best;
     out->candidates = count;
     out->default_queries_per_s = def_rate;
+    out->batch_chain = best_s.chain ? 1 : 0;
+    out->batch_group = best_s.group;
+    out->batch_share = best_s.bshare;
   }
   return MSI_OK;
 }

@@ -134,6 +134,8 @@ struct QueryView {
   uint32_t npartials_rows;      // warps of the row (or DTW) refinement launch
   uint32_t cand_cap;            // entries of cand / rc_d / rc_id
   uint32_t surv_cap;            // entries of surv
+  uint32_t items_cap;           // entries of items (a query that needs more overflows)
+  uint32_t blks_cap;            // entries of blks (likewise)
   uint32_t* ovf;                // per-query overflow flag written by q_finalize (or nullptr)
   float* qenv;                  // [2][len]: LB_Keogh envelope of the query, upper then lower (DTW)
   uint32_t* khist;              // [256]: k > 1, kept candidates per bucket of [0, kbase)
@@ -331,6 +333,15 @@ struct msi_index {
   bool ws_ready = false;
   msi::QueryView qv{};
   std::vector<msi::QueryView> slots;
+  // batched chain: one workspace per query of a batch (bounded lists), and their
+  // views in device memory for the batch kernels
+  std::vector<msi::QueryView> bws;
+  msi::QueryView* bws_dev = nullptr;
+  int bws_dev_cap = 0;
+  bool batch_chain = true;   // batched calls run the batched chain (false: the query slots)
+  int batch_group = 128;     // most queries per batched launch
+  int batch_share = 4;       // the batched kernels give each query 1/batch_share of a grid
+  bool batch_pdl = true;     // stages of a batch overlap their launch with the previous tail
   std::vector<cudaStream_t> slot_streams;
   std::vector<cudaEvent_t> slot_events;
   cudaEvent_t fork_event = nullptr;
@@ -406,10 +417,12 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
 cudaError_t slots_setup(msi_index* ix);
+// items_cap: work items (and 8x that many block tasks) a query may list; 0: room for
+// any query. A query that needs more is flagged as overflowed and run again.
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
-                            int64_t* bytes);
+                            int64_t* bytes, uint32_t items_cap = 0);
 void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap);
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap = 0);
 void free_workspace(QueryView& qv);
 // window < 0: Euclidean distance; window >= 0: DTW with that Sakoe-Chiba half-width.
 // call != nullptr: q_dev / ids_dev / dists_dev / d64_dev are ignored and query qi of
@@ -420,6 +433,14 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
                       int qi = 0);
 // Persistent grid sizes of the query kernels, computed once per index.
 cudaError_t grids_setup(msi_index* ix);
+// Batched chain (msi_query.cu): workspaces for ix->batch_group queries; then one launch
+// per stage for `count` queries of the call descriptor, queries qbase .. qbase+count-1
+// (count <= batch_group), each flagging in ovf[i] whether its bounded lists overflowed.
+cudaError_t batch_setup(msi_index* ix);
+void batch_release(msi_index* ix, int keep);
+// ev_a / ev_m / ev_b, when given, bracket the series filter and the row kernel.
+cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, int qbase, uint32_t* ovf,
+                        cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b);
 cudaError_t export_z(msi_index* ix, float* z_dev, cudaStream_t s);
 cudaError_t lower_bounds(msi_index* ix, const float* q_dev, float* series_lb_dev, float* leaf_lb_dev,
                          cudaStream_t s);

@@ -266,9 +266,8 @@ __device__ __forceinline__ float warp_fine_lb2(const IndexView& ix, const float*
 }
 
 // ------------------------------------------------------------------ q_prep
-__global__ void __launch_bounds__(kThreads)
-q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
-  pdl_begin();
+__device__ __forceinline__ void q_prep_body(const IndexView& ix, const float* __restrict__ q, const QueryView& qv, int k) {
+  
   if (qv.call) q = qv.call->queries + (size_t)qv.qi * ix.len;
   extern __shared__ float zs[];  // [len]
   __shared__ float thr_up_s[257], thr_lo_s[257];
@@ -466,6 +465,12 @@ q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads)
+q_prep(IndexView ix, const float* __restrict__ q, QueryView qv, int k) {
+  pdl_begin();
+  q_prep_body(ix, q, qv, k);
+}
+
 // ------------------------------------------------------------ k-th histogram
 // For k > 1 the candidates kept below kbase (the k-th best of the seed and front
 // leaves) are counted in 256 equal buckets of [0, kbase). If the buckets up to b hold
@@ -511,9 +516,8 @@ __device__ __forceinline__ unsigned khist_bound(const uint32_t* khist, float kba
 }
 
 // ------------------------------------------------------------------ q_seed
-__global__ void __launch_bounds__(kThreads)
-q_seed(IndexView ix, QueryView qv) {
-  pdl_begin();
+__device__ __forceinline__ void q_seed_body(const IndexView& ix, const QueryView& qv) {
+  
   extern __shared__ __align__(16) float qs[];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(qs, qv.qz, ix.len);
@@ -586,9 +590,14 @@ q_seed(IndexView ix, QueryView qv) {
   if (threadIdx.x == 0 && s_skip) atomicSub(&qv.st->seed_done, s_skip);
 }
 
-__global__ void __launch_bounds__(1024)
-q_seed_select(QueryView qv, int base) {
+__global__ void __launch_bounds__(kThreads)
+q_seed(IndexView ix, QueryView qv) {
   pdl_begin();
+  q_seed_body(ix, qv);
+}
+
+__device__ __forceinline__ void q_seed_select_body(const QueryView& qv, int base) {
+  
   __shared__ uint32_t hist[256], sel[2];
   const uint32_t count = min(qv.st->cand_count, qv.cand_cap);
   const unsigned long long* c = qv.cand;
@@ -612,10 +621,15 @@ q_seed_select(QueryView qv, int base) {
   if (threadIdx.x == 0) qv.st->kbase = kb;
 }
 
-// ------------------------------------------------------------------ q_leaf_filter
-__global__ void __launch_bounds__(kThreads)
-q_leaf_filter(IndexView ix, QueryView qv) {
+__global__ void __launch_bounds__(1024)
+q_seed_select(QueryView qv, int base) {
   pdl_begin();
+  q_seed_select_body(qv, base);
+}
+
+// ------------------------------------------------------------------ q_leaf_filter
+__device__ __forceinline__ void q_leaf_filter_body(const IndexView& ix, const QueryView& qv) {
+  
   __shared__ float thr_up_s[257], thr_lo_s[257], up_s[16], lo_s[16];
   for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
     thr_up_s[v] = ix.thr_up[v];
@@ -665,9 +679,13 @@ q_leaf_filter(IndexView ix, QueryView qv) {
       qv.leaf_list[slot] = (uint32_t)l;
       qv.leaf_lb2[slot] = lb2;
       const uint32_t t0 = b / kItem;
-      for (uint32_t j = 0; j < nit; ++j)
-        qv.items[ibase + j] = make_uint4(max(b, (t0 + j) * kItem), min(e, (t0 + j + 1) * kItem), __float_as_uint(lb2),
-                                         (uint32_t)l);
+      for (uint32_t j = 0; j < nit; ++j) {
+        if (ibase + j < qv.items_cap)
+          qv.items[ibase + j] = make_uint4(max(b, (t0 + j) * kItem), min(e, (t0 + j + 1) * kItem), __float_as_uint(lb2),
+                                           (uint32_t)l);
+        else
+          qv.st->overflow = 1u;
+      }
     }
   }
   // the block's lowest-bound surviving leaf (ties: lowest leaf), for the early
@@ -686,6 +704,12 @@ q_leaf_filter(IndexView ix, QueryView qv) {
     for (int w = 0; w < kThreads / 32; ++w) b = s_min[w] < b ? s_min[w] : b;
     qv.blockmin[blockIdx.x] = b;
   }
+}
+
+__global__ void __launch_bounds__(kThreads)
+q_leaf_filter(IndexView ix, QueryView qv) {
+  pdl_begin();
+  q_leaf_filter_body(ix, qv);
 }
 
 // The m lowest (bound bits << 32 | leaf) keys among the leaf filter's per-block minima
@@ -742,9 +766,8 @@ __host__ __device__ inline int front_count(int k) { return k == 1 ? 4 : kMaxFron
 // picks them from the leaf filter's per-block minima (front_leaves); warps take their
 // positions in a stride, skipping the seed range. Block 0 records the leaves, which
 // the block filter then skips.
-__global__ void __launch_bounds__(kThreads)
-q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
-  pdl_begin();
+__device__ __forceinline__ void q_front_body(const IndexView& ix, const QueryView& qv, uint32_t nblockmin) {
+  
   extern __shared__ __align__(16) float qs[];
   __shared__ unsigned s_min;
   __shared__ uint32_t s_leaf[kMaxFront], s_beg[kMaxFront], s_pre[kMaxFront + 1];
@@ -825,6 +848,12 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads)
+q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
+  pdl_begin();
+  q_front_body(ix, qv, nblockmin);
+}
+
 // ------------------------------------------------------------ refinement
 // The refinement in three streaming kernels (ProcessQueue and CalculateRealDistance,
 // Algorithms 8-9, with the block filter, the per-series filter and the real distances
@@ -870,9 +899,8 @@ __device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, co
   return __fmul_rn(acc, seglen);
 }
 
-__global__ void __launch_bounds__(kBlkThreads)
-q_filter_blocks(IndexView ix, QueryView qv) {
-  pdl_begin();
+__device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const QueryView& qv) {
+  
   extern __shared__ __align__(16) float Ts[];  // [w][card]
   __shared__ int qsym_s[16];
   __shared__ uint32_t s_cnt, s_base;
@@ -882,7 +910,7 @@ q_filter_blocks(IndexView ix, QueryView qv) {
   if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
   const uint32_t nfront = qv.st->nfront;
   if (threadIdx.x < nfront) fl_s[threadIdx.x] = qv.st->front_leaf[threadIdx.x];
-  const uint32_t ntask = qv.st->item_count * kBlocksPerItem;
+  const uint32_t ntask = min(qv.st->item_count, qv.items_cap) * kBlocksPerItem;
   const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
   const float seglen = (float)ix.seglen;
   for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < ntask; t0 += gridDim.x * blockDim.x) {
@@ -906,9 +934,18 @@ q_filter_blocks(IndexView ix, QueryView qv) {
     __syncthreads();
     if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&qv.st->blk_count, s_cnt) : 0u;
     __syncthreads();
-    if (threadIdx.x < s_cnt) qv.blks[s_base + threadIdx.x] = s_out[threadIdx.x];
+    if (threadIdx.x < s_cnt) {
+      if (s_base + threadIdx.x < qv.blks_cap) qv.blks[s_base + threadIdx.x] = s_out[threadIdx.x];
+      else qv.st->overflow = 1u;
+    }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kBlkThreads)
+q_filter_blocks(IndexView ix, QueryView qv) {
+  pdl_begin();
+  q_filter_blocks_body(ix, qv);
 }
 
 // One warp per surviving block: bounds every position by its SAX word and buffers
@@ -927,9 +964,8 @@ __device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int
   return __fmul_rn(acc, s);
 }
 
-__global__ void __launch_bounds__(kFiltWarps * 32)
-q_filter_series(IndexView ix, QueryView qv) {
-  pdl_begin();
+__device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const QueryView& qv) {
+  
   extern __shared__ __align__(16) float Ts[];  // [w][card], then T5 [w][32]
   float* T5s = Ts + ix.w * ix.card;
   __shared__ uint2 buf_s[kFiltWarps][64];
@@ -948,7 +984,7 @@ q_filter_series(IndexView ix, QueryView qv) {
   uint4* qw = qw_s[warp];
   uint32_t* qp = qp_s[warp];
   QState* st = qv.st;
-  const uint32_t ntask = st->blk_count;
+  const uint32_t ntask = min(st->blk_count, qv.blks_cap);
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
   const int cshift = ix.bits > 5 ? ix.bits - 5 : 0;
@@ -1063,10 +1099,15 @@ q_filter_series(IndexView ix, QueryView qv) {
   }
 }
 
-template <bool KONE>
-__global__ void __launch_bounds__(kRowWarps * 32)
-q_refine_rows(IndexView ix, QueryView qv) {
+__global__ void __launch_bounds__(kFiltWarps * 32)
+q_filter_series(IndexView ix, QueryView qv) {
   pdl_begin();
+  q_filter_series_body(ix, qv);
+}
+
+template <bool KONE>
+__device__ __forceinline__ void q_refine_rows_body(const IndexView& ix, const QueryView& qv) {
+  
   extern __shared__ __align__(16) float qs[];
   smem_fill(qs, qv.qz, ix.len);
   __syncthreads();
@@ -1219,6 +1260,13 @@ q_refine_rows(IndexView ix, QueryView qv) {
   if (lane == 0 && gw < kMaxRefineWarps) qv.partials[kMaxRefineWarps + gw] = n_ref;
 }
 
+template <bool KONE>
+__global__ void __launch_bounds__(kRowWarps * 32)
+q_refine_rows(IndexView ix, QueryView qv) {
+  pdl_begin();
+  q_refine_rows_body<KONE>(ix, qv);
+}
+
 // ------------------------------------------------------------------ final pick
 // The k-th smallest candidate squared distance T; candidates at or below
 // T (1 + eps) are re-checked in FP64 (one block).
@@ -1315,10 +1363,8 @@ constexpr int kSortCap = 2048;  // (distance, id) pairs sorted in shared memory
 // The exact answer (one block of 1024 threads): the k-th smallest candidate, the FP64
 // re-check of every candidate within the fp32 margin of it, and the k smallest by
 // (FP64 distance, id), written to the outputs.
-__global__ void __launch_bounds__(1024)
-q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out,
-           double* __restrict__ d64_out) {
-  pdl_begin();
+__device__ __forceinline__ void q_finalize_body(const IndexView& ix, const QueryView& qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out, double* __restrict__ d64_out) {
+  
   if (qv.call) {
     const CallDesc c = *qv.call;
     const size_t off = (size_t)qv.qi * qv.k;
@@ -1462,6 +1508,98 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
     atomicAdd(&c[ST_FINE], s_part[3]);
     atomicAdd(&c[ST_FINE_FRONT], (unsigned long long)st->fine_front);
   }
+}
+
+__global__ void __launch_bounds__(1024)
+q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __restrict__ dists_out,
+           double* __restrict__ d64_out) {
+  pdl_begin();
+  q_finalize_body(ix, qv, ids_out, dists_out, d64_out);
+}
+
+// ------------------------------------------------------------ batched chain
+// A batch of queries runs the same chain with one launch per stage for the whole
+// batch: blockIdx.y selects the query (its workspace in a device array of query
+// views), blockIdx.x and gridDim.x divide that query's work exactly as in the
+// one-query kernels. The batch's queries and outputs come from a call descriptor
+// (query qbase + blockIdx.y of the call), so a captured graph serves every call of
+// one shape. Queries of a batch share no state: each keeps its own BSF, lists and
+// counters, and the answers are those of the same queries run one at a time.
+struct BatchArgs {
+  const QueryView* __restrict__ qvs;  // [batch] device array: one workspace per query
+  const CallDesc* call;   // queries and outputs of the call
+  uint32_t* ovf;          // [batch] per-query overflow flags
+  int qbase;              // index of the batch's first query in the call
+  int k;
+  uint32_t np, npr;       // warps of the series filter and row kernels, per query
+};
+
+// The view of query blockIdx.y, read in place (qb_views wrote this call's fields into
+// it first), so that a kernel keeps in registers only the fields it uses.
+__device__ __forceinline__ const QueryView& batch_view(const BatchArgs& a) { return a.qvs[blockIdx.y]; }
+
+// First stage of every batch: the per-call fields of each query's view.
+__global__ void qb_views(QueryView* qvs, BatchArgs a, int count) {
+  pdl_begin();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  QueryView& qv = qvs[b];
+  qv.k = a.k;
+  qv.ovf = a.ovf + b;
+  qv.call = a.call;
+  qv.qi = a.qbase + b;
+  qv.npartials = a.np;
+  qv.npartials_rows = a.npr;
+  qv.window = -1;
+}
+
+__global__ void __launch_bounds__(kThreads) qb_prep(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_prep_body(ix, nullptr, qv, a.k);
+}
+__global__ void __launch_bounds__(kThreads) qb_seed(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_seed_body(ix, qv);
+}
+__global__ void __launch_bounds__(1024) qb_seed_select(BatchArgs a, int base) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_seed_select_body(qv, base);
+}
+__global__ void __launch_bounds__(kThreads) qb_leaf_filter(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_leaf_filter_body(ix, qv);
+}
+__global__ void __launch_bounds__(kThreads) qb_front(IndexView ix, BatchArgs a, uint32_t nblockmin) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_front_body(ix, qv, nblockmin);
+}
+__global__ void __launch_bounds__(kBlkThreads) qb_filter_blocks(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_filter_blocks_body(ix, qv);
+}
+// (the minimum-blocks hints keep the one-query kernels' occupancy: the query view's
+// pointers come from memory here instead of the parameter bank)
+__global__ void __launch_bounds__(kFiltWarps * 32, 4) qb_filter_series(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_filter_series_body(ix, qv);
+}
+template <bool KONE>
+__global__ void __launch_bounds__(kRowWarps * 32, 3) qb_refine_rows(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_refine_rows_body<KONE>(ix, qv);
+}
+__global__ void __launch_bounds__(1024) qb_finalize(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_finalize_body(ix, qv, nullptr, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ DTW
@@ -1932,12 +2070,16 @@ cudaError_t dalloc(T** p, size_t count) {
 
 // One query workspace with room for cand_cap candidates and surv_cap survivors
 // (work items, block lists and leaf lists always have room for any query).
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap);
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap);
+
+// Work items any query can need: each leaf touches at most (its size / kItem) + 2
+// aligned tiles of kItem positions.
+static int64_t full_items(const msi_index* ix) { return ix->n / kItem + 2 * ix->L + 2; }
 
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
-                            int64_t* bytes) {
+                            int64_t* bytes, uint32_t items_cap) {
   cudaError_t e;
-  const size_t items = (size_t)(ix->n / kItem + 2 * ix->L + 2);
+  const size_t items = items_cap ? std::min<size_t>(items_cap, (size_t)full_items(ix)) : (size_t)full_items(ix);
   if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T5, (size_t)ix->w * 32)) != cudaSuccess) return e;
@@ -1957,16 +2099,18 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   qv.window = -1;
   qv.cand_cap = cand_cap;
   qv.surv_cap = surv_cap;
+  qv.items_cap = (uint32_t)items;
+  qv.blks_cap = (uint32_t)(kBlocksPerItem * items);
   qv.ovf = nullptr;
   qv.eps = margin_eps();
   qv.tau = margin_tau(ix->len);
-  *bytes += workspace_bytes(ix, cand_cap, surv_cap);
+  *bytes += workspace_bytes(ix, cand_cap, surv_cap, items_cap);
   return cudaSuccess;
 }
 
 // Device bytes of one query workspace (alloc_workspace).
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap) {
-  const int64_t items = ix->n / kItem + 2 * ix->L + 2;
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap) {
+  const int64_t items = items_cap ? std::min<int64_t>(items_cap, full_items(ix)) : full_items(ix);
   return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
          items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
@@ -2220,6 +2364,110 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   // q_prep, q_seed, q_leaf_filter, q_front, q_filter_blocks, q_filter_series,
   // q_refine_rows, q_finalize, and q_seed_select twice for k > 1.
   ix->kernel_launches += 8 + (k > 1 ? 2 : 0);
+  return cudaGetLastError();
+}
+
+// Batch workspaces: the candidate list as a query slot's, survivor lists of n / 16
+// entries (at least 2^20, at most 2^23), and 2^18 work items (2^21 block tasks): a
+// query that needs more overflows and is run again alone with room for all n.
+// A slot capacity given at build time bounds these lists as it bounds a slot's.
+static void batch_capacities(const msi_index* ix, uint32_t* cand_cap, uint32_t* surv_cap, uint32_t* items_cap) {
+  uint32_t sc;
+  slot_capacities(ix, ix->slot_cap, cand_cap, &sc);
+  if (ix->slot_cap) {
+    *surv_cap = sc;
+    *items_cap = (uint32_t)std::max(256, ix->slot_cap / 4);
+    return;
+  }
+  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, std::min<int64_t>(1 << 23, std::max<int64_t>(1 << 20, ix->n / 16)));
+  *items_cap = 1u << 18;
+}
+
+cudaError_t batch_setup(msi_index* ix) {
+  cudaError_t e;
+  if ((e = refine_config(ix)) != cudaSuccess) return e;
+  const int G = std::max(1, ix->batch_group);
+  if ((int)ix->bws.size() < G) {
+    uint32_t cc, sc, ic;
+    batch_capacities(ix, &cc, &sc, &ic);
+    while ((int)ix->bws.size() < G) {
+      QueryView qv{};
+      if ((e = alloc_workspace(ix, qv, cc, sc, &ix->device_bytes, ic)) != cudaSuccess) {
+        free_workspace(qv);
+        return e;
+      }
+      qv.counters = ix->qv.counters;
+      ix->bws.push_back(qv);
+    }
+  }
+  if (ix->bws_dev_cap < (int)ix->bws.size()) {
+    if (ix->bws_dev) cudaFree(ix->bws_dev);
+    ix->bws_dev = nullptr;
+    ix->bws_dev_cap = 0;
+    if ((e = cudaMalloc(&ix->bws_dev, sizeof(QueryView) * ix->bws.size())) != cudaSuccess) return e;
+    ix->bws_dev_cap = (int)ix->bws.size();
+    if ((e = cudaMemcpy(ix->bws_dev, ix->bws.data(), sizeof(QueryView) * ix->bws.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+// Frees the batch workspaces beyond the first `keep` (no batch may be in flight).
+void batch_release(msi_index* ix, int keep) {
+  uint32_t cc, sc, ic;
+  batch_capacities(ix, &cc, &sc, &ic);
+  while ((int)ix->bws.size() > keep) {
+    free_workspace(ix->bws.back());
+    ix->device_bytes -= workspace_bytes(ix, cc, sc, ic);
+    ix->bws.pop_back();
+  }
+}
+
+cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, int qbase, uint32_t* ovf,
+                        cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b) {
+  cudaError_t e;
+  if (count < 1 || count > (int)ix->bws.size() || count > 65535) return cudaErrorInvalidValue;
+  const bool pdl = ix->batch_pdl;
+  const int share = std::max(1, ix->batch_share);
+  const int series_grid = std::max(1, ix->grid_series / share);
+  const int rows_grid = std::max(1, (k == 1 ? ix->grid_rows1 : ix->grid_rowsk) / share);
+  const int blocks_grid = std::max(1, ix->grid_blocks / share);
+  BatchArgs a;
+  a.qvs = ix->bws_dev;
+  a.call = call;
+  a.ovf = ovf;
+  a.qbase = qbase;
+  a.k = k;
+  a.np = (uint32_t)std::min<int64_t>((int64_t)series_grid * kFiltWarps, kMaxRefineWarps);
+  a.npr = (uint32_t)std::min<int64_t>((int64_t)rows_grid * kRowWarps, kMaxRefineWarps);
+  const IndexView v = ix->view();
+  const unsigned B = (unsigned)count;
+  const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+  MSI_LAUNCH(qb_views, (B + 127) / 128, 128, 0, s, ix->bws_dev, a, count);
+  MSI_LAUNCH(qb_prep, dim3(1, B), kThreads, qbytes, s, v, a);
+  const int64_t seed_max = std::max<int64_t>(ix->cap, k);
+  const int64_t seed_per_block = (k == 1 && ix->wf) ? 8 * kSeedGroup : 8;
+  MSI_LAUNCH(qb_seed, dim3((unsigned)std::min<int64_t>((seed_max + seed_per_block - 1) / seed_per_block, 1024), B),
+             kThreads, qbytes, s, v, a);
+  if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 0);
+  const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
+  MSI_LAUNCH(qb_leaf_filter, dim3(nlf, B), kThreads, 0, s, v, a);
+  MSI_LAUNCH(qb_front, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ix->cap + 7) / 8, 256) / share), B),
+             kThreads, qbytes, s, v, a, nlf);
+  if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);
+  MSI_LAUNCH(qb_filter_blocks, dim3(blocks_grid, B), kBlkThreads, fsmem, s, v, a);
+  if (ev_a) cudaEventRecord(ev_a, s);
+  MSI_LAUNCH(qb_filter_series, dim3(series_grid, B), kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s,
+             v, a);
+  if (ev_m) cudaEventRecord(ev_m, s);
+  const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+  if (k == 1) MSI_LAUNCH(qb_refine_rows<true>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
+  else MSI_LAUNCH(qb_refine_rows<false>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
+  if (ev_b) cudaEventRecord(ev_b, s);
+  MSI_LAUNCH(qb_finalize, dim3(1, B), 1024, 0, s, v, a);
+  ix->kernel_launches += 9 + (k > 1 ? 2 : 0);
   return cudaGetLastError();
 }
 

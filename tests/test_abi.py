@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(msi):
 
 
 def test_status_strings_and_version(msi):
-    assert msi.msi_abi_version() == 2
+    assert msi.msi_abi_version() == 3
     names = [msi.msi_status_str(s) for s in range(6)]
     assert names == ["MSI_OK", "MSI_EINVAL", "MSI_ENOMEM", "MSI_ECUDA", "MSI_ETIMEOUT", "MSI_EINTERNAL"]
     assert msi.msi_status_str(99) == "MSI_UNKNOWN"

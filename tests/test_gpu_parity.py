@@ -225,16 +225,25 @@ def test_stats_counters(msi):
     # filter, row refinement, finalize
     assert st["kernel_launches"] == 6 * 10
     msi.msi_query_stats_get(ix, reset=True)
+    msi.msi_set_timing(ix, False)
+    # two queries in one call: the batched chain launches each stage once for both
+    # (views, prep, seed, leaf filter, front leaves, block filter, series filter, rows,
+    # finalize)
     msi.msi_knn(ix, Q[:2], 1)
-    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 2 * 8
-    msi.msi_knn(ix, Q[:1], 40)  # k > 32: the same chain, no register top-k
-    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 2 * 8 + 10
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9
+    msi.msi_knn(ix, Q[:1], 40)  # one query, k > 32: its own chain, no register top-k
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9 + 10
+    msi.msi_schedule_set(ix, batch_chain=0)  # the query slots: a chain per query
+    msi.msi_knn(ix, Q[:2], 1)
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9 + 10 + 2 * 8
 
 
-def test_batched_slots_match_single_queries_and_oracle(msi):
-    """Queries run concurrently on the query slots give, for each query, the answer it
-    gets alone, which is the oracle's; a slot whose bounded lists overflow (many
-    exact ties) hands its query back to the full-capacity workspace."""
+@pytest.mark.parametrize("chain", [1, 0])
+def test_batched_slots_match_single_queries_and_oracle(msi, chain):
+    """Queries run together (chain = 1: the batched chain, in groups of 4 queries per
+    launch; chain = 0: concurrent query slots) give, for each query, the answer it gets
+    alone, which is the oracle's; a query whose bounded lists overflow (many exact
+    ties) is handed back to the full-capacity workspace."""
     n, length = 6000, 256
     X = datagen.walks(201, 0, n, length)
     X[1000:3500] = X[999]  # 2501 identical series: every one is a tie at distance 0
@@ -242,6 +251,7 @@ def test_batched_slots_match_single_queries_and_oracle(msi):
     Q = np.concatenate([datagen.paper_queries(n, length, count=7, data_seed=201), X[[999, 3000]]])
     for k in (1, 5, 32, 100):
         batched = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=3, slot_capacity=1024)
+        msi.msi_schedule_set(batched, batch_chain=chain, batch_group=4, batch_share=2)
         single = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=1)
         ids_b, d_b = msi.msi_knn(batched, Q, k)
         for i, q in enumerate(Q):
@@ -252,7 +262,8 @@ def test_batched_slots_match_single_queries_and_oracle(msi):
         assert ids_b[-2][0] == 999 and list(ids_b[-1][:min(k, 3)]) == [999, 1000, 1001][:min(k, 3)]
 
 
-def test_repeated_batched_shape_replays_with_new_pointers(msi):
+@pytest.mark.parametrize("chain", [1, 0])
+def test_repeated_batched_shape_replays_with_new_pointers(msi, chain):
     """A batched call shape (queries, k) seen before runs as a captured CUDA graph that
     takes its queries and outputs from a per-call descriptor: calls of the same shape
     with other query sets and other output buffers (host, device, with and without the
@@ -265,6 +276,7 @@ def test_repeated_batched_shape_replays_with_new_pointers(msi):
             for j in range(3)]
     want = [[oracle.knn_scan(Z, oracle.znorm(q)[0], k)[0] for q in Q] for Q in sets]
     ix = msi.msi_build(X, segments=16, leaf_capacity=64, query_slots=4)
+    msi.msi_schedule_set(ix, batch_chain=chain, batch_group=4)
     msi.msi_query_stats_get(ix, reset=True)
     calls = 0
     for rep in range(2):
@@ -282,7 +294,8 @@ def test_repeated_batched_shape_replays_with_new_pointers(msi):
             assert np.all(d64_x.cpu().numpy() >= 0)
     st = msi.msi_query_stats_get(ix)
     assert st["queries"] == calls * nq
-    assert st["kernel_launches"] == calls * nq * 10
+    # per call: 3 groups of at most 4 queries x 11 stages (k > 1), or 9 chains of 10
+    assert st["kernel_launches"] == calls * (3 * 11 if chain else nq * 10)
     ix.close()
 
 
@@ -301,9 +314,15 @@ def test_autotune_keeps_answers_and_picks_a_measured_schedule(msi):
     with pytest.raises(msi.MsiError):
         msi.msi_autotune(ix, Qd[:1], k)  # one query cannot be batched
     tr = msi.msi_autotune(ix, Qd, k, reps=2)
-    assert tr["query_slots"] in (4, 8, 12, 16, 24, 32)
-    assert 1 <= tr["grid_share"] <= min(6, tr["query_slots"])
-    assert tr["candidates"] == 29 and tr["queries_per_s"] >= tr["default_queries_per_s"] > 0
+    if tr["batch_chain"]:
+        assert tr["batch_group"] in (24, 128) and tr["batch_share"] in (1, 2, 4, 8)
+    else:
+        assert tr["query_slots"] in (4, 8, 12, 16, 24, 32)
+        assert 1 <= tr["grid_share"] <= min(6, tr["query_slots"])
+    # the index's own schedule, 4 batched-chain and 29 slot schedules
+    assert tr["candidates"] == 34 and tr["queries_per_s"] >= tr["default_queries_per_s"] > 0
+    sched = msi.msi_schedule_get(ix)
+    assert sched["batch_chain"] == tr["batch_chain"]
     after = msi.msi_knn(ix, Q, k)
     assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
     for i, q in enumerate(Q):

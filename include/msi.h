@@ -313,6 +313,8 @@ typedef struct msi_schedule {
   int32_t grid_share;
   int32_t batch_group;
   int32_t batch_share;
+  int32_t batch_overlap;  /* chain form: 1 launches each stage early (programmatic
+                             dependent launch) so it starts as the previous ends */
 } msi_schedule;
 MSI_API msi_status msi_schedule_set(msi_index* index, const msi_schedule* schedule);
 MSI_API msi_status msi_schedule_get(const msi_index* index, msi_schedule* schedule);

@@ -554,6 +554,7 @@ msi_status msi_schedule_set(msi_index* ix, const msi_schedule* sc) {
   if (e != cudaSuccess) return cuda_fail(e, "msi_schedule_set");
   forget_graphs(ix);  // graphs hold the previous schedule's launches
   put_sched(ix, Sched{sc->batch_chain != 0, sc->query_slots, sc->grid_share, sc->batch_group, sc->batch_share});
+  ix->batch_pdl = sc->batch_overlap != 0;
   release_unused(ix);
   return MSI_OK;
 }
@@ -566,6 +567,7 @@ msi_status msi_schedule_get(const msi_index* ix, msi_schedule* sc) {
   sc->grid_share = ix->grid_share;
   sc->batch_group = ix->batch_group;
   sc->batch_share = ix->batch_share;
+  sc->batch_overlap = ix->batch_pdl ? 1 : 0;
   return MSI_OK;
 }
 

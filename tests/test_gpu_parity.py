@@ -219,11 +219,17 @@ def test_stats_counters(msi):
     assert st["leaves_total"] == 6 * ix.leaves
     assert 0 < st["series_refined"] <= 6 * 8000
     assert st["candidates"] >= 6 * 5 and st["rechecked"] >= 6 * 5
-    assert st["refine_launches"] == 6 and st["refine_ms"] > 0
+    # timed, the six queries run as one group of the batched chain: one series filter
+    # and one row kernel launch timed for the group
+    assert st["refine_launches"] == 1 and st["refine_ms"] > 0
     assert st["series_lower_bounded"] < 6 * 8000  # leaves were pruned
-    # prep, seed, seed pick, leaf filter, front leaf, seed pick, block filter, series
-    # filter, row refinement, finalize
-    assert st["kernel_launches"] == 6 * 10
+    # views, prep, seed, seed pick, leaf filter, front leaves, seed pick, block filter,
+    # series filter, row refinement, finalize: once for the group
+    assert st["kernel_launches"] == 11
+    msi.msi_query_stats_get(ix, reset=True)
+    msi.msi_knn(ix, Q[:1], 5)  # one query timed: its own chain
+    st = msi.msi_query_stats_get(ix)
+    assert st["refine_launches"] == 1 and st["kernel_launches"] == 10
     msi.msi_query_stats_get(ix, reset=True)
     msi.msi_set_timing(ix, False)
     # two queries in one call: the batched chain launches each stage once for both

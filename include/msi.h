@@ -284,6 +284,8 @@ typedef struct msi_query_stats {
   int64_t fine_bounded;          /* series the series filter bounded by the fine PAA */
   int64_t front_fine_bounded;    /* front-leaf rows bounded by the fine PAA         */
   int64_t overflow_reruns;       /* batched queries whose bounded slot lists ran out */
+  int64_t tc_pairs;              /* (series, query) pairs bounded by the tensor-core */
+                                 /* filter                                          */
                                  /* of room and that ran again on the full workspace */
 } msi_query_stats;
 
@@ -315,6 +317,10 @@ typedef struct msi_schedule {
   int32_t batch_share;
   int32_t batch_overlap;  /* chain form: 1 launches each stage early (programmatic
                              dependent launch) so it starts as the previous ends */
+  int32_t batch_dense;    /* chain form: 1 replaces the leaf, block and series filters
+                             by the tensor-core filter (one streaming pass over the
+                             collection per pass of queries; len a multiple of 4,
+                             at most 2048) */
 } msi_schedule;
 MSI_API msi_status msi_schedule_set(msi_index* index, const msi_schedule* schedule);
 MSI_API msi_status msi_schedule_get(const msi_index* index, msi_schedule* schedule);
@@ -323,8 +329,10 @@ MSI_API msi_status msi_schedule_get(const msi_index* index, msi_schedule* schedu
  * msi_autotune -- choose the batched-query schedule of an index by measurement.
  * This call times msi_knn on `queries` (nq >= 2 of them, host or device, as msi_knn)
  * with k neighbours for every candidate schedule: the batched chain with groups of
- * {32, 64, 128} queries (at most nq) and batch shares {1, 2, 4, 8}; query slots
- * {4, 8, 12, 16, 24, 32} with grid shares {1, 2, 3, 4, 6} up to the slot count.
+ * {32, 64, 128} queries (at most nq) and batch shares {1, 2, 4, 8}; the same with the
+ * tensor-core filter (groups of one filter pass, shares {1, 4}) where len allows it;
+ * query slots {4, 8, 12, 16, 24, 32} with grid shares {1, 2, 3, 4, 6} up to the slot
+ * count.
  * Each candidate runs `reps` timed calls (0 selects 3) after three untimed ones, with
  * CUDA events on `stream` (NULL: the index's stream). The fastest schedule
  * (queries/s) stays with the index; answers are the same under every schedule. `out`
@@ -342,6 +350,7 @@ typedef struct msi_tune_result {
   int32_t batch_chain;   /* the form chosen, and its group and share (chain form) */
   int32_t batch_group;
   int32_t batch_share;
+  int32_t batch_dense;   /* the tensor-core filter chosen                        */
 } msi_tune_result;
 MSI_API msi_status msi_autotune(msi_index* index, const float* queries, int64_t nq, int32_t k, int32_t reps,
                                 msi_tune_result* out, void* stream);

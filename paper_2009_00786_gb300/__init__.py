@@ -61,7 +61,7 @@ class _QueryStats(ctypes.Structure):
         "series_refined", "seed_series", "candidates", "rechecked", "refine_launches")] + [
         ("refine_ms", ctypes.c_double), ("filter_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
         ("survivors", ctypes.c_int64), ("fine_bounded", ctypes.c_int64), ("front_fine_bounded", ctypes.c_int64),
-        ("overflow_reruns", ctypes.c_int64)]
+        ("overflow_reruns", ctypes.c_int64), ("tc_pairs", ctypes.c_int64)]
 
 
 _vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -339,12 +339,13 @@ def msi_set_timing(index, enable=True):
 class _TuneResult(ctypes.Structure):
     _fields_ = [("query_slots", ctypes.c_int32), ("grid_share", ctypes.c_int32), ("queries_per_s", ctypes.c_double),
                 ("candidates", ctypes.c_int32), ("default_queries_per_s", ctypes.c_double),
-                ("batch_chain", ctypes.c_int32), ("batch_group", ctypes.c_int32), ("batch_share", ctypes.c_int32)]
+                ("batch_chain", ctypes.c_int32), ("batch_group", ctypes.c_int32), ("batch_share", ctypes.c_int32),
+                ("batch_dense", ctypes.c_int32)]
 
 
 class _Schedule(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in ("batch_chain", "query_slots", "grid_share", "batch_group",
-                                              "batch_share", "batch_overlap")]
+                                              "batch_share", "batch_overlap", "batch_dense")]
 
 
 def msi_autotune(index, queries, k, reps=0, stream=None):
@@ -366,7 +367,8 @@ def msi_schedule_get(index):
 
 def msi_schedule_set(index, **changes):
     """msi_schedule_set: changes the named fields of the index's batched schedule
-    (batch_chain, query_slots, grid_share, batch_group, batch_share, batch_overlap)."""
+    (batch_chain, query_slots, grid_share, batch_group, batch_share, batch_overlap,
+    batch_dense)."""
     cur = msi_schedule_get(index)
     unknown = set(changes) - set(cur)
     if unknown:

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmsi.so")
-SOURCES = ["msi_api.cu", "msi_build.cu", "msi_query.cu", "msi_noalloc.cu", "msi_serve.cu", "msi_persist.cu", "msi_merge.cu"]
+SOURCES = ["msi_api.cu", "msi_build.cu", "msi_query.cu", "msi_noalloc.cu", "msi_serve.cu", "msi_persist.cu", "msi_merge.cu", "msi_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-Xptxas", "-v"]

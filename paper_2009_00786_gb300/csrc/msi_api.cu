@@ -111,6 +111,7 @@ void free_index(msi_index* ix) {
   msi::free_workspace(ix->qv);
   for (auto& qv : ix->slots) msi::free_workspace(qv);
   for (auto& qv : ix->bws) msi::free_workspace(qv);
+  msi::tc_free(ix);
   if (ix->bws_dev) cudaFree(ix->bws_dev);
   for (cudaStream_t st : ix->slot_streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : ix->slot_events) cudaEventDestroy(ev);
@@ -444,10 +445,18 @@ static msi_status knn_impl(msi_index* ix, const float* queries, int64_t nq, int3
     if (batched) {
       // run any query that overflowed a slot's bounded lists again on slot 0
       std::vector<uint32_t> ovf(cnt);
+      int tc_abort = 0;
       if ((e = cudaMemcpyAsync(ovf.data(), ix->ws_ovf, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost, s)) !=
               cudaSuccess ||
+          (ix->tc_ready && (e = cudaMemcpyAsync(&tc_abort, ix->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                               cudaSuccess) ||
           (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "query execution");
+      if (tc_abort) {  // a tensor-core filter gave up on a wait: every query of the chunk again
+        for (auto& o : ovf) o = 1u;
+        ++ix->tc_aborts;
+        if ((e = cudaMemsetAsync(ix->tc_err, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "query execution");
+      }
       for (int64_t i = 0; i < cnt; ++i) {
         if (!ovf[i]) continue;
         e = msi::query_one(ix, ix->qv, 1, qd + i * ix->len, k, id_base + i * k, d_base ? d_base + i * k : nullptr,
@@ -511,9 +520,10 @@ namespace {
 struct Sched {
   bool chain;
   int slots, share, group, bshare;
+  bool dense;
 };
 Sched get_sched(const msi_index* ix) {
-  return Sched{ix->batch_chain, ix->nslots, ix->grid_share, ix->batch_group, ix->batch_share};
+  return Sched{ix->batch_chain, ix->nslots, ix->grid_share, ix->batch_group, ix->batch_share, ix->batch_dense};
 }
 void put_sched(msi_index* ix, const Sched& c) {
   ix->batch_chain = c.chain;
@@ -521,6 +531,7 @@ void put_sched(msi_index* ix, const Sched& c) {
   ix->grid_share = c.share;
   ix->batch_group = c.group;
   ix->batch_share = c.bshare;
+  ix->batch_dense = c.chain && c.dense;
 }
 // Releases the slot and batch workspaces the index's schedule does not use (no call
 // may be in flight).
@@ -553,7 +564,10 @@ msi_status msi_schedule_set(msi_index* ix, const msi_schedule* sc) {
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "msi_schedule_set");
   forget_graphs(ix);  // graphs hold the previous schedule's launches
-  put_sched(ix, Sched{sc->batch_chain != 0, sc->query_slots, sc->grid_share, sc->batch_group, sc->batch_share});
+  if (sc->batch_dense && msi::tc_queries_per_pass(ix->len) == 0)
+    return fail(MSI_EINVAL, "the tensor-core filter needs len a multiple of 4 and at most 2048");
+  put_sched(ix, Sched{sc->batch_chain != 0, sc->query_slots, sc->grid_share, sc->batch_group, sc->batch_share,
+                      sc->batch_dense != 0});
   ix->batch_pdl = sc->batch_overlap != 0;
   release_unused(ix);
   return MSI_OK;
@@ -568,6 +582,7 @@ msi_status msi_schedule_get(const msi_index* ix, msi_schedule* sc) {
   sc->batch_group = ix->batch_group;
   sc->batch_share = ix->batch_share;
   sc->batch_overlap = ix->batch_pdl ? 1 : 0;
+  sc->batch_dense = ix->batch_dense ? 1 : 0;
   return MSI_OK;
 }
 
@@ -595,22 +610,23 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
   int count = 0;
   // the candidates: the index's own schedule first, then the batched chain, then slots
   std::vector<Sched> cands{keep};
-  for (int g : {32, 64, 128}) {
-    const int gg = (int)std::min<int64_t>(g, nq);
-    for (int bs : {1, 2, 4, 8}) {
-      const Sched c{true, keep.slots, keep.share, gg, bs};
-      bool dup = false;
-      for (const Sched& o : cands)
-        dup |= o.chain && o.group == c.group && o.bshare == c.bshare;
-      if (!dup) cands.push_back(c);
-    }
-  }
+  auto add = [&](const Sched& c) {
+    for (const Sched& o : cands)
+      if (o.chain == c.chain && o.dense == c.dense &&
+          (c.chain ? (o.group == c.group && o.bshare == c.bshare) : (o.slots == c.slots && o.share == c.share)))
+        return;
+    cands.push_back(c);
+  };
+  for (int g : {32, 64, 128})
+    for (int bs : {1, 2, 4, 8}) add(Sched{true, keep.slots, keep.share, (int)std::min<int64_t>(g, nq), bs, false});
+  // the tensor-core filter: one pass over the collection per pass of queries, so the
+  // largest group it takes in one pass
+  const int per = msi::tc_queries_per_pass(ix->len);
+  if (per > 0)
+    for (int bs : {1, 4}) add(Sched{true, keep.slots, keep.share, (int)std::min<int64_t>(per, nq), bs, true});
   for (int sl : {4, 8, 12, 16, 24, 32})
-    for (int sh : {1, 2, 3, 4, 6}) {
-      if (sh > sl) continue;
-      const Sched c{false, sl, sh, keep.group, keep.bshare};
-      if (!(!keep.chain && keep.slots == sl && keep.share == sh)) cands.push_back(c);
-    }
+    for (int sh : {1, 2, 3, 4, 6})
+      if (sh <= sl) add(Sched{false, sl, sh, keep.group, keep.bshare, false});
   if ((e = cudaMalloc(&ids, sizeof(int64_t) * (size_t)nq * k)) != cudaSuccess ||
       (e = cudaMalloc(&dists, sizeof(float) * (size_t)nq * k)) != cudaSuccess ||
       (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
@@ -664,6 +680,7 @@ msi_status msi_autotune(msi_index* ix, const float* queries, int64_t nq, int32_t
     out->batch_chain = best_s.chain ? 1 : 0;
     out->batch_group = best_s.group;
     out->batch_share = best_s.bshare;
+    out->batch_dense = best_s.dense ? 1 : 0;
   }
   return MSI_OK;
 }
@@ -820,6 +837,7 @@ msi_status msi_query_stats_get(msi_index* ix, msi_query_stats* st, int32_t reset
   st->fine_bounded = (int64_t)c[msi::ST_FINE];
   st->front_fine_bounded = (int64_t)c[msi::ST_FINE_FRONT];
   st->overflow_reruns = ix->overflow_reruns;
+  st->tc_pairs = (int64_t)c[msi::ST_TC_PAIRS];
   if (reset) {
     if ((e = cudaMemset(ix->qv.counters, 0, sizeof(unsigned long long) * msi::ST_COUNT)) != cudaSuccess)
       return cuda_fail(e, "resetting counters");

@@ -101,7 +101,7 @@ struct QState {
 enum StatSlot {
   ST_QUERIES = 0, ST_LEAVES_TOTAL, ST_LEAVES_SURVIVED, ST_LEAVES_PROCESSED, ST_SERIES_LB,
   ST_SERIES_REFINED, ST_SEED, ST_CANDIDATES, ST_RECHECKED, ST_BAD_QUERY, ST_SURVIVORS, ST_FINE, ST_FINE_FRONT,
-  ST_COUNT
+  ST_TC_PAIRS, ST_COUNT
 };
 
 // Base pointers of one batched call. A query launched from a cached CUDA graph finds
@@ -338,10 +338,21 @@ struct msi_index {
   std::vector<msi::QueryView> bws;
   msi::QueryView* bws_dev = nullptr;
   int bws_dev_cap = 0;
+  bool bws_dirty = false;    // bws changed since bws_dev was written
   bool batch_chain = true;   // batched calls run the batched chain (false: the query slots)
   int batch_group = 128;     // most queries per batched launch
   int batch_share = 4;       // the batched kernels give each query 1/batch_share of a grid
   bool batch_pdl = true;     // stages of a batch overlap their launch with the previous tail
+  bool batch_dense = false;  // batched chain: the tensor-core filter instead of the iSAX filters
+  // tensor-core filter (msi_tc.cu), set up on first use: collection id -> leaf
+  // position, collection-order moments, an abort flag, the collection's TMA map
+  bool tc_ready = false;
+  uint32_t* iperm = nullptr;
+  float2* cstats = nullptr;
+  int* tc_err = nullptr;
+  void* tc_map = nullptr;
+  int tc_grid = 0;
+  int64_t tc_aborts = 0;
   std::vector<cudaStream_t> slot_streams;
   std::vector<cudaEvent_t> slot_events;
   cudaEvent_t fork_event = nullptr;
@@ -438,6 +449,13 @@ cudaError_t grids_setup(msi_index* ix);
 // (count <= batch_group), each flagging in ovf[i] whether its bounded lists overflowed.
 cudaError_t batch_setup(msi_index* ix);
 void batch_release(msi_index* ix, int keep);
+// Tensor-core filter (msi_tc.cu): queries per pass for series of `len` points (0: not
+// available), one-time set-up, release, and one pass over the collection for queries
+// q0 .. q0+nq-1 of a batch (nq <= the pass size).
+int tc_queries_per_pass(int len);
+cudaError_t tc_setup(msi_index* ix);
+void tc_free(msi_index* ix);
+cudaError_t tc_filter(msi_index* ix, const QueryView* qvs_dev, int q0, int nq, cudaStream_t s);
 // ev_a / ev_m / ev_b, when given, bracket the series filter and the row kernel.
 cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, int qbase, uint32_t* ovf,
                         cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b);

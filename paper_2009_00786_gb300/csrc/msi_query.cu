@@ -2386,6 +2386,7 @@ static void batch_capacities(const msi_index* ix, uint32_t* cand_cap, uint32_t* 
 cudaError_t batch_setup(msi_index* ix) {
   cudaError_t e;
   if ((e = refine_config(ix)) != cudaSuccess) return e;
+  if (ix->batch_dense && !ix->tc_ready && (e = tc_setup(ix)) != cudaSuccess) return e;
   const int G = std::max(1, ix->batch_group);
   if ((int)ix->bws.size() < G) {
     uint32_t cc, sc, ic;
@@ -2398,6 +2399,7 @@ cudaError_t batch_setup(msi_index* ix) {
       }
       qv.counters = ix->qv.counters;
       ix->bws.push_back(qv);
+      ix->bws_dirty = true;
     }
   }
   if (ix->bws_dev_cap < (int)ix->bws.size()) {
@@ -2406,9 +2408,15 @@ cudaError_t batch_setup(msi_index* ix) {
     ix->bws_dev_cap = 0;
     if ((e = cudaMalloc(&ix->bws_dev, sizeof(QueryView) * ix->bws.size())) != cudaSuccess) return e;
     ix->bws_dev_cap = (int)ix->bws.size();
+    ix->bws_dirty = true;
+  }
+  // the device views must name the workspaces that exist now (every view is rewritten
+  // whenever one was allocated or freed)
+  if (ix->bws_dirty) {
     if ((e = cudaMemcpy(ix->bws_dev, ix->bws.data(), sizeof(QueryView) * ix->bws.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
       return e;
+    ix->bws_dirty = false;
   }
   return cudaSuccess;
 }
@@ -2421,6 +2429,7 @@ void batch_release(msi_index* ix, int keep) {
     free_workspace(ix->bws.back());
     ix->device_bytes -= workspace_bytes(ix, cc, sc, ic);
     ix->bws.pop_back();
+    ix->bws_dirty = true;
   }
 }
 
@@ -2428,6 +2437,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
                         cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_m, cudaEvent_t ev_b) {
   cudaError_t e;
   if (count < 1 || count > (int)ix->bws.size() || count > 65535) return cudaErrorInvalidValue;
+  if (ix->bws_dirty) return cudaErrorNotReady;  // batch_setup has not written the views
   const bool pdl = ix->batch_pdl;
   const int share = std::max(1, ix->batch_share);
   const int series_grid = std::max(1, ix->grid_series / share);
@@ -2445,6 +2455,34 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   const unsigned B = (unsigned)count;
   const size_t qbytes = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
+  if (ix->batch_dense) {
+    // the tensor-core filter in place of the leaf, block and series filters: the seed
+    // leaf gives each query its first k-th best, one pass over the collection per
+    // tc_queries_per_pass queries bounds every (series, query) pair, the row kernel
+    // computes the survivors' distances
+    if (!ix->tc_ready) return cudaErrorNotReady;  // batch_setup prepares it
+    a.np = 0;  // no series filter: its per-warp counters are not read
+    MSI_LAUNCH(qb_views, (B + 127) / 128, 128, 0, s, ix->bws_dev, a, count);
+    MSI_LAUNCH(qb_prep, dim3(1, B), kThreads, qbytes, s, v, a);
+    const int64_t seed_max = std::max<int64_t>(ix->cap, k);
+    const int64_t seed_per_block = (k == 1 && ix->wf) ? 8 * kSeedGroup : 8;
+    MSI_LAUNCH(qb_seed, dim3((unsigned)std::min<int64_t>((seed_max + seed_per_block - 1) / seed_per_block, 1024), B),
+               kThreads, qbytes, s, v, a);
+    if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);
+    const int per = tc_queries_per_pass(ix->len);
+    int passes = 0;
+    if (ev_a) cudaEventRecord(ev_a, s);
+    for (int p0 = 0; p0 < count; p0 += per, ++passes)
+      if ((e = tc_filter(ix, ix->bws_dev, p0, std::min(per, count - p0), s)) != cudaSuccess) return e;
+    if (ev_m) cudaEventRecord(ev_m, s);
+    const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
+    if (k == 1) MSI_LAUNCH(qb_refine_rows<true>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
+    else MSI_LAUNCH(qb_refine_rows<false>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
+    if (ev_b) cudaEventRecord(ev_b, s);
+    MSI_LAUNCH(qb_finalize, dim3(1, B), 1024, 0, s, v, a);
+    ix->kernel_launches += 6 + passes + (k > 1 ? 1 : 0);
+    return cudaGetLastError();
+  }
   MSI_LAUNCH(qb_views, (B + 127) / 128, 128, 0, s, ix->bws_dev, a, count);
   MSI_LAUNCH(qb_prep, dim3(1, B), kThreads, qbytes, s, v, a);
   const int64_t seed_max = std::max<int64_t>(ix->cap, k);

@@ -321,6 +321,8 @@ typedef struct msi_schedule {
                              by the tensor-core filter (one streaming pass over the
                              collection per pass of queries; len a multiple of 4,
                              at most 2048) */
+  int32_t batch_order;    /* chain form: 1 refines the series filter's survivors in
+                             ascending lower-bound order (a bucket sort per query) */
 } msi_schedule;
 MSI_API msi_status msi_schedule_set(msi_index* index, const msi_schedule* schedule);
 MSI_API msi_status msi_schedule_get(const msi_index* index, msi_schedule* schedule);

@@ -345,7 +345,7 @@ class _TuneResult(ctypes.Structure):
 
 class _Schedule(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int32) for f in ("batch_chain", "query_slots", "grid_share", "batch_group",
-                                              "batch_share", "batch_overlap", "batch_dense")]
+                                              "batch_share", "batch_overlap", "batch_dense", "batch_order")]
 
 
 def msi_autotune(index, queries, k, reps=0, stream=None):
@@ -368,7 +368,7 @@ def msi_schedule_get(index):
 def msi_schedule_set(index, **changes):
     """msi_schedule_set: changes the named fields of the index's batched schedule
     (batch_chain, query_slots, grid_share, batch_group, batch_share, batch_overlap,
-    batch_dense)."""
+    batch_dense, batch_order)."""
     cur = msi_schedule_get(index)
     unknown = set(changes) - set(cur)
     if unknown:

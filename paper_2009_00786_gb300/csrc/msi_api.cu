@@ -569,6 +569,7 @@ msi_status msi_schedule_set(msi_index* ix, const msi_schedule* sc) {
   put_sched(ix, Sched{sc->batch_chain != 0, sc->query_slots, sc->grid_share, sc->batch_group, sc->batch_share,
                       sc->batch_dense != 0});
   ix->batch_pdl = sc->batch_overlap != 0;
+  ix->batch_order = sc->batch_order != 0;
   release_unused(ix);
   return MSI_OK;
 }
@@ -583,6 +584,7 @@ msi_status msi_schedule_get(const msi_index* ix, msi_schedule* sc) {
   sc->batch_share = ix->batch_share;
   sc->batch_overlap = ix->batch_pdl ? 1 : 0;
   sc->batch_dense = ix->batch_dense ? 1 : 0;
+  sc->batch_order = ix->batch_order ? 1 : 0;
   return MSI_OK;
 }
 

@@ -95,6 +95,7 @@ struct QState {
   unsigned int fine_front;      // front-leaf rows bounded by the fine PAA
   unsigned int seed_done;       // seed rows whose distance was computed
   int32_t flag;                 // 1 constant query, -1 non-finite query
+  unsigned int ord_count;       // survivors in bound order (surv2), when ordered
 };
 
 // Device-wide work counters (u64), in msi_query_stats field order.
@@ -123,6 +124,8 @@ struct QueryView {
   float* leaf_lb2;              // [L]
   uint4* items;                 // [n / kItem + 2L]: {first pos, end pos, leaf bound^2 bits, leaf}
   uint2* surv;                  // [n]: {leaf-order position, bound^2 bits} of filter survivors
+  uint2* surv2;                 // [surv_cap]: the same in ascending bound buckets (batch workspaces)
+  const uint2* rsurv;           // the list the row kernel reads: surv2 when ordered, else null (surv)
   uint2* blks;                  // [8 (n / kItem + 2L)]: {block index, lo | hi << 8} of surviving blocks
   unsigned long long* blockmin; // [L / 256 + 2]: per leaf-filter block, min (bound^2 bits << 32 | leaf)
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
@@ -344,6 +347,7 @@ struct msi_index {
   int batch_share = 4;       // the batched kernels give each query 1/batch_share of a grid
   bool batch_pdl = true;     // stages of a batch overlap their launch with the previous tail
   bool batch_dense = false;  // batched chain: the tensor-core filter instead of the iSAX filters
+  bool batch_order = false;  // batched chain: survivors refined in ascending bound order
   // tensor-core filter (msi_tc.cu), set up on first use: collection id -> leaf
   // position, collection-order moments, an abort flag, the collection's TMA map
   bool tc_ready = false;

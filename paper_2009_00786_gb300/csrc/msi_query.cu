@@ -1115,7 +1115,8 @@ __device__ __forceinline__ void q_refine_rows_body(const IndexView& ix, const Qu
   QState* st = qv.st;
   volatile unsigned int* thr_v = &st->thr_bits;
   // a query whose lists overflowed is run again with room for all n: skip it here
-  const uint32_t nsurv = st->overflow ? 0u : min(st->surv_count, qv.surv_cap);
+  const uint2* surv = qv.rsurv ? qv.rsurv : qv.surv;
+  const uint32_t nsurv = st->overflow ? 0u : (qv.rsurv ? st->ord_count : min(st->surv_count, qv.surv_cap));
   const int k = qv.k;
   const unsigned lt = (1u << lane) - 1u;
   unsigned mine = 0x7f800000u;
@@ -1131,12 +1132,12 @@ __device__ __forceinline__ void q_refine_rows_body(const IndexView& ix, const Qu
   uint32_t id_b = 0;
   float2 ms_b = make_float2(0.f, 0.f);
   const uint32_t g0 = gw * kRows;
-  if (lane < kRows && g0 + lane < nsurv) sv_b = qv.surv[g0 + lane];
+  if (lane < kRows && g0 + lane < nsurv) sv_b = surv[g0 + lane];
   if (lane < kRows && g0 + lane < nsurv) {
     id_b = __ldg(ix.perm + sv_b.x);
     if (!ix.data_is_z) ms_b = __ldg(ix.stats + sv_b.x);
   }
-  if (lane < kRows && g0 + step + lane < nsurv) sv_a = qv.surv[g0 + step + lane];
+  if (lane < kRows && g0 + step + lane < nsurv) sv_a = surv[g0 + step + lane];
   for (uint32_t g = g0; g < nsurv; g += step) {
     const uint2 sv = sv_b;
     const uint32_t myid_cur = id_b;
@@ -1146,7 +1147,7 @@ __device__ __forceinline__ void q_refine_rows_body(const IndexView& ix, const Qu
       if (!ix.data_is_z) ms_b = __ldg(ix.stats + sv_a.x);
     }
     sv_b = sv_a;
-    if (lane < kRows && g + 2 * step + lane < nsurv) sv_a = qv.surv[g + 2 * step + lane];
+    if (lane < kRows && g + 2 * step + lane < nsurv) sv_a = surv[g + 2 * step + lane];
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
     const float bound2 = lb_bound2(thr, qv.eps, qv.tau);
     const uint32_t myp = sv.x;
@@ -1527,6 +1528,7 @@ q_finalize(IndexView ix, QueryView qv, int64_t* __restrict__ ids_out, float* __r
 // counters, and the answers are those of the same queries run one at a time.
 struct BatchArgs {
   const QueryView* __restrict__ qvs;  // [batch] device array: one workspace per query
+  int order;                          // 1: the row kernel reads the bound-ordered survivors
   const CallDesc* call;   // queries and outputs of the call
   uint32_t* ovf;          // [batch] per-query overflow flags
   int qbase;              // index of the batch's first query in the call
@@ -1551,6 +1553,62 @@ __global__ void qb_views(QueryView* qvs, BatchArgs a, int count) {
   qv.npartials = a.np;
   qv.npartials_rows = a.npr;
   qv.window = -1;
+  qv.rsurv = a.order ? qv.surv2 : nullptr;
+}
+
+// The priority order of ProcessQueue (Algorithm 8: DeleteMin takes the lowest bound
+// first), for the survivors of the series filter: one block per query counts the
+// survivors whose bound still passes the current BSF in 256 equal buckets of
+// [0, bound), then scatters them bucket by bucket into surv2, so the row kernel's
+// warps, which take survivors from the front of the list, refine the lowest bounds
+// first and tighten the BSF before the higher ones are read. (Within a bucket the
+// order is that of arrival.)
+__global__ void __launch_bounds__(1024) qb_order(BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  QState* st = qv.st;
+  __shared__ uint32_t hist[256], base[256];
+  if (st->overflow) return;  // the query runs again alone
+  const uint32_t m = min(st->surv_count, qv.surv_cap);
+  const float bound2 = lb_bound2(st->thr_bits, qv.eps, qv.tau);
+  // the bucket of a bound: [0, bound2) in 256 equal parts (all in one bucket while the
+  // BSF is still unknown)
+  const float scale = bound2 < INFINITY && bound2 > 0.0f ? __fdiv_rn(256.0f, bound2) : 0.0f;
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const float lb = __uint_as_float(qv.surv[i].y);
+    if (lb <= bound2) atomicAdd(&hist[min(255, (int)__fmul_rz(lb, scale))], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the 256 counts by one warp
+    const int lane = threadIdx.x;
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = hist[8 * lane + j];
+      sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      base[8 * lane + j] = run;
+      run += v[j];
+    }
+    if (lane == 31) st->ord_count = incl;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint2 sv = qv.surv[i];
+    const float lb = __uint_as_float(sv.y);
+    if (lb <= bound2) qv.surv2[atomicAdd(&base[min(255, (int)__fmul_rz(lb, scale))], 1u)] = sv;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) qb_prep(IndexView ix, BatchArgs a) {
@@ -2117,7 +2175,7 @@ int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_ca
 
 void free_workspace(QueryView& qv) {
   void* ptrs[] = {qv.qz, qv.T, qv.T5, qv.st, qv.leaf_list, qv.leaf_lb2, qv.items, qv.blks, qv.partials,
-                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv, qv.qenv, qv.khist};
+                  qv.blockmin, qv.cand, qv.rc_d, qv.rc_id, qv.surv, qv.qenv, qv.khist, qv.surv2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   qv = QueryView{};
@@ -2393,10 +2451,12 @@ cudaError_t batch_setup(msi_index* ix) {
     batch_capacities(ix, &cc, &sc, &ic);
     while ((int)ix->bws.size() < G) {
       QueryView qv{};
-      if ((e = alloc_workspace(ix, qv, cc, sc, &ix->device_bytes, ic)) != cudaSuccess) {
+      if ((e = alloc_workspace(ix, qv, cc, sc, &ix->device_bytes, ic)) != cudaSuccess ||
+          (e = dalloc(&qv.surv2, (size_t)sc)) != cudaSuccess) {
         free_workspace(qv);
         return e;
       }
+      ix->device_bytes += (int64_t)sc * 8;
       qv.counters = ix->qv.counters;
       ix->bws.push_back(qv);
       ix->bws_dirty = true;
@@ -2427,7 +2487,7 @@ void batch_release(msi_index* ix, int keep) {
   batch_capacities(ix, &cc, &sc, &ic);
   while ((int)ix->bws.size() > keep) {
     free_workspace(ix->bws.back());
-    ix->device_bytes -= workspace_bytes(ix, cc, sc, ic);
+    ix->device_bytes -= workspace_bytes(ix, cc, sc, ic) + (int64_t)sc * 8;
     ix->bws.pop_back();
     ix->bws_dirty = true;
   }
@@ -2445,6 +2505,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   const int blocks_grid = std::max(1, ix->grid_blocks / share);
   BatchArgs a;
   a.qvs = ix->bws_dev;
+  a.order = ix->batch_order && !ix->batch_dense ? 1 : 0;
   a.call = call;
   a.ovf = ovf;
   a.qbase = qbase;
@@ -2499,13 +2560,14 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(qb_filter_series, dim3(series_grid, B), kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s,
              v, a);
+  if (ix->batch_order) MSI_LAUNCH(qb_order, dim3(1, B), 1024, 0, s, a);
   if (ev_m) cudaEventRecord(ev_m, s);
   const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   if (k == 1) MSI_LAUNCH(qb_refine_rows<true>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
   else MSI_LAUNCH(qb_refine_rows<false>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
   if (ev_b) cudaEventRecord(ev_b, s);
   MSI_LAUNCH(qb_finalize, dim3(1, B), 1024, 0, s, v, a);
-  ix->kernel_launches += 9 + (k > 1 ? 2 : 0);
+  ix->kernel_launches += 9 + (k > 1 ? 2 : 0) + (ix->batch_order ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -337,15 +337,17 @@ def test_autotune_keeps_answers_and_picks_a_measured_schedule(msi):
     ix.close()
 
 
-@pytest.mark.parametrize("k", [1, 10])
-def test_mixed_shapes_match_oracle(msi, k):
+@pytest.mark.parametrize("k,order", [(1, 0), (10, 0), (1, 1), (10, 1)])
+def test_mixed_shapes_match_oracle(msi, k, order):
     """The harder value distributions (noisy sinusoids, Laplace-step walks with spike
-    bursts), with the fresh-draw-plus-noise queries of that workload."""
+    bursts), with the fresh-draw-plus-noise queries of that workload; order = 1 refines
+    the survivors in ascending bound order (the same answers)."""
     n, length = 20000, 256
     X = datagen.mixed(4, 0, n, length)
     Z = oracle.summarise(X, 16, 256)[0]
     Q = datagen.mixed_queries(count=12)
     ix = msi.msi_build(X, segments=16, cardinality=256, leaf_capacity=128)
+    msi.msi_schedule_set(ix, batch_chain=1, batch_order=order)
     ids, d = msi.msi_knn(ix, Q, k)
     for i, q in enumerate(Q):
         oid, od2 = oracle.knn_scan(Z, oracle.znorm(q)[0], k)

@@ -325,8 +325,9 @@ def test_autotune_keeps_answers_and_picks_a_measured_schedule(msi):
     else:
         assert tr["query_slots"] in (4, 8, 12, 16, 24, 32)
         assert 1 <= tr["grid_share"] <= min(6, tr["query_slots"])
-    # the index's own schedule, 4 batched-chain and 29 slot schedules
-    assert tr["candidates"] == 34 and tr["queries_per_s"] >= tr["default_queries_per_s"] > 0
+    # the index's own schedule, 4 batched-chain schedules, 2 with the tensor-core filter
+    # and 29 slot schedules
+    assert tr["candidates"] == 36 and tr["queries_per_s"] >= tr["default_queries_per_s"] > 0
     sched = msi.msi_schedule_get(ix)
     assert sched["batch_chain"] == tr["batch_chain"]
     after = msi.msi_knn(ix, Q, k)

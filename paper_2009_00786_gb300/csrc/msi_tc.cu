@@ -496,9 +496,10 @@ cudaError_t tc_setup(msi_index* ix) {
   }
   ix->tc_map = map;
   if ((e = cudaStreamSynchronize(ix->own_stream)) != cudaSuccess) return e;
-  const int kb = (ix->len + kKb - 1) / kKb;
-  if ((e = tc_attr<16>(kb)) != cudaSuccess || (e = tc_attr<32>(kb)) != cudaSuccess ||
-      (e = tc_attr<64>(kb)) != cudaSuccess || (e = tc_attr<128>(kb)) != cudaSuccess)
+  // the shared memory of every accumulator width a pass of this length can use
+  const int kb = (ix->len + kKb - 1) / kKb, per = tc_queries_per_pass(ix->len);
+  if ((e = tc_attr<16>(kb)) != cudaSuccess || (per >= 32 && (e = tc_attr<32>(kb)) != cudaSuccess) ||
+      (per >= 64 && (e = tc_attr<64>(kb)) != cudaSuccess) || (per >= 128 && (e = tc_attr<128>(kb)) != cudaSuccess))
     return e;
   int sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device)) != cudaSuccess) return e;

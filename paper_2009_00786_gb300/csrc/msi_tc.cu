@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kTcThreads = 192;     // 6 warps: producer, MMA, 4 epilogue
 constexpr int kTileRows = 128;      // UMMA M
-constexpr int kStages = 4;          // k-blocks of the row tile in flight
+constexpr int kStages = 5;          // k-blocks of the row tile in flight
 constexpr int kKb = 32;             // points per k-block (128 bytes of fp32)
 constexpr int kStageBytes = kTileRows * 128;
 constexpr uint64_t kWaitNs = 1000000000ull;  // one second
@@ -139,6 +139,22 @@ __device__ __forceinline__ bool epilogue_any(bool pred) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 16 consecutive fp32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -172,10 +188,13 @@ struct TcArgs {
 //   10 fraction bits (2 * 2^-10 relative, plus its square) and the fp32 accumulation
 //   of len terms (len 2^-22 relative at most), with a factor of two to spare;
 //   |z|^2 is len for a non-constant series (0 for a constant one) within len 2^-14.
-// The bound's own fp32 evaluation is covered by 2^-20 terms and 1e-3 absolute.
-struct RowTerm {
-  float mu, rsig, xn, zz;
-};
+// The bound's own fp32 evaluation (a few round-to-nearest operations on values of at
+// most 4 len) is covered by the absolute term len 2^-14 + 1e-3 and the 2^-19 terms.
+// Rearranged per pair: lb = (|z|^2 - c0) + qq + a mu S - a x.q - b |q| - c |S|, with
+// a = 2 rsig, b = 2 rsig (2^-8 + 2^-19) |x|, c = 2 rsig 2^-19 |mu|, c0 = len 2^-14 + 1e-3:
+// four fused multiply-adds against per-query constants {S, |S|, |q|, bound - qq}.
+constexpr float kTf32Rel = 0.00390625f + 1.9073486e-6f;  // 2^-8 + 2^-19
+constexpr float kFp32Rel = 1.9073486e-6f;                  // 2^-19
 
 template <int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -189,7 +208,8 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
-  __shared__ float qq_s[N], S_s[N], qn_s[N], lbb_s[N];
+  __shared__ float qq_s[N], S_s[N], qn_s[N];
+  __shared__ float4 qc_s[N];  // per query: S, |S|, |q|, this tile's bound - |q|^2
   __shared__ uint32_t sa_s[N], sb_s[N];
   __shared__ QState* st_s[N];
   __shared__ uint2* surv_s[N];
@@ -338,6 +358,7 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
     const float len = (float)ix.len;
     const float eps = eps_s, tau = tau_s;
     const int k = k_s;
+    const float c0 = __fmaf_ru(len, 6.1035156e-5f, 1e-3f);
     unsigned long long pairs = 0;
     uint32_t local = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++local) {
@@ -346,7 +367,8 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (er < N) {
         QState* st = st_s[er];
-        lbb_s[er] = st ? lb_bound2(*(volatile unsigned*)&st->thr_bits, eps, tau) : -INFINITY;
+        const float lbb = st ? lb_bound2(*(volatile unsigned*)&st->thr_bits, eps, tau) : -INFINITY;
+        qc_s[er] = make_float4(S_s[er], fabsf(S_s[er]), qn_s[er], lbb - qq_s[er]);
       }
       const uint32_t acc = local & 1, aph = (local >> 1) & 1;
       const bool ready = mbar_wait(&tfull_bar[acc], aph, abort_flag);
@@ -355,51 +377,49 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
       tc_fence_after();
       const int64_t id = t * kTileRows + row;
       const bool valid = id < ix.n;
-      RowTerm rt{0.f, 0.f, 0.f, 0.f};
+      // the row's terms (a row past the end, or a query slot past nq, never passes)
+      float am = 0.f, a2 = 0.f, b = 0.f, c = 0.f, base = INFINITY;
       uint32_t pos = 0;
       if (valid) {
-        const float2 ms = ix.data_is_z ? make_float2(0.f, __ldg(&a.cstats[id]).y) : __ldg(&a.cstats[id]);
+        const float2 ms = __ldg(&a.cstats[id]);
         pos = __ldg(&a.iperm[id]);
+        base = -c0;  // |z|^2 - c0, |z|^2 = 0 for a constant series (z = 0)
         if (ms.y > 0.0f) {
-          if (ix.data_is_z) {
-            rt.mu = 0.0f;
-            rt.rsig = 1.0f;
-            rt.xn = __fmul_ru(__fsqrt_ru(len), 1.0001f);
-          } else {
-            rt.mu = ms.x;
-            rt.rsig = ms.y;
-            const float sig = __frcp_ru(ms.y);
-            rt.xn = __fmul_ru(__fsqrt_ru(__fmul_ru(len, __fmaf_ru(ms.x, ms.x, __fmul_ru(sig, sig)))), 1.0001f);
-          }
-          rt.zz = len;
+          const float mu = ix.data_is_z ? 0.0f : ms.x, rsig = ix.data_is_z ? 1.0f : ms.y;
+          const float sig = ix.data_is_z ? 1.0f : __frcp_ru(ms.y);
+          const float xn = __fmul_ru(__fsqrt_ru(__fmul_ru(len, __fmaf_ru(mu, mu, __fmul_ru(sig, sig)))), 1.0001f);
+          a2 = 2.0f * rsig;
+          am = a2 * mu;
+          b = __fmul_ru(__fmul_ru(a2, kTf32Rel), xn);
+          c = __fmul_ru(__fmul_ru(a2, kFp32Rel), fabsf(mu));
+          base = len - c0;
         }
+        pairs += (unsigned long long)a.nq;
       }
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(g * 32) << 16) + acc * N + c0, v);
+      constexpr int CH = N < 32 ? N : 32;
+      for (int c0c = 0; c0c < N; c0c += CH) {
+        float v[CH];
+        if constexpr (CH == 32) tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + acc * N + c0c, v);
+        else tmem_ld16(tmem + ((uint32_t)(g * 32) << 16) + acc * N + c0c, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int j = c0 + i;
-          if (!valid || j >= a.nq) continue;
-          const float S = S_s[j], qq = qq_s[j], qn = qn_s[j];
-          const float dq = __fmaf_rn(-rt.mu, S, v[i]);          // x.q - mu S
-          const float zq = __fmul_rn(rt.rsig, dq);
-          const float est = __fmaf_rn(-2.0f, zq, rt.zz + qq);   // |z|^2 + |q|^2 - 2 z.q
-          const float xq = __fmul_ru(rt.xn, qn);
-          const float m = __fmaf_ru(__fmul_ru(2.0f * rt.rsig, 0.00390625f + 1.9073486e-6f), xq,
-                                    __fmaf_ru(__fmul_ru(2.0f * rt.rsig, 1.9073486e-6f), fabsf(rt.mu * S),
-                                              __fmaf_ru(len, 6.1035156e-5f, 1e-3f)));
-          const float lb = fmaxf(0.0f, __fsub_rd(est, m));
-          ++pairs;
-          if (lb > lbb_s[j]) continue;
-          if (pos >= sa_s[j] && pos < sb_s[j]) continue;  // the seed leaf's rows are candidates already
+        for (int i = 0; i < CH; ++i) {
+          const int j = c0c + i;
+          const float4 q = qc_s[j];  // S, |S|, |q|, bound - qq
+          float tt = __fmaf_rn(am, q.x, base);
+          tt = __fmaf_rn(-c, q.y, tt);
+          tt = __fmaf_rn(-b, q.z, tt);
+          tt = __fmaf_rn(-a2, v[i], tt);  // lb - qq
+          if (!(tt <= q.w)) continue;
+          if (j >= a.nq || pos >= sa_s[j] && pos < sb_s[j]) continue;  // the seed leaf's rows are candidates
+          const float lb = fmaxf(0.0f, tt + qq_s[j]);
           QState* st = st_s[j];
           const uint32_t slot = atomicAdd(&st->surv_count, 1u);
           if (slot < cap_s[j]) surv_s[j][slot] = make_uint2(pos, __float_as_uint(lb));
           else st->overflow = 1u;
-          if (k == 1) {  // the pair's upper bound is a distance bound of the 1-NN
-            const float ub = __fadd_ru(est, m);
-            if (ub < lbb_s[j]) atomicMin(&st->thr_bits, __float_as_uint(ub));
+          if (k == 1) {  // the pair's upper bound, lb + 2 (margin), bounds the 1-NN distance
+            const float m = __fmaf_ru(b, q.z, __fmaf_ru(c, q.y, c0));
+            const float ub = __fmul_ru(__fadd_ru(__fadd_ru(tt, qq_s[j]), __fmul_ru(2.0f, m)), 1.0f + 2.4e-7f);
+            atomicMin(&st->thr_bits, __float_as_uint(fmaxf(ub, 0.0f)));
           }
         }
       }

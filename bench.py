@@ -91,6 +91,15 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def bf16_peak():
+    """Dense bf16 TFLOP/s, measured (burst) when the file holds it, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -507,24 +516,45 @@ def main():
     st = msi.msi_query_stats_get(index, reset=True)
     launches = max(1, st["refine_launches"])
     main_refined = st["series_refined"] - st["seed_series"]
-    # algorithmic bytes per launch:
-    # q_filter_series: 16 per SAX word bounded + 8 per block task read + 2 wf per fine
-    # PAA read (wf fp16 means) + 8 per survivor written (survivors counted by the rows
-    # they became); row refinement: 8 per survivor read + 4 len + 4 + 8 per refined
-    # series (row, perm, moments) + 8 per kept candidate
+    sched = msi.msi_schedule_get(index)
     wf = msi.msi_index_info_get(index)["fine_segments"]
-    filt_bytes = (16 * st["series_lower_bounded"] + 8 * st["blocks_examined"] + 2 * wf * st["fine_bounded"]
-                  + 8 * main_refined) / launches
-    rows_bytes = ((8 + 4 * length + 4 + 8) * main_refined + 8 * st["candidates"]) / launches
+    peak, peak_kind = peaks()
     filt_s = st["filter_ms"] / launches / 1e3
     rows_s = (st["refine_ms"] - st["filter_ms"]) / launches / 1e3
-    peak, peak_kind = peaks()
-    kernels = {
-        "q_filter_series": {"alg_bytes_per_launch": filt_bytes, "avg_launch_us": filt_s * 1e6,
-                            "achieved_gbs": filt_bytes / filt_s / 1e9 if filt_s > 0 else 0.0},
-        "q_refine_rows": {"alg_bytes_per_launch": rows_bytes, "avg_launch_us": rows_s * 1e6,
-                          "achieved_gbs": rows_bytes / rows_s / 1e9 if rows_s > 0 else 0.0},
-    }
+    # algorithmic bytes per launch (a launch covers one group of queries in the
+    # batched chain, one query in the slot form):
+    # row refinement: 8 per survivor read + 4 len + 4 + 8 per refined series (row,
+    # perm, moments) + 8 per kept candidate
+    rows_bytes = ((8 + 4 * length + 4 + 8) * main_refined + 8 * st["candidates"]) / launches
+    kernels = {"q_refine_rows": {"alg_bytes_per_launch": rows_bytes, "avg_launch_us": rows_s * 1e6,
+                                 "achieved_gbs": rows_bytes / rows_s / 1e9 if rows_s > 0 else 0.0}}
+    tensor = None
+    if sched["batch_chain"] and sched["batch_dense"]:
+        # q_tc_filter: every pass reads the whole collection (4 len per series) and its
+        # id -> position map and moments (12 per series), and writes 8 per survivor;
+        # 2 len flops per (series, query) pair on the tensor cores (TF32)
+        per = next(m for m in (128, 64, 32, 16) if -(-length // 32) * m * 128 <= 128 * 1024)
+        groups = [min(sched["batch_group"], nq - g0) for g0 in range(0, nq, sched["batch_group"])]
+        passes = sum(-(-g // per) for g in groups)
+        tc_bytes = (passes * n * (4 * length + 12) + 8 * st["survivors"]) / launches
+        tc_flops = 2.0 * length * st["tc_pairs"] / launches
+        kernels["q_tc_filter"] = {"alg_bytes_per_launch": tc_bytes, "avg_launch_us": filt_s * 1e6,
+                                  "achieved_gbs": tc_bytes / filt_s / 1e9 if filt_s > 0 else 0.0,
+                                  "passes_per_launch": passes / launches, "flops_per_launch": tc_flops}
+        # TF32 dense peak taken as half the measured bf16 peak (the nominal ratio)
+        tf32_peak = bf16_peak() / 2.0
+        tensor = {"achieved_tflops": tc_flops / filt_s / 1e12 if filt_s > 0 else 0.0, "peak_tflops": tf32_peak,
+                  "peak_kind": "measured bf16 x 0.5 (nominal TF32 / BF16 ratio)",
+                  "frac": tc_flops / filt_s / 1e12 / tf32_peak if filt_s > 0 else 0.0}
+    else:
+        # the series filter (qb_filter_series in the batched chain): 16 per SAX word
+        # bounded + 8 per block task read + 2 wf per fine PAA read (wf fp16 means) + 8 per
+        # survivor written (survivors counted by the rows they became)
+        filt_bytes = (16 * st["series_lower_bounded"] + 8 * st["blocks_examined"] + 2 * wf * st["fine_bounded"]
+                      + 8 * main_refined) / launches
+        name = "qb_filter_series" if sched["batch_chain"] else "q_filter_series"
+        kernels[name] = {"alg_bytes_per_launch": filt_bytes, "avg_launch_us": filt_s * 1e6,
+                         "achieved_gbs": filt_bytes / filt_s / 1e9 if filt_s > 0 else 0.0}
     dom = max(kernels, key=lambda kk: kernels[kk]["avg_launch_us"])
     achieved = kernels[dom]["achieved_gbs"]
     alg_bytes, refine_s = kernels[dom]["alg_bytes_per_launch"], kernels[dom]["avg_launch_us"] / 1e6
@@ -532,9 +562,10 @@ def main():
     tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.txt")
     if os.path.exists(tpath):
         import hashlib
-        src = open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", "msi_query.cu"), "rb").read()
-        h = hashlib.sha256(src).hexdigest()[:16]
         kv = dict(l.split(":", 1) for l in open(tpath).read().splitlines() if ":" in l and not l.startswith("#"))
+        src_name = kv.get("source", "msi_query.cu").strip()
+        src = open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", src_name), "rb").read()
+        h = hashlib.sha256(src).hexdigest()[:16]
         if kv.get("source_sha256_16", "").strip() == h:
             # a capture on a smaller collection, scaled to this launch by its units
             # (the algorithmic bytes) when the file gives the ratio
@@ -565,7 +596,8 @@ def main():
         "gpu_launches": timed_launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6},
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6,
+                     **({"tensor": tensor} if tensor else {})},
         "refine_kernels": kernels,
         # every kernel of the chain together, over the timed batched steps: leaves (40 B
         # each), block envelopes and tasks (40 B per block bounded), SAX words (16 B),

@@ -18,8 +18,10 @@
 //   warp 1      TMEM allocation and the MMA issuer (one thread): per tile, len / 8
 //               tcgen05.mma.kind::tf32 instructions (M = 128 series, N = the queries,
 //               K = 8) into one of two TMEM accumulators;
-//   warps 2-5   epilogue: each thread owns one series (TMEM lane), reads its row of
-//               dot products with tcgen05.ld, forms the bounds and appends survivors.
+//   warps 2-17  epilogue: each thread owns one series (TMEM lane) and a quarter of the
+//               queries (columns), reads those dot products with tcgen05.ld, forms the
+//               bounds and appends survivors; four warps per scheduler hide the
+//               latency of each warp's dependent arithmetic.
 // The queries (z-normalised, fp32, zero padded) stay in shared memory for the whole
 // kernel in the same swizzled layout. Every wait is bounded: a wait that runs out
 // (about a second) raises the CTA's abort flag, every role leaves its loop, copies
@@ -37,7 +39,9 @@
 namespace msi {
 namespace {
 
-constexpr int kTcThreads = 192;     // 6 warps: producer, MMA, 4 epilogue
+constexpr int kEpiWarps = 16;       // 4 per TMEM lane quarter, each a quarter of the columns
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTcThreads = 64 + kEpiThreads;  // producer, MMA, epilogue
 constexpr int kTileRows = 128;      // UMMA M
 constexpr int kStages = 5;          // k-blocks of the row tile in flight
 constexpr int kKb = 32;             // points per k-block (128 bytes of fp32)
@@ -122,22 +126,42 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-// Barrier 1 over the 128 epilogue threads, returning whether any of them passed
+// Barrier 1 over the epilogue threads, returning whether any of them passed
 // `pred` (so that all four warps take the same decision).
 __device__ __forceinline__ bool epilogue_any(bool pred) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)pred)
+      : "r"((uint32_t)pred), "n"(kEpiThreads)
       : "memory");
   return r != 0;
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 4 / 8 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // 32 consecutive fp32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -272,7 +296,7 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4 * 32);
+      mbar_init(&tempty_bar[b], kEpiThreads);
     }
     mbar_init(&done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -352,19 +376,22 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
     }
   } else {
     // ---------------------------------------------------------- epilogue
-    const int g = warp & 3;  // TMEM lanes 32 g .. 32 g + 31
-    const int er = tid - 64; // 0..127: epilogue thread index
+    const int g = warp & 3;            // TMEM lanes 32 g .. 32 g + 31 (the warp's quarter)
+    constexpr int CW = N / 4;          // columns (queries) per epilogue warp
+    const int col0 = ((warp - 2) >> 2) * CW;
+    const int er = tid - 64;           // 0 .. kEpiThreads - 1: epilogue thread index
     const int row = g * 32 + lane;
     const float len = (float)ix.len;
     const float eps = eps_s, tau = tau_s;
     const int k = k_s;
     const float c0 = __fmaf_ru(len, 6.1035156e-5f, 1e-3f);
+    const int my_q = max(0, min(a.nq, col0 + CW) - col0);  // real queries among this thread's columns
     unsigned long long pairs = 0;
     uint32_t local = 0;
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++local) {
       // this tile's pruning bounds, from each query's current k-th best (the barrier
       // first: every thread is done with the previous tile's)
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
       if (er < N) {
         QState* st = st_s[er];
         const float lbb = st ? lb_bound2(*(volatile unsigned*)&st->thr_bits, eps, tau) : -INFINITY;
@@ -372,12 +399,12 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
       }
       const uint32_t acc = local & 1, aph = (local >> 1) & 1;
       const bool ready = mbar_wait(&tfull_bar[acc], aph, abort_flag);
-      // one decision for all four warps (and the bounds above become visible)
+      // one decision for all epilogue warps (and the bounds above become visible)
       if (epilogue_any(!ready)) break;
       tc_fence_after();
       const int64_t id = t * kTileRows + row;
       const bool valid = id < ix.n;
-      // the row's terms (a row past the end, or a query slot past nq, never passes)
+      // the row's terms (a row past the end never passes)
       float am = 0.f, a2 = 0.f, b = 0.f, c = 0.f, base = INFINITY;
       uint32_t pos = 0;
       if (valid) {
@@ -394,37 +421,49 @@ q_tc_filter(const __grid_constant__ CUtensorMap tmap, IndexView ix, TcArgs a) {
           c = __fmul_ru(__fmul_ru(a2, kFp32Rel), fabsf(mu));
           base = len - c0;
         }
-        pairs += (unsigned long long)a.nq;
+        pairs += (unsigned long long)my_q;
       }
-      constexpr int CH = N < 32 ? N : 32;
-      for (int c0c = 0; c0c < N; c0c += CH) {
-        float v[CH];
-        if constexpr (CH == 32) tmem_ld32(tmem + ((uint32_t)(g * 32) << 16) + acc * N + c0c, v);
-        else tmem_ld16(tmem + ((uint32_t)(g * 32) << 16) + acc * N + c0c, v);
+      float v[CW];
+      const uint32_t taddr = tmem + ((uint32_t)(g * 32) << 16) + acc * N + col0;
+      if constexpr (CW == 32) tmem_ld32(taddr, v);
+      else if constexpr (CW == 16) tmem_ld16(taddr, v);
+      else if constexpr (CW == 8) tmem_ld8(taddr, v);
+      else tmem_ld4(taddr, v);
+      // the pairs whose bound passes, as a bit mask (no branch per pair); slots past
+      // nq carry a bound of -inf and never pass
+      uint32_t keep = 0;
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const int j = c0c + i;
-          const float4 q = qc_s[j];  // S, |S|, |q|, bound - qq
-          float tt = __fmaf_rn(am, q.x, base);
-          tt = __fmaf_rn(-c, q.y, tt);
-          tt = __fmaf_rn(-b, q.z, tt);
-          tt = __fmaf_rn(-a2, v[i], tt);  // lb - qq
-          if (!(tt <= q.w)) continue;
-          if (j >= a.nq || pos >= sa_s[j] && pos < sb_s[j]) continue;  // the seed leaf's rows are candidates
-          const float lb = fmaxf(0.0f, tt + qq_s[j]);
+      for (int i = 0; i < CW; ++i) {
+        const float4 q = qc_s[col0 + i];  // S, |S|, |q|, bound - qq
+        float tt = __fmaf_rn(am, q.x, base);
+        tt = __fmaf_rn(-c, q.y, tt);
+        tt = __fmaf_rn(-b, q.z, tt);
+        tt = __fmaf_rn(-a2, v[i], tt);  // lb - qq
+        keep |= (tt <= q.w ? 1u : 0u) << i;
+        v[i] = tt;
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty_bar[acc]);  // the accumulator is free: the values are in registers
+      // the rare survivors (one warp-wide test; the loop indexes v statically)
+      if (__any_sync(kFull, keep != 0)) {
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+          const int j = col0 + i;
+          if (!((keep >> i) & 1u) || (pos >= sa_s[j] && pos < sb_s[j])) continue;  // seed rows: candidates already
+          const float lbq = v[i] + qq_s[j];
+          const float lb = fmaxf(0.0f, lbq);
           QState* st = st_s[j];
           const uint32_t slot = atomicAdd(&st->surv_count, 1u);
           if (slot < cap_s[j]) surv_s[j][slot] = make_uint2(pos, __float_as_uint(lb));
           else st->overflow = 1u;
           if (k == 1) {  // the pair's upper bound, lb + 2 (margin), bounds the 1-NN distance
+            const float4 q = qc_s[j];
             const float m = __fmaf_ru(b, q.z, __fmaf_ru(c, q.y, c0));
-            const float ub = __fmul_ru(__fadd_ru(__fadd_ru(tt, qq_s[j]), __fmul_ru(2.0f, m)), 1.0f + 2.4e-7f);
+            const float ub = __fmul_ru(__fadd_ru(lbq, __fmul_ru(2.0f, m)), 1.0f + 2.4e-7f);
             atomicMin(&st->thr_bits, __float_as_uint(fmaxf(ub, 0.0f)));
           }
         }
       }
-      tc_fence_before();
-      mbar_arrive(&tempty_bar[acc]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);

@@ -62,6 +62,10 @@ def parse():
                    help="concurrent query slots of the index (0: the autotuner's choice, default schedule 16)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default batched schedule (the batched chain, groups of 128, share 4)")
+    p.add_argument("--schedule", default="auto", choices=["auto", "chain", "dense", "slots"],
+                   help="batched form: auto (the autotuner's choice), the batched chain with the iSAX filters, "
+                        "the batched chain with the tensor-core filter, or query slots (no autotuning)")
+    p.add_argument("--tune-reps", type=int, default=10, help="timed calls per schedule candidate of the autotuner")
     p.add_argument("--slot-capacity", type=int, default=0,
                    help="entries of each bounded query slot's candidate and survivor lists (0: the defaults)")
     p.add_argument("--workload", default="walks", choices=["walks", "mixed"],
@@ -426,13 +430,16 @@ def main():
     else:
         Qt = torch.from_numpy(datagen.paper_queries(n, length, count=nq, data_seed=0, fresh_seed=7,
                                                     pick_seed=8)).to(dev) if first_id == 0 else Q
-    if args.query_slots:
+    if args.query_slots or args.schedule == "slots":
         msi.msi_schedule_set(index, batch_chain=0)
+    elif args.schedule in ("chain", "dense"):
+        msi.msi_schedule_set(index, batch_chain=1, batch_group=min(128, nq), batch_share=4,
+                             batch_dense=1 if args.schedule == "dense" else 0)
     schedule = dict(msi.msi_schedule_get(index), autotuned=False)
-    if not args.no_autotune and not args.query_slots:
-        tr = msi.msi_autotune(index, Qt, k, stream=stream)
+    if not args.no_autotune and not args.query_slots and args.schedule == "auto":
+        tr = msi.msi_autotune(index, Qt, k, reps=args.tune_reps, stream=stream)
         schedule = {"batch_chain": tr["batch_chain"], "batch_group": tr["batch_group"],
-                    "batch_share": tr["batch_share"], "query_slots": tr["query_slots"],
+                    "batch_share": tr["batch_share"], "batch_dense": tr["batch_dense"], "query_slots": tr["query_slots"],
                     "grid_share": tr["grid_share"], "autotuned": True,
                     "candidates": tr["candidates"], "tuned_qps": tr["queries_per_s"],
                     "untuned_schedule_qps": tr["default_queries_per_s"],

@@ -59,6 +59,10 @@ struct IndexView {
 };
 
 constexpr int kMaxFine = 64;
+// The coarse bound of the series filter reads each symbol's first kCoarseBits bits:
+// a table of kCoarse entries per segment.
+constexpr int kCoarseBits = 5;
+constexpr int kCoarse = 1 << kCoarseBits;
 // Segments of the fine PAA: the largest of 64, 32, 16, 8 that divides len into
 // segments of a power-of-two length and exceeds the iSAX word's w; 0 when none does.
 __host__ __device__ inline int fine_segments(int len, int w) {
@@ -118,7 +122,7 @@ struct CallDesc {
 struct QueryView {
   float* qz;                    // [len]
   float* T;                     // [w][card] squared per-segment gap, query PAA to each symbol
-  float* T5;                    // [w][32] the same to each 5-bit symbol prefix (coarse regions)
+  float* T5;                    // [w][kCoarse] the same to each kCoarseBits-bit symbol prefix (coarse regions)
   QState* st;
   uint32_t* leaf_list;          // [L]
   float* leaf_lb2;              // [L]

@@ -23,12 +23,12 @@
 namespace {
 
 // Layout: query state (QState) | device counters | query z [MSI_MAX_LEN] |
-// T [MSI_MAX_SEGMENTS * MSI_MAX_CARDINALITY] | T5 [MSI_MAX_SEGMENTS * 32].
+// T [MSI_MAX_SEGMENTS * MSI_MAX_CARDINALITY] | T5 [MSI_MAX_SEGMENTS * kCoarse].
 constexpr size_t kStateBytes = 1024;
 constexpr size_t kCounterBytes = 256;
 constexpr size_t kQzBytes = sizeof(float) * MSI_MAX_LEN;
 constexpr size_t kTBytes = sizeof(float) * MSI_MAX_SEGMENTS * MSI_MAX_CARDINALITY;
-constexpr size_t kT5Bytes = sizeof(float) * MSI_MAX_SEGMENTS * 32;
+constexpr size_t kT5Bytes = sizeof(float) * MSI_MAX_SEGMENTS * msi::kCoarse;
 constexpr size_t kScratchBytes = kStateBytes + kCounterBytes + kQzBytes + kTBytes + kT5Bytes;  // 35,072 bytes
 static_assert(sizeof(msi::QState) <= kStateBytes, "query state does not fit its scratch slot");
 static_assert(sizeof(unsigned long long) * msi::ST_COUNT <= kCounterBytes, "counters do not fit");

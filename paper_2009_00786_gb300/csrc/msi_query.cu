@@ -356,9 +356,9 @@ __device__ __forceinline__ void q_prep_body(const IndexView& ix, const float* __
   }
   // coarse table: gap to the union of the regions sharing a 5-bit symbol prefix
   {
-    const int cb = ix.bits < 5 ? ix.bits : 5, cs = ix.bits - cb;
-    for (int e = tid; e < ix.w * 32; e += blockDim.x) {
-      const int j = e >> 5, c = e & 31;
+    const int cb = ix.bits < kCoarseBits ? ix.bits : kCoarseBits, cs = ix.bits - cb;
+    for (int e = tid; e < ix.w * kCoarse; e += blockDim.x) {
+      const int j = e >> kCoarseBits, c = e & (kCoarse - 1);
       float d = 0.0f;
       if (c < (1 << cb)) {
         const float u = iv_up_s[j], l = iv_lo_s[j];
@@ -955,25 +955,36 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 // queued per warp and bounded from their full symbols (T) a whole warp at a time.
 constexpr int kQueue = 64;
 
-__device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int w, int cshift, float s) {
+// Bits [pos, pos + len) of v (one instruction).
+__device__ __forceinline__ uint32_t bits_of(uint32_t v, uint32_t pos, uint32_t len) {
+  uint32_t r;
+  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(pos), "r"(len));
+  return r;
+}
+
+// Coarse bound from the symbols' top bits: byte j of the word from bit 8 j, shifted
+// right by cshift (cpos[b] = 8 b + cshift, clen = 8 - cshift, both fixed per launch).
+__device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int w, uint4 cpos, uint32_t clen,
+                                                 float s) {
   const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
+  const uint32_t pos[4] = {cpos.x, cpos.y, cpos.z, cpos.w};
   float acc = 0.0f;
 #pragma unroll
   for (int j = 0; j < 16; ++j)
-    if (j < w) acc = __fadd_rn(acc, T5s[j * 32 + (((parts[j >> 2] >> (8 * (j & 3))) & 255) >> cshift)]);
+    if (j < w) acc = __fadd_rn(acc, T5s[j * kCoarse + bits_of(parts[j >> 2], pos[j & 3], clen)]);
   return __fmul_rn(acc, s);
 }
 
 __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const QueryView& qv) {
   
-  extern __shared__ __align__(16) float Ts[];  // [w][card], then T5 [w][32]
+  extern __shared__ __align__(16) float Ts[];  // [w][card], then T5 [w][kCoarse]
   float* T5s = Ts + ix.w * ix.card;
   __shared__ uint2 buf_s[kFiltWarps][64];
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(Ts, qv.T, ix.w * ix.card);
-  smem_fill(T5s, qv.T5, ix.w * 32);
+  smem_fill(T5s, qv.T5, ix.w * kCoarse);
   for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
     fup_s[j] = qv.st->fup[j];
     flo_s[j] = qv.st->flo[j];
@@ -987,7 +998,9 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   const uint32_t ntask = min(st->blk_count, qv.blks_cap);
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
-  const int cshift = ix.bits > 5 ? ix.bits - 5 : 0;
+  const int cshift = ix.bits > kCoarseBits ? ix.bits - kCoarseBits : 0;
+  const uint4 cpos = make_uint4((uint32_t)cshift, 8u + cshift, 16u + cshift, 24u + cshift);
+  const uint32_t clen = 8u - (uint32_t)cshift;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
@@ -1048,7 +1061,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
       const uint32_t p = task[u].x * 32 + lane;
       const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
-      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
+      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cpos, clen, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
       if (pass_c) {
         qw[nq + __popc(m & lt)] = wd[u];
@@ -2140,7 +2153,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   const size_t items = items_cap ? std::min<size_t>(items_cap, (size_t)full_items(ix)) : (size_t)full_items(ix);
   if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.T5, (size_t)ix->w * 32)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.T5, (size_t)ix->w * kCoarse)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.st, 1)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
@@ -2169,7 +2182,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
 // Device bytes of one query workspace (alloc_workspace).
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap) {
   const int64_t items = items_cap ? std::min<int64_t>(items_cap, full_items(ix)) : full_items(ix);
-  return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + 32) * 4 + (int64_t)ix->L * 8 +
+  return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + kCoarse) * 4 + (int64_t)ix->L * 8 +
          items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
 
@@ -2264,7 +2277,7 @@ static cudaError_t refine_config(msi_index* ix) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     if (e != cudaSuccess) return e;
     const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
-    const size_t ssmem = fsmem + sizeof(float) * (size_t)ix->w * 32;
+    const size_t ssmem = fsmem + sizeof(float) * (size_t)ix->w * kCoarse;
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, ssmem)) != cudaSuccess)
       return e;
@@ -2358,7 +2371,7 @@ static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const f
   if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);
   MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
-  MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s, v, qv);
+  MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s, v, qv);
   if (ev_m) cudaEventRecord(ev_m, s);
   if (k == 1) MSI_LAUNCH(q_refine_dtw<true>, dtw_grid, kDtwWarps * 32, dsm, s, v, qv);
   else MSI_LAUNCH(q_refine_dtw<false>, dtw_grid, kDtwWarps * 32, dsm, s, v, qv);
@@ -2412,7 +2425,7 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);  // the k-th best over seed and front
   MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
-  MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s, v, qv);
+  MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s, v, qv);
   if (ev_m) cudaEventRecord(ev_m, s);
   const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
   if (k == 1) MSI_LAUNCH(q_refine_rows<true>, rows_grid, kRowWarps * 32, rsmem, s, v, qv);
@@ -2558,7 +2571,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);
   MSI_LAUNCH(qb_filter_blocks, dim3(blocks_grid, B), kBlkThreads, fsmem, s, v, a);
   if (ev_a) cudaEventRecord(ev_a, s);
-  MSI_LAUNCH(qb_filter_series, dim3(series_grid, B), kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * 32, s,
+  MSI_LAUNCH(qb_filter_series, dim3(series_grid, B), kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s,
              v, a);
   if (ix->batch_order) MSI_LAUNCH(qb_order, dim3(1, B), 1024, 0, s, a);
   if (ev_m) cudaEventRecord(ev_m, s);

@@ -153,6 +153,165 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
   }
 }
 
+// ------------------------------------------------ summarise, two series per warp
+// The same canonical arithmetic with each half-warp on its own series: half-lane h
+// holds the points of canonical lanes h and h + 16 (parts A and B), so every point
+// is summed into the partial of its canonical lane exactly as above; the 16 lane
+// partials of each part are combined by the same pairwise tree (xor offsets 1..8
+// stay inside a half) and the last step of the 32-lane tree adds the two parts. The
+// shuffles, divisions and the key's ballots serve two series at once, and every lane
+// keeps twice the loads in flight.
+//
+// SAX symbol by a cell table: the value axis [-4, 4) in 1024 cells of 1/128; cell_lo[c]
+// is the number of thresholds at or below the left edge of cell c - 1 (one cell of room
+// for the rounding of the cell index), a lower bound of the symbol of any value whose
+// computed cell is c; exact comparisons with the next thresholds (at most a few) then
+// give the symbol: the number of thresholds at or below the value.
+constexpr int kSymCells = 1024;
+__device__ __forceinline__ int sax_symbol_cells(const float* thr_up_s, const uint8_t* cell_lo, int card, float p) {
+  const float x = fminf(fmaxf(floorf(__fmul_rn(__fadd_rn(p, 4.0f), 128.0f)), 0.0f), (float)(kSymCells - 1));
+  int sym = cell_lo[(int)x];
+  while (sym < card - 1 && thr_up_s[sym + 1] <= p) ++sym;
+  return sym;
+}
+
+// The interleaved key of the half-warp's word (lanes h < w of the half hold sym_h).
+__device__ __forceinline__ unsigned long long interleave_key_half(int sym, int w, int bits, int hl, int half) {
+  unsigned long long key = 0;
+  int used = 0;
+  for (int p = bits - 1; p >= 0 && used < 64; --p) {
+    const unsigned m = __ballot_sync(kFull, hl < w && ((sym >> p) & 1));
+    const unsigned mh = (m >> (16 * half)) & 0xffffu;
+    const unsigned rev = __brev(mh) >> (32 - w);  // segment 0 in the top bit of w
+    const int take = (64 - used) < w ? (64 - used) : w;
+    key = (key << take) | (unsigned long long)(rev >> (w - take));
+    used += take;
+  }
+  return used < 64 ? key << (64 - used) : key;
+}
+
+// Pairwise tree over xor offsets 1 .. width / 2 inside a half-warp.
+__device__ __forceinline__ float tree_half(float v, int width) {
+  for (int off = 1; off < width && off < 16; off <<= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, off));
+  return v;
+}
+
+// NC <= 4 (len <= 512) and G <= 16 (segments of at most 64 points).
+template <int NC>
+__global__ void __launch_bounds__(kSumWarps * 32)
+summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bits, int G,
+               const float* __restrict__ thr_up_g, const uint8_t* __restrict__ cell_lo_g, SumOut o) {
+  __shared__ float thr_s[257];
+  __shared__ uint8_t cell_s[kSymCells];
+  __shared__ __align__(16) uint8_t sw_s[kSumWarps][2][16];
+  __shared__ __align__(16) __half fs_s[kSumWarps][2][kMaxFine];
+  __shared__ float paa_s[kSumWarps][2][16];
+  for (int v = threadIdx.x; v <= card; v += blockDim.x) thr_s[v] = thr_up_g[v];
+  for (int c = threadIdx.x; c < kSymCells; c += blockDim.x) cell_s[c] = cell_lo_g[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, hl = lane & 15;
+  const int len = NC * 128;
+  const int s = 4 * G;
+  const int segs_per_chunk = 128 / s;
+  const int sf = o.sf;
+  uint8_t* sw = sw_s[warp][half];
+  __half* fs = fs_s[warp][half];
+  float* paa = paa_s[warp][half];
+  for (int64_t i0 = 2 * ((int64_t)blockIdx.x * kSumWarps + warp); i0 < n; i0 += 2 * (int64_t)gridDim.x * kSumWarps) {
+    const int64_t i = i0 + half;
+    const bool valid = i < n;
+    const float4* row = reinterpret_cast<const float4*>(src + (valid ? i : i0) * len);
+    // part A: canonical lane hl, part B: canonical lane hl + 16 (float4 index 32 c + lane)
+    float4 va[NC], vb[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      va[c] = __ldcs(row + c * 32 + hl);
+      vb[c] = __ldcs(row + c * 32 + hl + 16);
+    }
+    float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      sa = __fadd_rn(sa, va[c].x); sb = __fadd_rn(sb, vb[c].x);
+      sa = __fadd_rn(sa, va[c].y); sb = __fadd_rn(sb, vb[c].y);
+      sa = __fadd_rn(sa, va[c].z); sb = __fadd_rn(sb, vb[c].z);
+      sa = __fadd_rn(sa, va[c].w); sb = __fadd_rn(sb, vb[c].w);
+    }
+    const float mu = __fdiv_rn(__fadd_rn(tree_half(sa, 16), tree_half(sb, 16)), (float)len);
+    float qa = 0.0f, qb = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float d = __fsub_rn(va[c].x, mu); qa = __fmaf_rn(d, d, qa);
+      d = __fsub_rn(vb[c].x, mu); qb = __fmaf_rn(d, d, qb);
+      d = __fsub_rn(va[c].y, mu); qa = __fmaf_rn(d, d, qa);
+      d = __fsub_rn(vb[c].y, mu); qb = __fmaf_rn(d, d, qb);
+      d = __fsub_rn(va[c].z, mu); qa = __fmaf_rn(d, d, qa);
+      d = __fsub_rn(vb[c].z, mu); qb = __fmaf_rn(d, d, qb);
+      d = __fsub_rn(va[c].w, mu); qa = __fmaf_rn(d, d, qa);
+      d = __fsub_rn(vb[c].w, mu); qb = __fmaf_rn(d, d, qb);
+    }
+    const Moments m = finish_moments(mu, __fadd_rn(tree_half(qa, 16), tree_half(qb, 16)), len);
+    if (valid && m.flag < 0 && hl == 0) atomicMin(o.first_bad, (unsigned long long)i);
+    const bool cst = m.flag != 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const float4 x = part ? vb[c] : va[c];
+        const int L = hl + 16 * part;  // canonical lane
+        float4 z;
+        z.x = cst ? 0.0f : znorm_value(x.x, m.mu, m.rsig);
+        z.y = cst ? 0.0f : znorm_value(x.y, m.mu, m.rsig);
+        z.z = cst ? 0.0f : znorm_value(x.z, m.mu, m.rsig);
+        z.w = cst ? 0.0f : znorm_value(x.w, m.mu, m.rsig);
+        if (o.z_out && valid) __stcs(reinterpret_cast<float4*>(o.z_out + i * len) + c * 32 + L, z);
+        if (o.fine) {  // this canonical lane's points are 4 (32 c + L) .. + 3
+          const int t0 = 4 * (32 * c + L);
+          if (sf == 1) {
+            fs[t0] = __float2half_rn(z.x);
+            fs[t0 + 1] = __float2half_rn(z.y);
+            fs[t0 + 2] = __float2half_rn(z.z);
+            fs[t0 + 3] = __float2half_rn(z.w);
+          } else if (sf == 2) {
+            fs[t0 / 2] = __float2half_rn(__fmul_rn(__fadd_rn(z.x, z.y), 0.5f));
+            fs[t0 / 2 + 1] = __float2half_rn(__fmul_rn(__fadd_rn(z.z, z.w), 0.5f));
+          } else {
+            float gf = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
+            gf = tree_half(gf, sf / 4);  // sf / 4 <= 16 consecutive canonical lanes, one part
+            if ((L & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(__fdiv_rn(gf, (float)sf));
+          }
+        }
+        // PAA: groups of 4 points, G consecutive canonical lanes per segment (G <= 16,
+        // so a segment lies in one part), combined by the pairwise tree
+        float g = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
+        g = tree_half(g, G);
+        if ((L & (G - 1)) == 0) {
+          const int j = c * segs_per_chunk + L / G;
+          if (j < 16) paa[j] = __fdiv_rn(g, (float)s);
+        }
+      }
+    }
+    __syncwarp();
+    int sym = 0;
+    if (hl < w) sym = sax_symbol_cells(thr_s, cell_s, card, paa[hl]);
+    if (hl < 16) sw[hl] = (uint8_t)sym;
+    __syncwarp();
+    const unsigned long long key = interleave_key_half(sym, w, bits, hl, half);
+    if (valid && hl == 0) {
+      o.stats[i] = make_float2(m.mu, m.rsig);
+      o.words[i] = *reinterpret_cast<const uint4*>(sw);
+      o.keys[i] = key;
+      o.ids[i] = (uint32_t)i;
+    }
+    if (o.fine) {
+      __syncwarp();
+      const int chunks = o.wf / 8;
+      if (valid && hl < chunks) o.fine[i * chunks + hl] = reinterpret_cast<const uint4*>(fs)[hl];
+    }
+    __syncwarp();
+  }
+}
+
 // Generic path: any length up to MSI_MAX_LEN and any segment length. The warp
 // stages the z values in shared memory and lanes j < w reduce their segment in the
 // canonical order.
@@ -689,7 +848,29 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   const int G = s_len / 4;
   const bool fast = (len % 128 == 0) && (len / 128) <= 16 && (s_len % 4 == 0) && G >= 1 && G <= 32 &&
                     (G & (G - 1)) == 0 && ((len / 128) & (len / 128 - 1)) == 0;
-  if (fast) {
+  const bool pair = fast && len / 128 <= 4 && G <= 16 && (o.sf == 0 || o.sf <= 64);
+  if (pair) {
+    // the symbol cell table: thresholds t_1..t_{card-1} at or below the left edge of
+    // the previous cell (-4 + (c - 1) / 128), counted on the host from the same table
+    std::vector<uint8_t> cells(kSymCells, 0);
+    for (int c = 1; c < kSymCells; ++c) {
+      const double edge = -4.0 + (double)(c - 1) / 128.0;
+      int cnt = 0;
+      for (int v = 1; v < ix->card; ++v) cnt += (double)ix->h_thr_up[v] <= edge ? 1 : 0;
+      cells[c] = (uint8_t)cnt;
+    }
+    uint8_t* cell_d;
+    MSI_TRY(tmp.get(&cell_d, kSymCells));
+    MSI_TRY(cudaMemcpyAsync(cell_d, cells.data(), kSymCells, cudaMemcpyHostToDevice, s));
+    MSI_TRY(cudaStreamSynchronize(s));  // the host table is freed on return
+    const int64_t pairs = (n + 1) / 2;
+    const int64_t blocks = std::min<int64_t>((pairs + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);
+    switch (len / 128) {
+      case 1: summarise_pair<1><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+      case 2: summarise_pair<2><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+      default: summarise_pair<4><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+    }
+  } else if (fast) {
     const int64_t blocks = std::min<int64_t>((n + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);
     switch (len / 128) {
       case 1: summarise_fast<1><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, o); break;

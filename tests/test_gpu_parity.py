@@ -41,6 +41,8 @@ CASES = [
     (4000, 256, 8, 16, 30),
     (1500, 60, 4, 4, 20),
     (777, 50, 5, 256, 10),
+    (3333, 512, 16, 256, 100),   # two series per warp, segments of 32 points, odd n
+    (2001, 256, 4, 64, 50),      # two series per warp, segments of 64 points
 ]
 IDS = [f"n{c[0]}-len{c[1]}-w{c[2]}-c{c[3]}-cap{c[4]}" for c in CASES]
 

@@ -362,7 +362,7 @@ summarise_generic(const float* __restrict__ src, int64_t n, int len, int w, int 
 // ------------------------------------------------------------------ radix sort
 // Stable LSD radix sort of (u64 key, u32 value), 8-bit digits. Per pass: a tile
 // histogram (upsweep), an exclusive scan of the digit-major histogram, and a stable
-// scatter that ranks keys inside a tile with warp match + per-digit warp prefixes.
+// scatter through a tile sorted in shared memory.
 constexpr int kRsThreads = 256;
 constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsThreads * kRsRounds;
@@ -383,24 +383,65 @@ rs_upsweep(const unsigned long long* __restrict__ keys, int64_t n, int shift, ui
   hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// The stable scatter: each round of 256 keys is ranked inside the tile with warp
+// match and per-digit warp prefixes; every key goes to its rank among the tile's keys
+// of equal digit in shared memory, and the tile is then written out in that order, so
+// keys of one digit leave as one contiguous run instead of one scattered store each.
+// The tile's count of digit d is the difference of consecutive scanned offsets
+// (digit-major).
+constexpr size_t kRsSmem = (size_t)kRsTile * (sizeof(unsigned long long) + sizeof(uint32_t));
 __global__ void __launch_bounds__(kRsThreads)
-rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
-           unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
-           const uint32_t* __restrict__ offs, int64_t tiles) {
+rs_scatter_local(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+                 unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                 const uint32_t* __restrict__ offs, int64_t tiles) {
   constexpr int kW = kRsThreads / 32;
-  __shared__ uint32_t run[256];
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(rs_smem);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kRsTile);
+  __shared__ uint32_t run[256], lstart[256], gstart[256];
   __shared__ uint32_t wc[kW][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  run[threadIdx.x] = offs[(int64_t)threadIdx.x * tiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  const int count = (int)((n - base) < (int64_t)kRsTile ? (n - base) : (int64_t)kRsTile);
   const unsigned lt = (1u << lane) - 1u;
+  {  // this tile's digit counts, their exclusive scan (tile-local starts), global starts
+    const int64_t idx = (int64_t)threadIdx.x * tiles + blockIdx.x;
+    const uint32_t g0 = offs[idx];
+    const uint32_t g1 = (idx + 1 < 256 * tiles) ? offs[idx + 1] : (uint32_t)n;
+    gstart[threadIdx.x] = g0;
+    const uint32_t c = g1 - g0;
+    // block exclusive scan of the 256 counts (one per thread)
+    uint32_t x = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) wc[0][warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t t = lane < kW ? wc[0][lane] : 0;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, t, off);
+        if (lane >= off) t += y;
+      }
+      if (lane < kW) wc[1][lane] = t;
+    }
+    __syncthreads();
+    const uint32_t st = (warp ? wc[1][warp - 1] : 0u) + x - c;
+    lstart[threadIdx.x] = st;
+    run[threadIdx.x] = st;
+    __syncthreads();
+  }
   for (int r = 0; r < kRsRounds; ++r) {
 #pragma unroll
     for (int q = 0; q < kW; ++q) wc[q][threadIdx.x] = 0;
     __syncthreads();
-    const int64_t idx = base + r * kRsThreads + threadIdx.x;
-    const bool valid = idx < n;
-    const unsigned long long key = valid ? kin[idx] : 0ull;
+    const int li = r * kRsThreads + threadIdx.x;
+    const bool valid = li < count;
+    const unsigned long long key = valid ? kin[base + li] : 0ull;
+    const uint32_t val = valid ? vin[base + li] : 0u;
     const int d = valid ? (int)((key >> shift) & 255) : 256;
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & lt);
@@ -418,11 +459,18 @@ rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restric
     }
     __syncthreads();
     if (valid) {
-      const uint32_t pos = wc[warp][d] + (uint32_t)rank;
-      kout[pos] = key;
-      vout[pos] = vin[idx];
+      const uint32_t pos = wc[warp][d] + (uint32_t)rank;  // tile-local sorted position
+      sk[pos] = key;
+      sv[pos] = val;
     }
     __syncthreads();
+  }
+  for (int i = threadIdx.x; i < count; i += kRsThreads) {
+    const unsigned long long key = sk[i];
+    const int d = (int)((key >> shift) & 255);
+    const uint32_t dst = gstart[d] + ((uint32_t)i - lstart[d]);
+    kout[dst] = key;
+    vout[dst] = sv[i];
   }
 }
 
@@ -905,11 +953,12 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(tmp.get(&sums, (size_t)((tiles * 256 + kScanTile - 1) / kScanTile + 1)));
   unsigned long long *ka = o.keys, *kb = keys_alt;
   uint32_t *va = o.ids, *vb = ids_alt;
+  MSI_TRY(cudaFuncSetAttribute(rs_scatter_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRsSmem));
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 8 * pass;
     rs_upsweep<<<(unsigned)tiles, kRsThreads, 0, s>>>(ka, n, shift, hist, tiles);
     MSI_TRY(exclusive_scan(hist, hist, tiles * 256, sums, s));
-    rs_scatter<<<(unsigned)tiles, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, tiles);
+    rs_scatter_local<<<(unsigned)tiles, kRsThreads, kRsSmem, s>>>(ka, va, kb, vb, n, shift, hist, tiles);
     MSI_TRY(cudaGetLastError());
     std::swap(ka, kb);
     std::swap(va, vb);

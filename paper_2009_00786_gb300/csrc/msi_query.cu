@@ -120,13 +120,19 @@ __device__ __forceinline__ float warp_sqdist(const IndexView& ix, uint32_t id, f
   return acc;
 }
 
-// Squared iSAX lower bound of one SAX word: s * sum_j T[j][sym_j].
+// Squared iSAX lower bound of one SAX word: s * sum_j T[j][sym_j]. Symbol byte b of
+// a 32-bit part becomes its byte offset in the row with one shift and one mask.
 __device__ __forceinline__ float word_lb2(uint4 wd, const float* Ts, int w, int card, float s) {
   const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
+  const char* tb = reinterpret_cast<const char*>(Ts);
   float acc = 0.0f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if (j < w) acc = __fadd_rn(acc, Ts[j * card + ((parts[j >> 2] >> (8 * (j & 3))) & 255)]);
+    if (j < w) {
+      const uint32_t p = parts[j >> 2];
+      const uint32_t off = (j & 3) == 0 ? (p << 2) & 0x3FCu : (p >> (8 * (j & 3) - 2)) & 0x3FCu;
+      acc = __fadd_rn(acc, *reinterpret_cast<const float*>(tb + (size_t)j * card * 4 + off));
+    }
   }
   return __fmul_rn(acc, s);
 }
@@ -955,23 +961,28 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 // queued per warp and bounded from their full symbols (T) a whole warp at a time.
 constexpr int kQueue = 64;
 
-// Bits [pos, pos + len) of v (one instruction).
-__device__ __forceinline__ uint32_t bits_of(uint32_t v, uint32_t pos, uint32_t len) {
-  uint32_t r;
-  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(pos), "r"(len));
-  return r;
-}
-
-// Coarse bound from the symbols' top bits: byte j of the word from bit 8 j, shifted
-// right by cshift (cpos[b] = 8 b + cshift, clen = 8 - cshift, both fixed per launch).
-__device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int w, uint4 cpos, uint32_t clen,
-                                                 float s) {
+// Coarse bound from the symbols' top kCoarseBits bits. The table entry's byte offset
+// inside segment j's row comes straight from the word: symbol byte b of a 32-bit part
+// shifted right by 8 b + cshift - 2 and masked to bits 2 .. kCoarseBits + 1 (one shift
+// and one mask per segment; cshift >= 2, i.e. symbols of at least kCoarseBits + 2
+// bits, else the plain index).
+__device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int w, int cshift, float s) {
   const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
-  const uint32_t pos[4] = {cpos.x, cpos.y, cpos.z, cpos.w};
+  const char* tb = reinterpret_cast<const char*>(T5s);
+  constexpr uint32_t kMask = (uint32_t)(kCoarse - 1) << 2;
   float acc = 0.0f;
+  if (cshift >= 2) {
+    const int sh0 = cshift - 2;
 #pragma unroll
-  for (int j = 0; j < 16; ++j)
-    if (j < w) acc = __fadd_rn(acc, T5s[j * kCoarse + bits_of(parts[j >> 2], pos[j & 3], clen)]);
+    for (int j = 0; j < 16; ++j)
+      if (j < w)
+        acc = __fadd_rn(acc, *reinterpret_cast<const float*>(tb + j * kCoarse * 4 +
+                                                              ((parts[j >> 2] >> (8 * (j & 3) + sh0)) & kMask)));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < w) acc = __fadd_rn(acc, T5s[j * kCoarse + (((parts[j >> 2] >> (8 * (j & 3))) & 255) >> cshift)]);
+  }
   return __fmul_rn(acc, s);
 }
 
@@ -999,8 +1010,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
   const int cshift = ix.bits > kCoarseBits ? ix.bits - kCoarseBits : 0;
-  const uint4 cpos = make_uint4((uint32_t)cshift, 8u + cshift, 16u + cshift, 24u + cshift);
-  const uint32_t clen = 8u - (uint32_t)cshift;
+
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
@@ -1061,7 +1071,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
       const uint32_t p = task[u].x * 32 + lane;
       const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
-      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cpos, clen, seglen) <= bound2;
+      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
       if (pass_c) {
         qw[nq + __popc(m & lt)] = wd[u];

@@ -1654,6 +1654,121 @@ __global__ void __launch_bounds__(kThreads) qb_leaf_filter(IndexView ix, BatchAr
   const QueryView& qv = batch_view(a);
   q_leaf_filter_body(ix, qv);
 }
+// The leaf filter for the whole batch, leaf-major: a thread per leaf loads its
+// envelope once, turns it into the 16 region edges, and bounds it against every query
+// of the batch from those (the one-query filter's arithmetic, operation for
+// operation); each query's survivors, work items and per-block minimum go to its own
+// workspace as in q_leaf_filter.
+constexpr int kBatchMax = 128;  // queries per leaf-major launch (the batch group cap)
+__global__ void __launch_bounds__(kThreads) qb_leaf_filter_lm(IndexView ix, BatchArgs a, int count) {
+  pdl_begin();
+  __shared__ float thr_up_s[257], thr_lo_s[257];
+  __shared__ float paa_s[kBatchMax][16];
+  __shared__ float bnd_s[kBatchMax];
+  __shared__ uint32_t sa_s[kBatchMax], sb_s[kBatchMax];
+  __shared__ unsigned long long bmin_s[kBatchMax];
+  for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
+    thr_up_s[v] = ix.thr_up[v];
+    thr_lo_s[v] = ix.thr_lo[v];
+  }
+  for (int e = threadIdx.x; e < count * 16; e += blockDim.x) {
+    const int q = e >> 4, j = e & 15;
+    paa_s[q][j] = j < ix.w ? a.qvs[q].st->qpaa[j] : 0.0f;
+  }
+  for (int q = threadIdx.x; q < count; q += blockDim.x) {
+    const QueryView& qv = a.qvs[q];
+    bnd_s[q] = lb_bound2(qv.st->thr_bits, qv.eps, qv.tau);
+    sa_s[q] = qv.st->seed_a;
+    sb_s[q] = qv.st->seed_b;
+    bmin_s[q] = ~0ull;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool have = l < ix.L;
+  float lower[16], upper[16];
+  uint32_t b = 0, e = 0, nit = 0;
+  if (have) {
+    const uint4 lo = ix.env[2 * l], hi = ix.env[2 * l + 1];
+    const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
+      lower[j] = j < ix.w ? thr_lo_s[sl] : -INFINITY;
+      upper[j] = j < ix.w ? thr_up_s[sh + 1] : INFINITY;
+    }
+    b = ix.leaf_begin[l];
+    e = ix.leaf_begin[l + 1];
+    nit = (e - 1) / kItem - b / kItem + 1;  // aligned tiles of kItem positions touched
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      lower[j] = -INFINITY;
+      upper[j] = INFINITY;
+    }
+  }
+  const float seglen = (float)ix.seglen;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int q = 0; q < count; ++q) {
+    bool keep = false;
+    float lb2 = 0.0f;
+    if (have && !(b >= sa_s[q] && e <= sb_s[q])) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j < ix.w) {
+          const float p = paa_s[q][j];
+          float d = 0.0f;
+          if (p < lower[j]) d = __fsub_rn(lower[j], p);
+          else if (p > upper[j]) d = __fsub_rn(p, upper[j]);
+          acc = __fadd_rn(acc, __fmul_rn(d, d));
+        }
+      }
+      lb2 = __fmul_rn(acc, seglen);
+      keep = lb2 <= bnd_s[q];
+    }
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (!m) continue;
+    const QueryView& qv = a.qvs[q];
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&qv.st->leaf_count, (uint32_t)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    const uint32_t mynit = keep ? nit : 0u;
+    uint32_t incl = mynit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t ibase = 0;
+    if (lane == 31) ibase = atomicAdd(&qv.st->item_count, incl);
+    ibase = __shfl_sync(kFull, ibase, 31) + incl - mynit;
+    unsigned long long mine = keep ? (((unsigned long long)__float_as_uint(lb2) << 32) | (uint32_t)l) : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, mine, o);
+      mine = other < mine ? other : mine;
+    }
+    if (lane == 0) atomicMin(&bmin_s[q], mine);
+    if (keep) {
+      const uint32_t slot = base + __popc(m & lt);
+      qv.leaf_list[slot] = (uint32_t)l;
+      qv.leaf_lb2[slot] = lb2;
+      const uint32_t t0 = b / kItem;
+      for (uint32_t j = 0; j < nit; ++j) {
+        if (ibase + j < qv.items_cap)
+          qv.items[ibase + j] = make_uint4(max(b, (t0 + j) * kItem), min(e, (t0 + j + 1) * kItem), __float_as_uint(lb2),
+                                           (uint32_t)l);
+        else
+          qv.st->overflow = 1u;
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < count; q += blockDim.x) a.qvs[q].blockmin[blockIdx.x] = bmin_s[q];
+}
+
 __global__ void __launch_bounds__(kThreads) qb_front(IndexView ix, BatchArgs a, uint32_t nblockmin) {
   pdl_begin();
   const QueryView& qv = batch_view(a);
@@ -2575,7 +2690,8 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
              kThreads, qbytes, s, v, a);
   if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 0);
   const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
-  MSI_LAUNCH(qb_leaf_filter, dim3(nlf, B), kThreads, 0, s, v, a);
+  if (count <= kBatchMax) MSI_LAUNCH(qb_leaf_filter_lm, nlf, kThreads, 0, s, v, a, count);
+  else MSI_LAUNCH(qb_leaf_filter, dim3(nlf, B), kThreads, 0, s, v, a);
   MSI_LAUNCH(qb_front, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ix->cap + 7) / 8, 256) / share), B),
              kThreads, qbytes, s, v, a, nlf);
   if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);

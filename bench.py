@@ -66,6 +66,8 @@ def parse():
                    help="batched form: auto (the autotuner's choice), the batched chain with the iSAX filters, "
                         "the batched chain with the tensor-core filter, or query slots (no autotuning)")
     p.add_argument("--tune-reps", type=int, default=10, help="timed calls per schedule candidate of the autotuner")
+    p.add_argument("--batch-order", action="store_true",
+                   help="batched chain: refine each query's survivors in ascending lower-bound order")
     p.add_argument("--slot-capacity", type=int, default=0,
                    help="entries of each bounded query slot's candidate and survivor lists (0: the defaults)")
     p.add_argument("--workload", default="walks", choices=["walks", "mixed"],
@@ -435,6 +437,8 @@ def main():
     elif args.schedule in ("chain", "dense"):
         msi.msi_schedule_set(index, batch_chain=1, batch_group=min(128, nq), batch_share=4,
                              batch_dense=1 if args.schedule == "dense" else 0)
+    if args.batch_order:
+        msi.msi_schedule_set(index, batch_order=1)
     schedule = dict(msi.msi_schedule_get(index), autotuned=False)
     if not args.no_autotune and not args.query_slots and args.schedule == "auto":
         tr = msi.msi_autotune(index, Qt, k, reps=args.tune_reps, stream=stream)

@@ -428,7 +428,7 @@ MSI_API msi_status msi_merge_topk(const int64_t* ids, const double* sqdists64, i
  *
  * It computes the same lower bounds, with the same kernels, and calls no cudaMalloc,
  * cudaFree or allocating library routine: the per-query temporaries (query state,
- * z-normalised query, per-segment gap tables, counters; 35,072 bytes) live in one
+ * z-normalised query, per-segment gap tables, counters; 38,144 bytes) live in one
  * fixed file-scope device array that every GPU loading the library holds until the
  * process exits. Every call shares that array and finds the previous call's contents
  * in it (it clears what must start at zero); calls whose work overlaps on the GPU

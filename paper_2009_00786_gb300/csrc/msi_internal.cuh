@@ -60,8 +60,10 @@ struct IndexView {
 
 constexpr int kMaxFine = 64;
 // The coarse bound of the series filter reads each symbol's first kCoarseBits bits:
-// a table of kCoarse entries per segment.
-constexpr int kCoarseBits = 5;
+// a table of kCoarse entries per segment (6 bits: two-way bank conflicts at most, and
+// at 100M x 256 the batched series filter ran 1.27 ms per 100 queries against 1.42 ms
+// with 5 bits).
+constexpr int kCoarseBits = 6;
 constexpr int kCoarse = 1 << kCoarseBits;
 // Segments of the fine PAA: the largest of 64, 32, 16, 8 that divides len into
 // segments of a power-of-two length and exceeds the iSAX word's w; 0 when none does.

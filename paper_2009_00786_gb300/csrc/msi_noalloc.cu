@@ -29,7 +29,7 @@ constexpr size_t kCounterBytes = 256;
 constexpr size_t kQzBytes = sizeof(float) * MSI_MAX_LEN;
 constexpr size_t kTBytes = sizeof(float) * MSI_MAX_SEGMENTS * MSI_MAX_CARDINALITY;
 constexpr size_t kT5Bytes = sizeof(float) * MSI_MAX_SEGMENTS * msi::kCoarse;
-constexpr size_t kScratchBytes = kStateBytes + kCounterBytes + kQzBytes + kTBytes + kT5Bytes;  // 35,072 bytes
+constexpr size_t kScratchBytes = kStateBytes + kCounterBytes + kQzBytes + kTBytes + kT5Bytes;  // 38,144 bytes
 static_assert(sizeof(msi::QState) <= kStateBytes, "query state does not fit its scratch slot");
 static_assert(sizeof(unsigned long long) * msi::ST_COUNT <= kCounterBytes, "counters do not fit");
 

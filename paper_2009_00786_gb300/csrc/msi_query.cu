@@ -360,7 +360,7 @@ __device__ __forceinline__ void q_prep_body(const IndexView& ix, const float* __
     else if (l > upper) d = __fsub_rn(l, upper);
     qv.T[e] = __fmul_rn(d, d);
   }
-  // coarse table: gap to the union of the regions sharing a 5-bit symbol prefix
+  // coarse table: gap to the union of the regions sharing a kCoarseBits-bit symbol prefix
   {
     const int cb = ix.bits < kCoarseBits ? ix.bits : kCoarseBits, cs = ix.bits - cb;
     for (int e = tid; e < ix.w * kCoarse; e += blockDim.x) {
@@ -956,8 +956,8 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 
 // One warp per surviving block: bounds every position by its SAX word and buffers
 // the survivors {position, bound}, flushed 32 at a time. kUnroll blocks are in flight
-// per warp. Each word is first bounded from its 5-bit symbol prefixes (T5: 32 entries
-// per segment, so the lookups of a warp never conflict); the words that pass are
+// per warp. Each word is first bounded from its kCoarseBits-bit symbol prefixes (T5:
+// kCoarse entries per segment, at most two lanes per bank); the words that pass are
 // queued per warp and bounded from their full symbols (T) a whole warp at a time.
 constexpr int kQueue = 64;
 

@@ -747,19 +747,10 @@ msi_status msi_index_export(const msi_index* cix, const msi_export* ex) {
     }
   }
   if (ex->thresholds) std::memcpy(ex->thresholds, ix->h_thr_up + 1, sizeof(float) * (ix->card - 1));
-  if (ex->fine && ix->fine) {
-    const size_t per = (size_t)ix->wf;
-    std::vector<uint16_t> fl((size_t)n * per);
-    if (perm.empty()) {
-      perm.resize(n);
-      if ((e = cudaMemcpy(perm.data(), ix->perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(e, "export");
-    }
-    if ((e = cudaMemcpy(fl.data(), ix->fine, sizeof(uint16_t) * fl.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
-      return cuda_fail(e, "export");
-    for (int64_t p = 0; p < n; ++p)
-      std::memcpy(ex->fine + (size_t)perm[p] * per, fl.data() + (size_t)p * per, sizeof(uint16_t) * per);
-  }
+  if (ex->fine && ix->fine &&  // kept in collection order
+      (e = cudaMemcpy(ex->fine, ix->fine, sizeof(uint16_t) * (size_t)n * ix->wf, cudaMemcpyDeviceToHost)) !=
+          cudaSuccess)
+    return cuda_fail(e, "export");
   if (ex->znorm) {
     const size_t bytes = sizeof(float) * (size_t)n * ix->len;
     if (ix->data_is_z) {

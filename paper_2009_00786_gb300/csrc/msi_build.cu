@@ -829,16 +829,6 @@ __global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, 
   stats_out[p] = stats_in[id];
 }
 
-// The fine PAA into leaf order: one thread per uint4 (chunks per series).
-__global__ void gather_fine(const uint32_t* __restrict__ perm, int64_t n, int chunks, const uint4* __restrict__ in,
-                            uint4* __restrict__ out) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n * chunks) return;
-  const int64_t p = u / chunks;
-  const int c = (int)(u - p * chunks);
-  out[u] = in[(int64_t)perm[p] * chunks + c];
-}
-
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
@@ -885,7 +875,10 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   o.fine = nullptr;
   o.wf = (ix->flags & MSI_BUILD_NO_FINE_BOUND) ? 0 : fine_segments(len, w);
   o.sf = o.wf ? len / o.wf : 0;
-  if (o.wf) MSI_TRY(tmp.get(&o.fine, (size_t)n * (o.wf / 8)));
+  if (o.wf) {  // written by the summarise kernel straight into the index (collection order)
+    MSI_TRY(dalloc(&ix->fine, (size_t)n * (o.wf / 8)));
+    o.fine = ix->fine;
+  }
   MSI_TRY(cudaMemsetAsync(o.first_bad, 0xff, sizeof(unsigned long long), s));
 
   // 1. summarise
@@ -1087,11 +1080,9 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(cudaMemcpyAsync(ix->perm, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
   gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.words, o.stats, ix->words, ix->stats);
   if (o.wf) {
-    MSI_TRY(dalloc(&ix->fine, (size_t)n * (o.wf / 8)));
     ix->wf = o.wf;
     ix->sf = o.sf;
     ix->device_bytes += (int64_t)n * 2 * o.wf;
-    gather_fine<<<grid_for(n * (o.wf / 8), 256), 256, 0, s>>>(ix->perm, n, o.wf / 8, o.fine, ix->fine);
   }
   envelopes<<<grid_for(ix->L * 32, 256), 256, 0, s>>>(ix->words, ix->leaf_begin, ix->L, ka, ix->env, ix->leaf_key);
   block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, n, ix->benv);

@@ -49,8 +49,10 @@ struct IndexView {
   const int32_t* root_child;
   const int32_t* tree_child;
   const int8_t* tree_seg;
-  // [n][wf / 8] leaf order: the series' means over wf equal segments of sf points
-  // (the fine PAA), fp16 rounded to nearest; null when wf = 0
+  // [n][wf / 8] collection order (indexed by id = perm[position]): the series' means
+  // over wf equal segments of sf points (the fine PAA), fp16 rounded to nearest; null
+  // when wf = 0. Kept in collection order: its reads are random anyway (only series
+  // whose iSAX bound passed are bounded by it), and the build then writes it once.
   const uint4* fine;
   int64_t n;
   int64_t L;

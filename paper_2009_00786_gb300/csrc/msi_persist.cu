@@ -21,7 +21,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'S', 'I', 'I', 'N', 'D', 'E', 'X'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;  // 3: the fine PAA in collection order
 constexpr size_t kStage = size_t(64) << 20;  // pinned staging buffer
 
 struct FileHeader {

@@ -226,13 +226,13 @@ __device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ 
   for (int i = 4 * n4 + threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-// Lower bound^2 of position p from the fine PAA: sf times the sum over the fine
+// Lower bound^2 of series `id` from the fine PAA: sf times the sum over the fine
 // segments of the squared gap between the series' mean and the query's interval
 // [lo_j, up_j]. The stored mean h is fp16, within e = |h| 2^-11 + 2^-25 of the fp32
 // mean (half an fp16 ulp), so each gap is taken e short; every step rounds down.
-__device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t p) {
+__device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t id) {
   const int chunks = ix.wf >> 3;
-  const uint4* src = ix.fine + (size_t)p * chunks;
+  const uint4* src = ix.fine + (size_t)id * chunks;
   float acc = 0.0f;
   for (int c = 0; c < chunks; ++c) {
     const uint4 v = __ldg(src + c);
@@ -254,11 +254,11 @@ __device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup,
   return __fmul_rd(acc, (float)ix.sf);
 }
 
-// The same bound computed by a whole warp for one position (lane l takes segments l,
+// The same bound computed by a whole warp for one series (lane l takes segments l,
 // l + 32, ...); every lane returns lane 0's sum.
-__device__ __forceinline__ float warp_fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t p) {
+__device__ __forceinline__ float warp_fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t id) {
   const int lane = threadIdx.x & 31;
-  const __half* src = reinterpret_cast<const __half*>(ix.fine) + (size_t)p * ix.wf;
+  const __half* src = reinterpret_cast<const __half*>(ix.fine) + (size_t)id * ix.wf;
   float acc = 0.0f;
   for (int j = lane; j < ix.wf; j += 32) {
     const float h = __half2float(src[j]);
@@ -558,7 +558,7 @@ __device__ __forceinline__ void q_seed_body(const IndexView& ix, const QueryView
          g0 += warps * kSeedGroup) {
       const uint32_t g = g0 + lane;
       const bool have = lane < kSeedGroup && g < nrow;
-      const float lb = have ? fine_lb2(ix, fup_s, flo_s, a + g) : INFINITY;
+      const float lb = have ? fine_lb2(ix, fup_s, flo_s, ix.perm[a + g]) : INFINITY;
       float m = lb;
       int mi = lane;
 #pragma unroll
@@ -828,7 +828,7 @@ __device__ __forceinline__ void q_front_body(const IndexView& ix, const QueryVie
       const uint32_t pos = g < total ? position(g) : 0u;
       const bool screen = g < total && !(pos >= sa && pos < sb);
       n_fine += __popc(__ballot_sync(kFull, screen));
-      const bool want = screen && fine_lb2(ix, fup_s, flo_s, pos) <= lbb;
+      const bool want = screen && fine_lb2(ix, fup_s, flo_s, ix.perm[pos]) <= lbb;
       for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
     }
   } else {
@@ -1025,7 +1025,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     bool pass = have && lb2 <= bound2;
     if (pass && ix.wf) {  // the fine PAA's bound, before the series is read
       ++n_fine;
-      lb2 = fmaxf(lb2, fine_lb2(ix, fup_s, flo_s, p));
+      lb2 = fmaxf(lb2, fine_lb2(ix, fup_s, flo_s, __ldg(ix.perm + p)));
       pass = lb2 <= bound2;
     }
     __syncwarp();
@@ -1991,7 +1991,7 @@ q_front_dtw(IndexView ix, QueryView qv, uint32_t nblockmin) {
     if (ix.wf) {  // the fine PAA's bound against the envelope, before the row is read
       const unsigned thr0 = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);
       ++n_fine;
-      if (warp_fine_lb2(ix, fup_s, flo_s, pos) > lb_bound2(thr0, qv.eps, qv.tau)) continue;
+      if (warp_fine_lb2(ix, fup_s, flo_s, ix.perm[pos]) > lb_bound2(thr0, qv.eps, qv.tau)) continue;
     }
     stage_row(ix, ix.perm[pos], ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos], ys);
     const unsigned thr = __shfl_sync(kFull, lane == 0 ? *thr_v : 0u, 0);

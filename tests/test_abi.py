@@ -128,7 +128,7 @@ def test_index_load_rejects_bad_files_before_the_device(msi, tmp_path):
     assert "not an index file" in msi.msi_last_error()
     # a consistent header (n = 1000, len 256, 16 segments, cardinality 256, 4 leaves)
     # whose arrays are missing: rejected by its size
-    hdr = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 2, 112, 1000, 256, 16, 256, 8, 16, 2000, 0, 1, 4,
+    hdr = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 3, 112, 1000, 256, 16, 256, 8, 16, 2000, 0, 1, 4,
                       (1000 + 31) // 32, 0, 0, 0, 0, 0)
     assert len(hdr) == 112
     short = tmp_path / "short.idx"
@@ -136,15 +136,17 @@ def test_index_load_rejects_bad_files_before_the_device(msi, tmp_path):
     assert lib.msi_index_load(str(short).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
     assert "truncated" in msi.msi_last_error()
     # the same header claiming a borrowed collection needs one
-    hdr_b = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 2, 112, 1000, 256, 16, 256, 8, 16, 2000, 1, 0, 4,
+    hdr_b = struct.pack("<8sIIqiiiiiiIiqqQ4Q", b"MSIINDEX", 3, 112, 1000, 256, 16, 256, 8, 16, 2000, 1, 0, 4,
                         (1000 + 31) // 32, 0, 0, 0, 0, 0)
     borrowed = tmp_path / "borrowed.idx"
     borrowed.write_bytes(hdr_b)
     assert lib.msi_index_load(str(borrowed).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
     assert "borrows" in msi.msi_last_error()
-    # files of the first format (no fine PAA section) are refused by their version
-    old = tmp_path / "v1.idx"
-    old.write_bytes(hdr[:8] + struct.pack("<I", 1) + hdr[12:] + b"\0" * 100)
-    assert lib.msi_index_load(str(old).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
-    assert "version" in msi.msi_last_error()
+    # files of earlier formats (no fine PAA section; the fine PAA in leaf order) are
+    # refused by their version
+    for v in (1, 2):
+        old = tmp_path / f"v{v}.idx"
+        old.write_bytes(hdr[:8] + struct.pack("<I", v) + hdr[12:] + b"\0" * 100)
+        assert lib.msi_index_load(str(old).encode(), None, None, ctypes.byref(out)) == msi.MSI_EINVAL
+        assert "version" in msi.msi_last_error()
     assert lib.msi_index_save(None, str(tmp_path / "x.idx").encode()) == msi.MSI_EINVAL

@@ -78,6 +78,9 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
   const int len = NC * 128;
   const int s = 4 * G;
   const int segs_per_chunk = 128 / s;
+  // len, s and sf are powers of two here: their exact reciprocals
+  const float inv_len = 1.0f / (float)len, inv_s = 1.0f / (float)s;
+  const float inv_sf = o.sf ? 1.0f / (float)o.sf : 0.0f;
   uint8_t* sw = sw_s[warp];
   __half* fs = fs_s[warp];
   const int sf = o.sf;  // fine segment length: 1, 2, or 4 Gf (Gf lanes per segment)
@@ -94,7 +97,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
       acc = __fadd_rn(acc, v[c].z);
       acc = __fadd_rn(acc, v[c].w);
     }
-    const float mu = __fdiv_rn(tree32(acc), (float)len);
+    const float mu = div_pow2(tree32(acc), inv_len);
     float acc2 = 0.0f;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -107,7 +110,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
       d = __fsub_rn(v[c].w, mu);
       acc2 = __fmaf_rn(d, d, acc2);
     }
-    const Moments m = finish_moments(mu, tree32(acc2), len);
+    const Moments m = finish_moments(mu, tree32(acc2), len, inv_len);
     if (m.flag < 0 && lane == 0) atomicMin(o.first_bad, (unsigned long long)i);
     const bool cst = m.flag != 0;
 #pragma unroll
@@ -131,14 +134,14 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
         } else {
           float gf = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
           for (int off = 1; off < sf / 4; off <<= 1) gf = __fadd_rn(gf, __shfl_xor_sync(kFull, gf, off));
-          if ((lane & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(__fdiv_rn(gf, (float)sf));
+          if ((lane & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(div_pow2(gf, inv_sf));
         }
       }
       float g = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
       for (int off = 1; off < G; off <<= 1) g = __fadd_rn(g, __shfl_xor_sync(kFull, g, off));
       if ((lane & (G - 1)) == 0) {
         const int j = c * segs_per_chunk + lane / G;
-        if (j < 16) paa_s[warp][j] = __fdiv_rn(g, (float)s);
+        if (j < 16) paa_s[warp][j] = div_pow2(g, inv_s);
       }
     }
     // one symbol search for all segments: lane j takes segment j
@@ -215,6 +218,9 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
   const int s = 4 * G;
   const int segs_per_chunk = 128 / s;
   const int sf = o.sf;
+  // len, s and sf are powers of two here: their exact reciprocals
+  const float inv_len = 1.0f / (float)len, inv_s = 1.0f / (float)s;
+  const float inv_sf = sf ? 1.0f / (float)sf : 0.0f;
   uint8_t* sw = sw_s[warp][half];
   __half* fs = fs_s[warp][half];
   float* paa = paa_s[warp][half];
@@ -237,7 +243,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
       sa = __fadd_rn(sa, va[c].z); sb = __fadd_rn(sb, vb[c].z);
       sa = __fadd_rn(sa, va[c].w); sb = __fadd_rn(sb, vb[c].w);
     }
-    const float mu = __fdiv_rn(__fadd_rn(tree_half(sa, 16), tree_half(sb, 16)), (float)len);
+    const float mu = div_pow2(__fadd_rn(tree_half(sa, 16), tree_half(sb, 16)), inv_len);
     float qa = 0.0f, qb = 0.0f;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -250,7 +256,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
       d = __fsub_rn(va[c].w, mu); qa = __fmaf_rn(d, d, qa);
       d = __fsub_rn(vb[c].w, mu); qb = __fmaf_rn(d, d, qb);
     }
-    const Moments m = finish_moments(mu, __fadd_rn(tree_half(qa, 16), tree_half(qb, 16)), len);
+    const Moments m = finish_moments(mu, __fadd_rn(tree_half(qa, 16), tree_half(qb, 16)), len, inv_len);
     if (valid && m.flag < 0 && hl == 0) atomicMin(o.first_bad, (unsigned long long)i);
     const bool cst = m.flag != 0;
 #pragma unroll
@@ -278,7 +284,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
           } else {
             float gf = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
             gf = tree_half(gf, sf / 4);  // sf / 4 <= 16 consecutive canonical lanes, one part
-            if ((L & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(__fdiv_rn(gf, (float)sf));
+            if ((L & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(div_pow2(gf, inv_sf));
           }
         }
         // PAA: groups of 4 points, G consecutive canonical lanes per segment (G <= 16,
@@ -287,7 +293,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
         g = tree_half(g, G);
         if ((L & (G - 1)) == 0) {
           const int j = c * segs_per_chunk + L / G;
-          if (j < 16) paa[j] = __fdiv_rn(g, (float)s);
+          if (j < 16) paa[j] = div_pow2(g, inv_s);
         }
       }
     }

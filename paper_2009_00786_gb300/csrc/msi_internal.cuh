@@ -178,12 +178,18 @@ struct Moments {
   int flag;    // 0 normal, 1 constant, -1 non-finite
 };
 
-// mu = S1 / n already rounded; v = the combined sum of squared deviations.
-__device__ __forceinline__ Moments finish_moments(float mu, float v, int len) {
+// x / d for a power of two d: the product with its exact reciprocal, the same
+// correctly rounded value as the division at a fraction of its instructions (both are
+// the exact quotient rounded once).
+__device__ __forceinline__ float div_pow2(float x, float inv_d) { return __fmul_rn(x, inv_d); }
+
+// mu = S1 / n already rounded; v = the combined sum of squared deviations. inv_len
+// > 0: len is a power of two and inv_len its exact reciprocal (v / n by div_pow2).
+__device__ __forceinline__ Moments finish_moments(float mu, float v, int len, float inv_len = 0.0f) {
   Moments m;
   const float n = (float)len;
   m.mu = mu;
-  const float sigma = __fsqrt_rn(__fdiv_rn(v, n));
+  const float sigma = __fsqrt_rn(inv_len > 0.0f ? div_pow2(v, inv_len) : __fdiv_rn(v, n));
   if (!isfinite(m.mu) || !isfinite(sigma)) {
     m.flag = -1;
     m.rsig = 0.0f;

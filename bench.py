@@ -570,14 +570,14 @@ def main():
     achieved = kernels[dom]["achieved_gbs"]
     alg_bytes, refine_s = kernels[dom]["alg_bytes_per_launch"], kernels[dom]["avg_launch_us"] / 1e6
     traffic = None
+    import hashlib
+    dom_src = "msi_tc.cu" if dom == "q_tc_filter" else "msi_query.cu"
+    dom_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", dom_src), "rb").read()
+                             ).hexdigest()[:16]
     tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.txt")
     if os.path.exists(tpath):
-        import hashlib
         kv = dict(l.split(":", 1) for l in open(tpath).read().splitlines() if ":" in l and not l.startswith("#"))
-        src_name = kv.get("source", "msi_query.cu").strip()
-        src = open(os.path.join(ROOT, "paper_2009_00786_gb300", "csrc", src_name), "rb").read()
-        h = hashlib.sha256(src).hexdigest()[:16]
-        if kv.get("source_sha256_16", "").strip() == h:
+        if kv.get("source", dom_src).strip() == dom_src and kv.get("source_sha256_16", "").strip() == dom_sha:
             # a capture on a smaller collection, scaled to this launch by its units
             # (the algorithmic bytes) when the file gives the ratio
             if "dram_bytes_per_alg_byte" in kv:
@@ -608,6 +608,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": refine_s * 1e6,
+                     "source": dom_src, "source_sha256_16": dom_sha,
                      **({"tensor": tensor} if tensor else {})},
         "refine_kernels": kernels,
         # every kernel of the chain together, over the timed batched steps: leaves (40 B

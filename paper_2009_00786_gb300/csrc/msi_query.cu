@@ -122,19 +122,25 @@ __device__ __forceinline__ float warp_sqdist(const IndexView& ix, uint32_t id, f
 
 // Squared iSAX lower bound of one SAX word: s * sum_j T[j][sym_j]. Symbol byte b of
 // a 32-bit part becomes its byte offset in the row with one shift and one mask.
-__device__ __forceinline__ float word_lb2(uint4 wd, const float* Ts, int w, int card, float s) {
+template <bool kW16>
+__device__ __forceinline__ float word_lb2_t(uint4 wd, const float* Ts, int w, int card, float s) {
   const uint32_t parts[4] = {wd.x, wd.y, wd.z, wd.w};
   const char* tb = reinterpret_cast<const char*>(Ts);
   float acc = 0.0f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if (j < w) {
+    if (kW16 || j < w) {
       const uint32_t p = parts[j >> 2];
       const uint32_t off = (j & 3) == 0 ? (p << 2) & 0x3FCu : (p >> (8 * (j & 3) - 2)) & 0x3FCu;
       acc = __fadd_rn(acc, *reinterpret_cast<const float*>(tb + (size_t)j * card * 4 + off));
     }
   }
   return __fmul_rn(acc, s);
+}
+// (16 segments, the paper's configuration, takes a path without the per-segment
+// test of a run-time segment count)
+__device__ __forceinline__ float word_lb2(uint4 wd, const float* Ts, int w, int card, float s) {
+  return w == 16 ? word_lb2_t<true>(wd, Ts, w, card, s) : word_lb2_t<false>(wd, Ts, w, card, s);
 }
 
 // Squared iSAX lower bound of a leaf from its per-segment symbol envelope: the gap
@@ -971,7 +977,13 @@ __device__ __forceinline__ float word_lb2_coarse(uint4 wd, const float* T5s, int
   const char* tb = reinterpret_cast<const char*>(T5s);
   constexpr uint32_t kMask = (uint32_t)(kCoarse - 1) << 2;
   float acc = 0.0f;
-  if (cshift >= 2) {
+  if (cshift >= 2 && w == 16) {  // 16 segments: no per-segment test of the count
+    const int sh0 = cshift - 2;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      acc = __fadd_rn(acc, *reinterpret_cast<const float*>(tb + j * kCoarse * 4 +
+                                                            ((parts[j >> 2] >> (8 * (j & 3) + sh0)) & kMask)));
+  } else if (cshift >= 2) {
     const int sh0 = cshift - 2;
 #pragma unroll
     for (int j = 0; j < 16; ++j)

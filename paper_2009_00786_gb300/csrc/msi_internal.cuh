@@ -290,6 +290,55 @@ __device__ __forceinline__ unsigned long long interleave_key(int sym, int w, int
   return used < 64 ? key << (64 - used) : key;
 }
 
+// ------------------------------------------------------- async copies, mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of parity `parity` of barrier b, at most about `limit_ns`
+// nanoseconds; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 63) == 63) {
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+    }
+  }
+}
+// One bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16),
+// completing on barrier b's transaction count.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+
 // ------------------------------------------------------------------ margins
 // The two margins of the exactness argument for series of `len` points: eps relative
 // on squared distances (2^-16), tau absolute on lower bounds (1e-3 at len 256, growing
@@ -448,10 +497,12 @@ cudaError_t query_setup(msi_index* ix);
 cudaError_t slots_setup(msi_index* ix);
 // items_cap: work items (and 8x that many block tasks) a query may list; 0: room for
 // any query. A query that needs more is flagged as overflowed and run again.
+// blks_cap: block tasks (0: 8 per work item).
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
-                            int64_t* bytes, uint32_t items_cap = 0);
+                            int64_t* bytes, uint32_t items_cap = 0, uint32_t blks_cap = 0);
 void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap);
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap = 0);
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap = 0,
+                        uint32_t blks_cap = 0);
 void free_workspace(QueryView& qv);
 // window < 0: Euclidean distance; window >= 0: DTW with that Sakoe-Chiba half-width.
 // call != nullptr: q_dev / ids_dev / dists_dev / d64_dev are ignored and query qi of

@@ -1006,13 +1006,36 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
-  smem_fill(Ts, qv.T, ix.w * ix.card);
-  smem_fill(T5s, qv.T5, ix.w * kCoarse);
+  __shared__ __align__(8) uint64_t tbar_s[2];  // the coarse table arrived, the full table arrived
+  // The tables come in by two bulk copies (one thread issues them): the coarse one is
+  // waited for before the first word, the full one only before a warp's first full
+  // bound, so the warps start on the coarse bounds while it is still arriving.
+  const uint32_t t_bytes = (uint32_t)(ix.w * ix.card) * 4u, t5_bytes = (uint32_t)(ix.w * kCoarse) * 4u;
+  const bool bulk = (t_bytes & 15u) == 0 && ((reinterpret_cast<uintptr_t>(qv.T) | reinterpret_cast<uintptr_t>(qv.T5)) & 15u) == 0;
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      mbar_init(&tbar_s[0], 1);
+      mbar_init(&tbar_s[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mbar_expect_tx(&tbar_s[0], t5_bytes);
+      bulk_copy_g2s(T5s, qv.T5, t5_bytes, &tbar_s[0]);
+      mbar_expect_tx(&tbar_s[1], t_bytes);
+      bulk_copy_g2s(Ts, qv.T, t_bytes, &tbar_s[1]);
+    }
+  } else {
+    smem_fill(Ts, qv.T, ix.w * ix.card);
+    smem_fill(T5s, qv.T5, ix.w * kCoarse);
+  }
   for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
     fup_s[j] = qv.st->fup[j];
     flo_s[j] = qv.st->flo[j];
   }
   __syncthreads();
+  // a copy that has not landed within a second: the query is flagged and run again
+  // (the tables are then not trusted; the waits below stay bounded)
+  constexpr uint64_t kTableWaitNs = 1000000000ull;
+  if (bulk && !mbar_wait_for(&tbar_s[0], 0, kTableWaitNs)) qv.st->overflow = 1u;
+  bool t_ready = !bulk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
   uint4* qw = qw_s[warp];
@@ -1031,6 +1054,10 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
 
   // full bounds of the first 32 queued words (one per lane); survivors to the buffer
   auto drain32 = [&](uint32_t count) {
+    if (!t_ready) {  // the full table, once per warp
+      if (!mbar_wait_for(&tbar_s[1], 0, kTableWaitNs)) qv.st->overflow = 1u;
+      t_ready = true;
+    }
     const bool have = lane < (int)count;
     const uint32_t p = have ? qp[lane] : 0u;
     float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
@@ -1102,6 +1129,8 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     drain32(c);
     nq = c > 32 ? c - 32 : 0;
   }
+  // the full table's copy has landed before the CTA leaves (a warp that never needed it)
+  if (!t_ready && !mbar_wait_for(&tbar_s[1], 0, kTableWaitNs)) qv.st->overflow = 1u;
   // the last partial buffers of the CTA's warps: one atomic for the whole CTA
   __syncwarp();
   __shared__ uint32_t wbase_s[kFiltWarps], cbase_s;
@@ -2278,16 +2307,18 @@ cudaError_t dalloc(T** p, size_t count) {
 
 // One query workspace with room for cand_cap candidates and surv_cap survivors
 // (work items, block lists and leaf lists always have room for any query).
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap);
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap,
+                        uint32_t blks_cap);
 
 // Work items any query can need: each leaf touches at most (its size / kItem) + 2
 // aligned tiles of kItem positions.
 static int64_t full_items(const msi_index* ix) { return ix->n / kItem + 2 * ix->L + 2; }
 
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
-                            int64_t* bytes, uint32_t items_cap) {
+                            int64_t* bytes, uint32_t items_cap, uint32_t blks_cap) {
   cudaError_t e;
   const size_t items = items_cap ? std::min<size_t>(items_cap, (size_t)full_items(ix)) : (size_t)full_items(ix);
+  const size_t blks = blks_cap ? std::min<size_t>(blks_cap, (size_t)kBlocksPerItem * items) : kBlocksPerItem * items;
   if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T5, (size_t)ix->w * kCoarse)) != cudaSuccess) return e;
@@ -2295,7 +2326,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   if ((e = dalloc(&qv.leaf_list, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.leaf_lb2, (size_t)ix->L)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.items, items)) != cudaSuccess) return e;
-  if ((e = dalloc(&qv.blks, (size_t)kBlocksPerItem * items)) != cudaSuccess) return e;
+  if ((e = dalloc(&qv.blks, blks)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.partials, (size_t)4 * kMaxRefineWarps)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.blockmin, (size_t)(ix->L / kThreads + 2))) != cudaSuccess) return e;
   if ((e = dalloc(&qv.cand, (size_t)cand_cap)) != cudaSuccess) return e;
@@ -2308,19 +2339,21 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
   qv.cand_cap = cand_cap;
   qv.surv_cap = surv_cap;
   qv.items_cap = (uint32_t)items;
-  qv.blks_cap = (uint32_t)(kBlocksPerItem * items);
+  qv.blks_cap = (uint32_t)blks;
   qv.ovf = nullptr;
   qv.eps = margin_eps();
   qv.tau = margin_tau(ix->len);
-  *bytes += workspace_bytes(ix, cand_cap, surv_cap, items_cap);
+  *bytes += workspace_bytes(ix, cand_cap, surv_cap, items_cap, blks_cap);
   return cudaSuccess;
 }
 
 // Device bytes of one query workspace (alloc_workspace).
-int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap) {
+int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap,
+                        uint32_t blks_cap) {
   const int64_t items = items_cap ? std::min<int64_t>(items_cap, full_items(ix)) : full_items(ix);
+  const int64_t blks = blks_cap ? std::min<int64_t>(blks_cap, kBlocksPerItem * items) : kBlocksPerItem * items;
   return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + kCoarse) * 4 + (int64_t)ix->L * 8 +
-         items * (16 + 8 * kBlocksPerItem) + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
+         items * 16 + blks * 8 + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
 
 void free_workspace(QueryView& qv) {
@@ -2575,20 +2608,25 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   return cudaGetLastError();
 }
 
-// Batch workspaces: the candidate list as a query slot's, survivor lists of n / 16
-// entries (at least 2^20, at most 2^23), and 2^18 work items (2^21 block tasks): a
-// query that needs more overflows and is run again alone with room for all n.
-// A slot capacity given at build time bounds these lists as it bounds a slot's.
-static void batch_capacities(const msi_index* ix, uint32_t* cand_cap, uint32_t* surv_cap, uint32_t* items_cap) {
+// Batch workspaces: the candidate list as a query slot's, survivor lists of n / 8
+// entries (at least 2^20, at most 2^24), room for any query's work items, and block
+// tasks for n / 16 positions (at least 2^21): a query that needs more overflows and is
+// run again alone with room for all n. (Smaller lists made k = 100 queries overflow:
+// 783 of 4096 at 100M x 256 with 2^18 items and n / 16 survivors.) A slot capacity
+// given at build time bounds these lists as it bounds a slot's.
+static void batch_capacities(const msi_index* ix, uint32_t* cand_cap, uint32_t* surv_cap, uint32_t* items_cap,
+                             uint32_t* blks_cap) {
   uint32_t sc;
   slot_capacities(ix, ix->slot_cap, cand_cap, &sc);
   if (ix->slot_cap) {
     *surv_cap = sc;
     *items_cap = (uint32_t)std::max(256, ix->slot_cap / 4);
+    *blks_cap = 0;  // 8 per item
     return;
   }
-  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, std::min<int64_t>(1 << 23, std::max<int64_t>(1 << 20, ix->n / 16)));
-  *items_cap = 1u << 18;
+  *surv_cap = (uint32_t)std::min<int64_t>(ix->n, std::min<int64_t>(1 << 24, std::max<int64_t>(1 << 20, ix->n / 8)));
+  *items_cap = 0;  // room for any query
+  *blks_cap = (uint32_t)std::min<int64_t>(kBlocksPerItem * full_items(ix), std::max<int64_t>(1 << 21, ix->n / 16));
 }
 
 cudaError_t batch_setup(msi_index* ix) {
@@ -2597,20 +2635,29 @@ cudaError_t batch_setup(msi_index* ix) {
   if (ix->batch_dense && !ix->tc_ready && (e = tc_setup(ix)) != cudaSuccess) return e;
   const int G = std::max(1, ix->batch_group);
   if ((int)ix->bws.size() < G) {
-    uint32_t cc, sc, ic;
-    batch_capacities(ix, &cc, &sc, &ic);
+    uint32_t cc, sc, ic, bc;
+    batch_capacities(ix, &cc, &sc, &ic, &bc);
     while ((int)ix->bws.size() < G) {
       QueryView qv{};
-      if ((e = alloc_workspace(ix, qv, cc, sc, &ix->device_bytes, ic)) != cudaSuccess ||
-          (e = dalloc(&qv.surv2, (size_t)sc)) != cudaSuccess) {
+      if ((e = alloc_workspace(ix, qv, cc, sc, &ix->device_bytes, ic, bc)) != cudaSuccess) {
         free_workspace(qv);
         return e;
       }
-      ix->device_bytes += (int64_t)sc * 8;
       qv.counters = ix->qv.counters;
       ix->bws.push_back(qv);
       ix->bws_dirty = true;
     }
+  }
+  // the bound-ordered copy of the survivors, only while ordering is on
+  if (ix->batch_order) {
+    uint32_t cc, sc, ic, bc;
+    batch_capacities(ix, &cc, &sc, &ic, &bc);
+    for (auto& qv : ix->bws)
+      if (!qv.surv2) {
+        if ((e = dalloc(&qv.surv2, (size_t)sc)) != cudaSuccess) return e;
+        ix->device_bytes += (int64_t)sc * 8;
+        ix->bws_dirty = true;
+      }
   }
   if (ix->bws_dev_cap < (int)ix->bws.size()) {
     if (ix->bws_dev) cudaFree(ix->bws_dev);
@@ -2633,11 +2680,11 @@ cudaError_t batch_setup(msi_index* ix) {
 
 // Frees the batch workspaces beyond the first `keep` (no batch may be in flight).
 void batch_release(msi_index* ix, int keep) {
-  uint32_t cc, sc, ic;
-  batch_capacities(ix, &cc, &sc, &ic);
+  uint32_t cc, sc, ic, bc;
+  batch_capacities(ix, &cc, &sc, &ic, &bc);
   while ((int)ix->bws.size() > keep) {
+    ix->device_bytes -= workspace_bytes(ix, cc, sc, ic, bc) + (ix->bws.back().surv2 ? (int64_t)sc * 8 : 0);
     free_workspace(ix->bws.back());
-    ix->device_bytes -= workspace_bytes(ix, cc, sc, ic) + (int64_t)sc * 8;
     ix->bws.pop_back();
     ix->bws_dirty = true;
   }
@@ -2648,6 +2695,9 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   cudaError_t e;
   if (count < 1 || count > (int)ix->bws.size() || count > 65535) return cudaErrorInvalidValue;
   if (ix->bws_dirty) return cudaErrorNotReady;  // batch_setup has not written the views
+  if (ix->batch_order && !ix->batch_dense)  // batch_setup allocates the ordered copies
+    for (int i = 0; i < count; ++i)
+      if (!ix->bws[i].surv2) return cudaErrorNotReady;
   const bool pdl = ix->batch_pdl;
   const int share = std::max(1, ix->batch_share);
   const int series_grid = std::max(1, ix->grid_series / share);

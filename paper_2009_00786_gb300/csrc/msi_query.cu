@@ -897,18 +897,24 @@ constexpr int kBlkThreads = 256;
 // and lists the surviving blocks; the list is compacted per CTA (one atomic per CTA).
 // Squared iSAX bound of a symbol envelope (per-segment min / max symbols lo, hi):
 // T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range.
-__device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
-                                         float seglen) {
+template <bool kW16>
+__device__ __forceinline__ float env_lb2_t(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
+                                           float seglen) {
   const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
   float acc = 0.0f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if (j < w) {
+    if (kW16 || j < w) {
       const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
       acc = __fadd_rn(acc, Ts[j * card + min(max(qsym[j], sl), sh)]);
     }
   }
   return __fmul_rn(acc, seglen);
+}
+__device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
+                                         float seglen) {
+  return w == 16 ? env_lb2_t<true>(lo, hi, Ts, qsym, w, card, seglen)
+                 : env_lb2_t<false>(lo, hi, Ts, qsym, w, card, seglen);
 }
 
 __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const QueryView& qv) {
@@ -1006,36 +1012,13 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
-  __shared__ __align__(8) uint64_t tbar_s[2];  // the coarse table arrived, the full table arrived
-  // The tables come in by two bulk copies (one thread issues them): the coarse one is
-  // waited for before the first word, the full one only before a warp's first full
-  // bound, so the warps start on the coarse bounds while it is still arriving.
-  const uint32_t t_bytes = (uint32_t)(ix.w * ix.card) * 4u, t5_bytes = (uint32_t)(ix.w * kCoarse) * 4u;
-  const bool bulk = (t_bytes & 15u) == 0 && ((reinterpret_cast<uintptr_t>(qv.T) | reinterpret_cast<uintptr_t>(qv.T5)) & 15u) == 0;
-  if (bulk) {
-    if (threadIdx.x == 0) {
-      mbar_init(&tbar_s[0], 1);
-      mbar_init(&tbar_s[1], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      mbar_expect_tx(&tbar_s[0], t5_bytes);
-      bulk_copy_g2s(T5s, qv.T5, t5_bytes, &tbar_s[0]);
-      mbar_expect_tx(&tbar_s[1], t_bytes);
-      bulk_copy_g2s(Ts, qv.T, t_bytes, &tbar_s[1]);
-    }
-  } else {
-    smem_fill(Ts, qv.T, ix.w * ix.card);
-    smem_fill(T5s, qv.T5, ix.w * kCoarse);
-  }
+  smem_fill(Ts, qv.T, ix.w * ix.card);
+  smem_fill(T5s, qv.T5, ix.w * kCoarse);
   for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
     fup_s[j] = qv.st->fup[j];
     flo_s[j] = qv.st->flo[j];
   }
   __syncthreads();
-  // a copy that has not landed within a second: the query is flagged and run again
-  // (the tables are then not trusted; the waits below stay bounded)
-  constexpr uint64_t kTableWaitNs = 1000000000ull;
-  if (bulk && !mbar_wait_for(&tbar_s[0], 0, kTableWaitNs)) qv.st->overflow = 1u;
-  bool t_ready = !bulk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint2* buf = buf_s[warp];
   uint4* qw = qw_s[warp];
@@ -1054,10 +1037,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
 
   // full bounds of the first 32 queued words (one per lane); survivors to the buffer
   auto drain32 = [&](uint32_t count) {
-    if (!t_ready) {  // the full table, once per warp
-      if (!mbar_wait_for(&tbar_s[1], 0, kTableWaitNs)) qv.st->overflow = 1u;
-      t_ready = true;
-    }
     const bool have = lane < (int)count;
     const uint32_t p = have ? qp[lane] : 0u;
     float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
@@ -1129,8 +1108,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     drain32(c);
     nq = c > 32 ? c - 32 : 0;
   }
-  // the full table's copy has landed before the CTA leaves (a warp that never needed it)
-  if (!t_ready && !mbar_wait_for(&tbar_s[1], 0, kTableWaitNs)) qv.st->overflow = 1u;
   // the last partial buffers of the CTA's warps: one atomic for the whole CTA
   __syncwarp();
   __shared__ uint32_t wbase_s[kFiltWarps], cbase_s;

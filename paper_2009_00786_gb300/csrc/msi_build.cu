@@ -840,13 +840,35 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
+// The build's temporaries: carved from one device allocation reserved up front (one
+// cudaMalloc and one cudaFree instead of one per array), with a fallback to separate
+// allocations should the reservation run short.
 struct Freer {
   std::vector<void*> ptrs;
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
   ~Freer() {
     for (void* p : ptrs) cudaFree(p);
+    if (base) cudaFree(base);
+  }
+  cudaError_t reserve(size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)&base, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      return cudaSuccess;  // the separate allocations below still work (or fail alone)
+    }
+    cap = bytes;
+    return cudaSuccess;
   }
   template <typename T>
   cudaError_t get(T** p, size_t count) {
+    const size_t bytes = (sizeof(T) * (count ? count : 1) + 255) & ~size_t(255);
+    if (base && used + bytes <= cap) {
+      *p = reinterpret_cast<T*>(base + used);
+      used += bytes;
+      return cudaSuccess;
+    }
     cudaError_t e = dalloc(p, count);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
@@ -870,6 +892,15 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   unsigned long long* keys_alt;
   uint32_t* ids_alt;
   *stage = "allocating build scratch";
+  {  // words, keys and ids twice, moments, flags, ranks, radix histograms, the nodes of
+     // a level (and the balanced split's sort buffers); 64 MB of room for the rest
+    const int64_t tiles_b = (n + kRsTile - 1) / kRsTile;
+    const bool bal = (ix->flags & MSI_BUILD_BALANCED_SPLIT) != 0;
+    const size_t want = (size_t)n * (16 + 8 + 4 + 8 + 8 + 4 + 1 + 4 + (bal ? 36 : 0)) + (size_t)tiles_b * 1024 +
+                        (size_t)16 * std::min<int64_t>(n, (1ll << std::min(w * ix->bits, 20)) + 2 * (n / ix->cap) + 2) +
+                        ((size_t)64 << 20);
+    MSI_TRY(tmp.reserve(want));
+  }
   MSI_TRY(tmp.get(&o.words, n));
   MSI_TRY(tmp.get(&o.keys, n));
   MSI_TRY(tmp.get(&o.ids, n));

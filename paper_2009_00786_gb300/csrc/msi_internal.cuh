@@ -96,6 +96,8 @@ struct QState {
                                 // range [0, kbase) of the candidate histogram (0: none yet)
   uint32_t nfront;              // leaves refined early (the lowest-bound survivors)
   uint32_t front_leaf[8];       // their ids; the filters skip them
+  uint32_t front_beg[8], front_end[8];  // batched chain: their position ranges
+  unsigned int front_lb[8];     // batched chain: their bounds (fp32 bits, ascending)
   unsigned int cand_count;      // candidates appended
   unsigned int rc_count;        // FP64 re-checks appended
   unsigned int final_bits;      // k-th smallest candidate squared distance (fp32 bits)

@@ -866,6 +866,151 @@ q_front(IndexView ix, QueryView qv, uint32_t nblockmin) {
   q_front_body(ix, qv, nblockmin);
 }
 
+// The batched chain's front leaves, picked once per query by one block: the m lowest
+// (bound bits << 32 | leaf) keys among the leaf filter's per-block minima whose bound
+// passes the BSF as thread 0 reads it (front_leaves' choice, with the whole block
+// scanning the minima in each round). Their ids, position ranges and bounds go to the
+// query's state, where the front blocks and the block filter read them.
+__device__ __forceinline__ void q_front_pick_body(const IndexView& ix, const QueryView& qv, uint32_t nblockmin) {
+  __shared__ unsigned long long s_w[kThreads / 32];
+  __shared__ unsigned long long s_best;
+  __shared__ float s_bound2;
+  QState* st = qv.st;
+  if (threadIdx.x == 0) s_bound2 = lb_bound2(*(volatile unsigned*)&st->thr_bits, qv.eps, qv.tau);
+  const int m = front_count(qv.k);
+  const int lane = threadIdx.x & 31;
+  unsigned long long last = 0;
+  int count = 0;
+  for (int round = 0; round < m; ++round) {
+    unsigned long long best = ~0ull;
+    for (uint32_t i = threadIdx.x; i < nblockmin; i += blockDim.x) {
+      const unsigned long long v = qv.blockmin[i];
+      if ((round == 0 || v > last) && v < best) best = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+      best = other < best ? other : best;
+    }
+    if (lane == 0) s_w[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long b = ~0ull;
+      for (int w = 0; w < kThreads / 32; ++w) b = s_w[w] < b ? s_w[w] : b;
+      s_best = b;
+    }
+    __syncthreads();
+    best = s_best;  // the same in every thread: one decision for the block
+    if (best == ~0ull || __uint_as_float((uint32_t)(best >> 32)) > s_bound2) break;
+    if (threadIdx.x == 0) {
+      const uint32_t l = (uint32_t)best;
+      st->front_leaf[count] = l;
+      st->front_beg[count] = ix.leaf_begin[l];
+      st->front_end[count] = ix.leaf_begin[l + 1];
+      st->front_lb[count] = (uint32_t)(best >> 32);
+    }
+    last = best;
+    ++count;
+  }
+  if (threadIdx.x == 0) st->nfront = (uint32_t)count;
+}
+
+// The batched chain's front refinement over the picked leaves (q_front_body's work
+// with the pick read from the query's state). A block first drops the leaves whose
+// bound the current BSF already prunes (a prefix stays: the bounds ascend), and a
+// block whose warps start past the remaining rows returns before loading the query.
+__device__ __forceinline__ void q_front_picked_body(const IndexView& ix, const QueryView& qv) {
+  extern __shared__ __align__(16) float qs[];
+  __shared__ unsigned s_min;
+  __shared__ uint32_t s_beg[kMaxFront], s_pre[kMaxFront + 1];
+  __shared__ int s_nf;
+  __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
+  QState* st = qv.st;
+  if (threadIdx.x == 0) {
+    const float bound2 = lb_bound2(*(volatile unsigned*)&st->thr_bits, qv.eps, qv.tau);
+    const int n = (int)st->nfront;
+    int nf = 0;
+    s_pre[0] = 0;
+    while (nf < n && __uint_as_float(st->front_lb[nf]) <= bound2) {
+      s_beg[nf] = st->front_beg[nf];
+      s_pre[nf + 1] = s_pre[nf] + (st->front_end[nf] - s_beg[nf]);
+      ++nf;
+    }
+    s_nf = nf;
+    s_min = 0x7f800000u;
+  }
+  __syncthreads();
+  const int nf = s_nf;
+  const uint32_t total = s_pre[nf];
+  const uint32_t warps = gridDim.x * (kThreads / 32);
+  const uint32_t w0 = blockIdx.x * (kThreads / 32);
+  const bool fine = ix.wf != 0;
+  if (nf == 0 || (uint64_t)w0 * (fine ? 32u : 1u) >= total) return;  // the same in every thread
+  smem_fill(qs, qv.qz, ix.len);
+  for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
+    fup_s[j] = st->fup[j];
+    flo_s[j] = st->flo[j];
+  }
+  __syncthreads();
+  const uint32_t sa = st->seed_a, sb = st->seed_b;
+  const unsigned thr = *(volatile unsigned*)&st->thr_bits;
+  const float keep2 = keep_bound2(thr, qv.eps);
+  const uint32_t gw = w0 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  unsigned bestd = 0x7f800000u;
+  uint32_t n_front = 0, n_fine = 0;
+  auto position = [&](uint32_t g) {
+    int f = 0;
+    while (g >= s_pre[f + 1]) ++f;
+    return s_beg[f] + (g - s_pre[f]);
+  };
+  auto refine = [&](uint32_t pos) {
+    const uint32_t id = ix.perm[pos];
+    const float2 ms = ix.data_is_z ? make_float2(0.f, 0.f) : ix.stats[pos];
+    const float d2 = warp_sqdist(ix, id, ms, qs);
+    if (lane == 0) {
+      ++n_front;
+      if (d2 <= keep2) {
+        const uint32_t slot = atomicAdd(&st->cand_count, 1u);
+        if (slot < qv.cand_cap) qv.cand[slot] = pack(d2, pos);
+        else st->overflow = 1u;
+      }
+    }
+    bestd = min(bestd, __float_as_uint(d2));
+  };
+  const float lbb = lb_bound2(thr, qv.eps, qv.tau);
+  if (fine && lbb < INFINITY) {
+    for (uint32_t g0 = gw * 32; g0 < total; g0 += warps * 32) {
+      const uint32_t g = g0 + lane;
+      const uint32_t pos = g < total ? position(g) : 0u;
+      const bool screen = g < total && !(pos >= sa && pos < sb);
+      n_fine += __popc(__ballot_sync(kFull, screen));
+      const bool want = screen && fine_lb2(ix, fup_s, flo_s, ix.perm[pos]) <= lbb;
+      for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
+    }
+  } else {
+    for (uint32_t g = gw; g < total; g += warps) {
+      const uint32_t pos = position(g);
+      if (pos >= sa && pos < sb) continue;  // already refined by the seed
+      refine(pos);
+    }
+  }
+  __shared__ unsigned s_n, s_nfine;
+  if (threadIdx.x == 0) s_n = s_nfine = 0;
+  __syncthreads();
+  if (lane == 0) {
+    if (bestd < 0x7f800000u) atomicMin(&s_min, bestd);
+    if (n_front) atomicAdd(&s_n, n_front);
+    if (n_fine) atomicAdd(&s_nfine, n_fine);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_n) atomicAdd(&st->series_refined, s_n);
+    if (s_nfine) atomicAdd(&st->fine_front, s_nfine);
+    if (qv.k == 1 && s_min < thr) atomicMin(&st->thr_bits, s_min);
+  }
+}
+
 // ------------------------------------------------------------ refinement
 // The refinement in three streaming kernels (ProcessQueue and CalculateRealDistance,
 // Algorithms 8-9, with the block filter, the per-series filter and the real distances
@@ -1731,16 +1876,15 @@ __global__ void __launch_bounds__(kThreads) qb_leaf_filter_lm(IndexView ix, Batc
     bool keep = false;
     float lb2 = 0.0f;
     if (have && !(b >= sa_s[q] && e <= sb_s[q])) {
+      // the gap to [lower, upper] without branches: lower <= upper, so at most one
+      // difference is positive (a NaN PAA value gives 0, as the compare form does);
+      // segments past w have an infinite envelope and add an exact 0
       float acc = 0.0f;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        if (j < ix.w) {
-          const float p = paa_s[q][j];
-          float d = 0.0f;
-          if (p < lower[j]) d = __fsub_rn(lower[j], p);
-          else if (p > upper[j]) d = __fsub_rn(p, upper[j]);
-          acc = __fadd_rn(acc, __fmul_rn(d, d));
-        }
+        const float p = paa_s[q][j];
+        const float d = fmaxf(fmaxf(__fsub_rn(lower[j], p), __fsub_rn(p, upper[j])), 0.0f);
+        acc = __fadd_rn(acc, __fmul_rn(d, d));
       }
       lb2 = __fmul_rn(acc, seglen);
       keep = lb2 <= bnd_s[q];
@@ -1762,13 +1906,11 @@ __global__ void __launch_bounds__(kThreads) qb_leaf_filter_lm(IndexView ix, Batc
     uint32_t ibase = 0;
     if (lane == 31) ibase = atomicAdd(&qv.st->item_count, incl);
     ibase = __shfl_sync(kFull, ibase, 31) + incl - mynit;
-    unsigned long long mine = keep ? (((unsigned long long)__float_as_uint(lb2) << 32) | (uint32_t)l) : ~0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(kFull, mine, o);
-      mine = other < mine ? other : mine;
-    }
-    if (lane == 0) atomicMin(&bmin_s[q], mine);
+    // the warp's lowest (bound, leaf) key: the lowest bound bits, then the lowest leaf
+    // among the lanes that hold it (bounds are >= 0, so their bits order as the values)
+    const unsigned lbits = __reduce_min_sync(kFull, keep ? __float_as_uint(lb2) : ~0u);
+    const unsigned lmin = __reduce_min_sync(kFull, keep && __float_as_uint(lb2) == lbits ? (uint32_t)l : ~0u);
+    if (lane == 0) atomicMin(&bmin_s[q], ((unsigned long long)lbits << 32) | lmin);
     if (keep) {
       const uint32_t slot = base + __popc(m & lt);
       qv.leaf_list[slot] = (uint32_t)l;
@@ -1787,10 +1929,15 @@ __global__ void __launch_bounds__(kThreads) qb_leaf_filter_lm(IndexView ix, Batc
   for (int q = threadIdx.x; q < count; q += blockDim.x) a.qvs[q].blockmin[blockIdx.x] = bmin_s[q];
 }
 
-__global__ void __launch_bounds__(kThreads) qb_front(IndexView ix, BatchArgs a, uint32_t nblockmin) {
+__global__ void __launch_bounds__(kThreads) qb_front_pick(IndexView ix, BatchArgs a, uint32_t nblockmin) {
   pdl_begin();
   const QueryView& qv = batch_view(a);
-  q_front_body(ix, qv, nblockmin);
+  q_front_pick_body(ix, qv, nblockmin);
+}
+__global__ void __launch_bounds__(kThreads) qb_front(IndexView ix, BatchArgs a) {
+  pdl_begin();
+  const QueryView& qv = batch_view(a);
+  q_front_picked_body(ix, qv);
 }
 __global__ void __launch_bounds__(kBlkThreads) qb_filter_blocks(IndexView ix, BatchArgs a) {
   pdl_begin();
@@ -2731,8 +2878,9 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   const uint32_t nlf = (uint32_t)((ix->L + kThreads - 1) / kThreads);
   if (count <= kBatchMax) MSI_LAUNCH(qb_leaf_filter_lm, nlf, kThreads, 0, s, v, a, count);
   else MSI_LAUNCH(qb_leaf_filter, dim3(nlf, B), kThreads, 0, s, v, a);
+  MSI_LAUNCH(qb_front_pick, dim3(1, B), kThreads, 0, s, v, a, nlf);
   MSI_LAUNCH(qb_front, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ix->cap + 7) / 8, 256) / share), B),
-             kThreads, qbytes, s, v, a, nlf);
+             kThreads, qbytes, s, v, a);
   if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);
   MSI_LAUNCH(qb_filter_blocks, dim3(blocks_grid, B), kBlkThreads, fsmem, s, v, a);
   if (ev_a) cudaEventRecord(ev_a, s);
@@ -2745,7 +2893,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   else MSI_LAUNCH(qb_refine_rows<false>, dim3(rows_grid, B), kRowWarps * 32, rsmem, s, v, a);
   if (ev_b) cudaEventRecord(ev_b, s);
   MSI_LAUNCH(qb_finalize, dim3(1, B), 1024, 0, s, v, a);
-  ix->kernel_launches += 9 + (k > 1 ? 2 : 0) + (ix->batch_order ? 1 : 0);
+  ix->kernel_launches += 10 + (k > 1 ? 2 : 0) + (ix->batch_order ? 1 : 0);
   return cudaGetLastError();
 }
 

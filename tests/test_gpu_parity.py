@@ -225,9 +225,9 @@ def test_stats_counters(msi):
     # and one row kernel launch timed for the group
     assert st["refine_launches"] == 1 and st["refine_ms"] > 0
     assert st["series_lower_bounded"] < 6 * 8000  # leaves were pruned
-    # views, prep, seed, seed pick, leaf filter, front leaves, seed pick, block filter,
-    # series filter, row refinement, finalize: once for the group
-    assert st["kernel_launches"] == 11
+    # views, prep, seed, seed pick, leaf filter, front pick, front leaves, seed pick,
+    # block filter, series filter, row refinement, finalize: once for the group
+    assert st["kernel_launches"] == 12
     msi.msi_query_stats_get(ix, reset=True)
     msi.msi_knn(ix, Q[:1], 5)  # one query timed: its own chain
     st = msi.msi_query_stats_get(ix)
@@ -235,15 +235,15 @@ def test_stats_counters(msi):
     msi.msi_query_stats_get(ix, reset=True)
     msi.msi_set_timing(ix, False)
     # two queries in one call: the batched chain launches each stage once for both
-    # (views, prep, seed, leaf filter, front leaves, block filter, series filter, rows,
-    # finalize)
+    # (views, prep, seed, leaf filter, front pick, front leaves, block filter, series
+    # filter, rows, finalize)
     msi.msi_knn(ix, Q[:2], 1)
-    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 10
     msi.msi_knn(ix, Q[:1], 40)  # one query, k > 32: its own chain, no register top-k
-    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9 + 10
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 10 + 10
     msi.msi_schedule_set(ix, batch_chain=0)  # the query slots: a chain per query
     msi.msi_knn(ix, Q[:2], 1)
-    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 9 + 10 + 2 * 8
+    assert msi.msi_query_stats_get(ix)["kernel_launches"] == 10 + 10 + 2 * 8
 
 
 @pytest.mark.parametrize("chain", [1, 0])
@@ -302,8 +302,8 @@ def test_repeated_batched_shape_replays_with_new_pointers(msi, chain):
             assert np.all(d64_x.cpu().numpy() >= 0)
     st = msi.msi_query_stats_get(ix)
     assert st["queries"] == calls * nq
-    # per call: 3 groups of at most 4 queries x 11 stages (k > 1), or 9 chains of 10
-    assert st["kernel_launches"] == calls * (3 * 11 if chain else nq * 10)
+    # per call: 3 groups of at most 4 queries x 12 stages (k > 1), or 9 chains of 10
+    assert st["kernel_launches"] == calls * (3 * 12 if chain else nq * 10)
     ix.close()
 
 

@@ -459,6 +459,7 @@ struct msi_index {
   double* ws_d64 = nullptr;
   bool grids_ready = false;  // persistent grid sizes of every refinement mode
   int grid_series = 0, grid_blocks = 0, grid_rows1 = 0, grid_rowsk = 0;
+  int grid_series_b = 0;  // the batched chain's series filter (its own register budget)
   int grid_dtw = 0, grid_dtw_check = 0;  // DTW refinement and FP64 re-check
   bool timing = false;
   std::vector<cudaEvent_t> events;  // refinement timing: three per query (start, after filter, end)

@@ -1023,13 +1023,14 @@ __device__ __forceinline__ void q_front_picked_body(const IndexView& ix, const Q
 // q_filter_series: a warp per task bounds every position by its SAX word (a coarse
 //   bound first, then the full one, then the fine PAA's when the index keeps one);
 //   survivors {position, bound} go to a per-warp buffer flushed 32 at a time to the
-//   survivor list. The words of kStages tasks are in flight per warp.
+//   survivor list. kUnroll tasks are in flight per warp.
 // q_refine_rows: real distances of the survivors whose bound still passes the
 //   current BSF, kRows rows per warp at a time. k = 1: the BSF is an atomicMin taken
 //   only by a distance below the current BSF. k > 1: the shared candidate histogram
 //   (khist_bound), and for k <= 32 each warp's own k best in registers (lane i holds
 //   the i-th), published once it has k.
 constexpr int kFiltWarps = 8;
+constexpr int kUnroll = 4;
 constexpr int kBlocksPerItem = kItem / 32;
 constexpr int kRows = 4;
 constexpr int kRowWarps = 8;
@@ -1123,14 +1124,11 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 }
 
 // One warp per surviving block: bounds every position by its SAX word and buffers
-// the survivors {position, bound}, flushed 32 at a time. A warp keeps the words of its
-// next kStages blocks in flight in a shared-memory ring (16-byte asynchronous copies,
-// one per lane and block), with their descriptors loaded a ring ahead of that. Each
-// word is first bounded from its kCoarseBits-bit symbol prefixes (T5: kCoarse entries
-// per segment, at most two lanes per bank); the words that pass are queued per warp
-// and bounded from their full symbols (T) a whole warp at a time.
+// the survivors {position, bound}, flushed 32 at a time. kUnroll blocks are in flight
+// per warp. Each word is first bounded from its kCoarseBits-bit symbol prefixes (T5:
+// kCoarse entries per segment, at most two lanes per bank); the words that pass are
+// queued per warp and bounded from their full symbols (T) a whole warp at a time.
 constexpr int kQueue = 64;
-constexpr int kStages = 4;
 
 // Coarse bound from the symbols' top kCoarseBits bits. The table entry's byte offset
 // inside segment j's row comes straight from the word: symbol byte b of a 32-bit part
@@ -1170,7 +1168,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   __shared__ uint2 buf_s[kFiltWarps][64];
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
-  __shared__ uint4 ring_s[kFiltWarps][kStages][32];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   smem_fill(T5s, qv.T5, ix.w * kCoarse);
@@ -1228,50 +1225,31 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     }
   };
 
-  // the warp's blocks are t = gw + i * stride, i = 0, 1, ...; block i sits in ring
-  // stage i % kStages; tk holds the descriptors of the blocks in flight, tn those of
-  // the next ring (loaded while the current one is bounded)
-  const uint32_t cnt = ntask > gw ? (ntask - gw + stride - 1) / stride : 0u;
-  auto desc = [&](uint32_t i) { return i < cnt ? qv.blks[gw + i * stride] : make_uint2(0, 0); };
-  uint4(*ring)[32] = ring_s[warp];
-  auto issue = [&](int u, uint2 d) {  // the block's 32 words into stage u; lanes outside its range fill 0
-    const bool in = lane >= (int)(d.y & 255u) && lane < (int)(d.y >> 8);
-    cp_async16(&ring[u][lane], in ? ix.words + (d.x * 32 + lane) : ix.words, in);
-    cp_async_commit();
-  };
-  uint2 tk[kStages], tn[kStages];
-  unsigned thr = 0;
-  if (cnt) {
-#pragma unroll
-    for (int u = 0; u < kStages; ++u) tk[u] = desc(u);
-#pragma unroll
-    for (int u = 0; u < kStages; ++u) tn[u] = desc(kStages + u);
-#pragma unroll
-    for (int u = 0; u < kStages; ++u) issue(u, tk[u]);
-    thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u, 0);
-  }
-  for (uint32_t i0 = 0; i0 < cnt; i0 += kStages) {
-    // the BSF for this ring, and a fresh reading for the next one (a BSF read earlier
-    // is only larger: it prunes less, never wrongly)
+  for (uint32_t t0 = gw; t0 < ntask; t0 += stride * kUnroll) {
+    const unsigned thr = __shfl_sync(kFull, lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u, 0);
     bound2 = lb_bound2(thr, qv.eps, qv.tau);
-    const unsigned thr_next = lane == 0 ? *(volatile unsigned*)&st->thr_bits : 0u;
+    uint2 task[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kStages; ++u) {
-      cp_async_wait<kStages - 1>();  // block i0 + u has landed (this lane's copy)
-      __syncwarp();                  // and every lane's
-      const uint4 wd = ring[u][lane];
-      const uint2 task = tk[u];
-      __syncwarp();  // the stage is read: refill it with block i0 + u + kStages
-      tk[u] = tn[u];
-      issue(u, tk[u]);
-      tn[u] = desc(i0 + u + 2 * kStages);
-      const uint32_t p = task.x * 32 + lane;
-      const bool valid = lane >= (int)(task.y & 255u) && lane < (int)(task.y >> 8) && (p < sa || p >= sb);
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t t = t0 + u * stride;
+      task[u] = t < ntask ? qv.blks[t] : make_uint2(0, 0);  // an empty range when past the end
+    }
+    uint4 wd[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t p = task[u].x * 32 + lane;
+      const bool in = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8);
+      wd[u] = in ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t p = task[u].x * 32 + lane;
+      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
-      const bool pass_c = valid && word_lb2_coarse(wd, T5s, ix.w, cshift, seglen) <= bound2;
+      const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
       if (pass_c) {
-        qw[nq + __popc(m & lt)] = wd;
+        qw[nq + __popc(m & lt)] = wd[u];
         qp[nq + __popc(m & lt)] = p;
       }
       nq += __popc(m);
@@ -1281,9 +1259,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
         nq -= 32;
       }
     }
-    thr = __shfl_sync(kFull, thr_next, 0);
   }
-  cp_async_wait<0>();  // the ring's last (empty) copies have landed before the block ends
   while (nq > 0) {
     const uint32_t c = nq;
     drain32(c);
@@ -2609,13 +2585,6 @@ static cudaError_t refine_config(msi_index* ix) {
     const size_t fsmem = sizeof(float) * (size_t)ix->w * ix->card;
     const size_t ssmem = fsmem + sizeof(float) * (size_t)ix->w * kCoarse;
     const size_t rsmem = sizeof(float) * (size_t)((ix->len + 3) & ~3);
-    // the series filters' tables and their static buffers (the word ring) pass 48 KB
-    // together: the launches need the larger dynamic limit
-    if ((e = cudaFuncSetAttribute(q_filter_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem)) !=
-            cudaSuccess ||
-        (e = cudaFuncSetAttribute(qb_filter_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem)) !=
-            cudaSuccess)
-      return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_series, kFiltWarps * 32, ssmem)) != cudaSuccess)
       return e;
     ix->grid_series = std::max(1, per_sm) * sms;

@@ -1036,84 +1036,72 @@ constexpr int kRows = 4;
 constexpr int kRowWarps = 8;
 constexpr int kBlkThreads = 256;
 
-// The block filter: one thread per (work item, aligned block of 32 positions)
-// re-tests the item's leaf bound against the current BSF, bounds the block by its
-// symbol envelope and lists the surviving blocks.
-// Squared iSAX bound of a block's symbol envelope from the breakpoints alone: per
-// segment, the gap between the query's interval [l_j, u_j] and the region of the
-// symbol clamp(query symbol, lo_j, hi_j), i.e. the table entry T[j][that symbol]
-// recomputed with the same operations (lower <= upper and l <= u, so at most one of
-// the two differences is positive; a NaN interval gives 0, as the table's compares do).
-__device__ __forceinline__ float env_lb2_edges(uint4 lo, uint4 hi, const float* thr_lo_s, const float* thr_up_s,
-                                               const float* iu, const float* il, const int* qsym, int w,
-                                               float seglen) {
+// One thread per (work item, aligned block of 32 positions): re-tests the item's
+// leaf bound against the current BSF, bounds the block by its symbol envelope
+// (T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range),
+// and lists the surviving blocks; the list is compacted per CTA (one atomic per CTA).
+// Squared iSAX bound of a symbol envelope (per-segment min / max symbols lo, hi):
+// T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range.
+template <bool kW16>
+__device__ __forceinline__ float env_lb2_t(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
+                                           float seglen) {
   const uint32_t lop[4] = {lo.x, lo.y, lo.z, lo.w}, hip[4] = {hi.x, hi.y, hi.z, hi.w};
   float acc = 0.0f;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if (j < w) {
+    if (kW16 || j < w) {
       const int sl = (lop[j >> 2] >> (8 * (j & 3))) & 255, sh = (hip[j >> 2] >> (8 * (j & 3))) & 255;
-      const int v = min(max(qsym[j], sl), sh);
-      const float d = fmaxf(fmaxf(__fsub_rn(thr_lo_s[v], iu[j]), __fsub_rn(il[j], thr_up_s[v + 1])), 0.0f);
-      acc = __fadd_rn(acc, __fmul_rn(d, d));
+      acc = __fadd_rn(acc, Ts[j * card + min(max(qsym[j], sl), sh)]);
     }
   }
   return __fmul_rn(acc, seglen);
 }
+__device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, const int* qsym, int w, int card,
+                                         float seglen) {
+  return w == 16 ? env_lb2_t<true>(lo, hi, Ts, qsym, w, card, seglen)
+                 : env_lb2_t<false>(lo, hi, Ts, qsym, w, card, seglen);
+}
 
-// One thread per (work item, aligned block of 32 positions); each warp compacts its
-// surviving blocks with a ballot and one atomic, so warps never wait on one another.
 __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const QueryView& qv) {
-  __shared__ float thr_lo_s[257], thr_up_s[257];
-  __shared__ float iu_s[16], il_s[16];
+  
+  extern __shared__ __align__(16) float Ts[];  // [w][card]
   __shared__ int qsym_s[16];
+  __shared__ uint32_t s_cnt, s_base;
+  __shared__ uint2 s_out[kBlkThreads];
   __shared__ uint32_t fl_s[kMaxFront];
-  for (int v = threadIdx.x; v <= ix.card; v += blockDim.x) {
-    thr_lo_s[v] = ix.thr_lo[v];
-    thr_up_s[v] = ix.thr_up[v];
-  }
-  if (threadIdx.x < ix.w) {
-    qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
-    iu_s[threadIdx.x] = qv.st->qup[threadIdx.x];
-    il_s[threadIdx.x] = qv.st->qlo[threadIdx.x];
-  }
+  smem_fill(Ts, qv.T, ix.w * ix.card);
+  if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
   const uint32_t nfront = qv.st->nfront;
   if (threadIdx.x < nfront) fl_s[threadIdx.x] = qv.st->front_leaf[threadIdx.x];
   const uint32_t ntask = min(qv.st->item_count, qv.items_cap) * kBlocksPerItem;
   const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
   const float seglen = (float)ix.seglen;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  __syncthreads();
   for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < ntask; t0 += gridDim.x * blockDim.x) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
     const uint32_t t = t0 + threadIdx.x;
-    bool keep = false;
-    uint2 out = make_uint2(0, 0);
     if (t < ntask) {
       const uint4 item = qv.items[t / kBlocksPerItem];
       const uint32_t blk = (item.x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
       bool front = false;  // a leaf refined early
       for (uint32_t f = 0; f < nfront; ++f) front |= fl_s[f] == item.w;
       if (!front && __uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
-        keep = env_lb2_edges(__ldg(ix.benv + 2 * blk), __ldg(ix.benv + 2 * blk + 1), thr_lo_s, thr_up_s, iu_s, il_s,
-                             qsym_s, ix.w, seglen) <= bound2;
-        // task: block index, and the block's positions inside the item: [lo, hi) offsets
-        const uint32_t lo_off = max(item.x, blk * 32) - blk * 32, hi_off = min(item.y, blk * 32 + 32) - blk * 32;
-        out = make_uint2(blk, lo_off | (hi_off << 8));
+        if (env_lb2(__ldg(ix.benv + 2 * blk), __ldg(ix.benv + 2 * blk + 1), Ts, qsym_s, ix.w, ix.card, seglen) <=
+            bound2) {
+          // task: block index, and the block's positions inside the item: [lo, hi) offsets
+          const uint32_t lo_off = max(item.x, blk * 32) - blk * 32, hi_off = min(item.y, blk * 32 + 32) - blk * 32;
+          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, lo_off | (hi_off << 8));
+        }
       }
     }
-    const unsigned m = __ballot_sync(kFull, keep);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&qv.st->blk_count, (uint32_t)__popc(m));
-      base = __shfl_sync(kFull, base, leader);
-      if (keep) {
-        const uint32_t slot = base + __popc(m & lt);
-        if (slot < qv.blks_cap) qv.blks[slot] = out;
-        else qv.st->overflow = 1u;
-      }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&qv.st->blk_count, s_cnt) : 0u;
+    __syncthreads();
+    if (threadIdx.x < s_cnt) {
+      if (s_base + threadIdx.x < qv.blks_cap) qv.blks[s_base + threadIdx.x] = s_out[threadIdx.x];
+      else qv.st->overflow = 1u;
     }
+    __syncthreads();
   }
 }
 
@@ -2592,7 +2580,7 @@ static cudaError_t refine_config(msi_index* ix) {
         cudaSuccess)
       return e;
     ix->grid_series_b = std::max(1, per_sm) * sms;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_filter_blocks, kBlkThreads, fsmem)) != cudaSuccess)
       return e;
     ix->grid_blocks = std::max(1, per_sm) * sms;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_refine_rows<true>, kRowWarps * 32, rsmem)) !=
@@ -2679,7 +2667,7 @@ static cudaError_t query_one_dtw(msi_index* ix, QueryView qv, int share, const f
   MSI_LAUNCH(q_leaf_filter, nlf, kThreads, 0, s, v, qv);
   MSI_LAUNCH(q_front_dtw, (unsigned)std::min<int64_t>((ix->cap + kDtwWarps - 1) / kDtwWarps, 512), kDtwWarps * 32, dsm, s, v, qv, nlf);
   if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);
-  MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, 0, s, v, qv);
+  MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s, v, qv);
   if (ev_m) cudaEventRecord(ev_m, s);
@@ -2733,7 +2721,7 @@ cudaError_t query_one(msi_index* ix, const QueryView& ws, int share, const float
   MSI_LAUNCH(q_leaf_filter, nlf, kThreads, 0, s, v, qv);
   MSI_LAUNCH(q_front, (unsigned)std::min<int64_t>((ix->cap + 7) / 8, 256), kThreads, qbytes, s, v, qv, nlf);
   if (k > 1) MSI_LAUNCH(q_seed_select, 1, 1024, 0, s, qv, 1);  // the k-th best over seed and front
-  MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, 0, s, v, qv);
+  MSI_LAUNCH(q_filter_blocks, blocks_grid, kBlkThreads, fsmem, s, v, qv);
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(q_filter_series, series_grid, kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s, v, qv);
   if (ev_m) cudaEventRecord(ev_m, s);
@@ -2835,7 +2823,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   cudaError_t e;
   if (count < 1 || count > (int)ix->bws.size() || count > 65535) return cudaErrorInvalidValue;
   if (ix->bws_dirty) return cudaErrorNotReady;  // batch_setup has not written the views
-  if ((e = refine_config(ix)) != cudaSuccess) return e;  // grid sizes and launch limits, once per index
+  if ((e = refine_config(ix)) != cudaSuccess) return e;  // grid sizes, once per index
   if (ix->batch_order && !ix->batch_dense)  // batch_setup allocates the ordered copies
     for (int i = 0; i < count; ++i)
       if (!ix->bws[i].surv2) return cudaErrorNotReady;
@@ -2899,7 +2887,7 @@ cudaError_t query_batch(msi_index* ix, int count, int k, const CallDesc* call, i
   MSI_LAUNCH(qb_front, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ix->cap + 7) / 8, 256) / share), B),
              kThreads, qbytes, s, v, a);
   if (k > 1) MSI_LAUNCH(qb_seed_select, dim3(1, B), 1024, 0, s, a, 1);
-  MSI_LAUNCH(qb_filter_blocks, dim3(blocks_grid, B), kBlkThreads, 0, s, v, a);
+  MSI_LAUNCH(qb_filter_blocks, dim3(blocks_grid, B), kBlkThreads, fsmem, s, v, a);
   if (ev_a) cudaEventRecord(ev_a, s);
   MSI_LAUNCH(qb_filter_series, dim3(series_grid, B), kFiltWarps * 32, fsmem + sizeof(float) * (size_t)ix->w * kCoarse, s,
              v, a);

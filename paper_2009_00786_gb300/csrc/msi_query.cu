@@ -236,51 +236,32 @@ __device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ 
 // segments of the squared gap between the series' mean and the query's interval
 // [lo_j, up_j]. The stored mean h is fp16, within e = |h| 2^-11 + 2^-25 of the fp32
 // mean (half an fp16 ulp), so each gap is taken e short; every step rounds down.
-__device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t id) {
-  const int chunks = ix.wf >> 3;
-  const uint4* src = ix.fine + (size_t)id * chunks;
-  float acc = 0.0f;
-  for (int c = 0; c < chunks; ++c) {
-    const uint4 v = __ldg(src + c);
-    const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int h2 = 0; h2 < 4; ++h2) {
-      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&parts[h2]));
-      const float hv[2] = {f.x, f.y};
-#pragma unroll
-      for (int e2 = 0; e2 < 2; ++e2) {
-        const int j = 8 * c + 2 * h2 + e2;
-        const float h = hv[e2];
-        const float e = __fmaf_ru(fabsf(h), 4.8828125e-4f, 2.98023223876953125e-8f);
-        const float g = fmaxf(0.0f, fmaxf(__fsub_rd(__fsub_rd(h, fup[j]), e), __fsub_rd(__fsub_rd(flo[j], h), e)));
-        acc = __fmaf_rd(g, g, acc);
-      }
-    }
-  }
-  return __fmul_rd(acc, (float)ix.sf);
-}
-
-// The same bound for up to 32 series at once (lane i: series id, for i < count),
-// eight lanes per series: in round r of a half, lane 8 g + c reads 16-byte chunk c
-// (segments 8 c .. 8 c + 7) of series 16 half + 4 r + g, the half's four loads issued
-// before any arithmetic, and the eight partial sums are combined by shuffles. Every
-// step rounds down, so the sum stays at or below the exact one in this order too.
+// Computed for up to 32 series at once (lane i: series id, for the lanes in `valid`;
+// the others return 0) by all 32 lanes of the warp together, eight lanes per series: in round r of a half, lane 8 g + c
+// reads 16-byte chunk c (segments 8 c .. 8 c + 7) of series 16 half + 4 r + g, the
+// half's four loads issued before any arithmetic, and the eight partial sums are
+// combined by shuffles. Every step rounds down, so the sum stays at or below the
+// exact one in this order too.
 __device__ __forceinline__ float warp_fine_lb2_32(const IndexView& ix, const float* fup, const float* flo,
-                                                  uint32_t id, int count) {
+                                                  uint32_t id, unsigned valid) {
   const int lane = threadIdx.x & 31, c = lane & 7, g = lane >> 3;
   const int chunks = ix.wf >> 3;
   float mine = 0.0f;
+  if (!valid) return mine;  // the same in every lane
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
+    if (!((valid >> (16 * half)) & 0xffffu)) continue;  // warp-uniform: no series in this half
     uint4 v[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int s = 16 * half + 4 * r + g;
       const uint32_t sid = __shfl_sync(kFull, id, s);
-      v[r] = s < count && c < chunks ? __ldg(ix.fine + (size_t)sid * chunks + c) : make_uint4(0, 0, 0, 0);
+      v[r] = ((valid >> s) & 1u) && c < chunks ? __ldg(ix.fine + (size_t)sid * chunks + c) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
+      const int base = 16 * half + 4 * r;
+      if (!((valid >> base) & 0xfu)) continue;  // warp-uniform: no series in this round
       float acc = 0.0f;
       if (c < chunks) {
         const uint32_t parts[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
@@ -302,7 +283,6 @@ __device__ __forceinline__ float warp_fine_lb2_32(const IndexView& ix, const flo
       acc = __fadd_rd(acc, __shfl_xor_sync(kFull, acc, 1));  // the same sum in all 8 lanes
       acc = __fadd_rd(acc, __shfl_xor_sync(kFull, acc, 2));
       acc = __fadd_rd(acc, __shfl_xor_sync(kFull, acc, 4));
-      const int base = 16 * half + 4 * r;
       const float t = __shfl_sync(kFull, acc, 8 * ((lane - base) & 3));
       if (lane >= base && lane < base + 4) mine = t;
     }
@@ -579,9 +559,13 @@ __device__ __forceinline__ unsigned khist_bound(const uint32_t* khist, float kba
 
 // ------------------------------------------------------------------ q_seed
 __device__ __forceinline__ void q_seed_body(const IndexView& ix, const QueryView& qv) {
-  
   extern __shared__ __align__(16) float qs[];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
+  const uint32_t a = qv.st->seed_a, b = qv.st->seed_b;
+  // the grid covers the largest leaf: a block whose warps start past the seed leaf's
+  // rows returns before it loads the query (the same decision in every thread)
+  const uint32_t rows_per_block = (kThreads / 32) * ((qv.k == 1 && ix.wf) ? kSeedGroup : 1);
+  if ((uint64_t)blockIdx.x * rows_per_block >= b - a) return;
   smem_fill(qs, qv.qz, ix.len);
   for (int j = threadIdx.x; j < ix.wf; j += blockDim.x) {
     fup_s[j] = qv.st->fup[j];
@@ -590,7 +574,6 @@ __device__ __forceinline__ void q_seed_body(const IndexView& ix, const QueryView
   __syncthreads();
   __shared__ unsigned s_min;
   if (threadIdx.x == 0) s_min = 0x7f800000u;
-  const uint32_t a = qv.st->seed_a, b = qv.st->seed_b;
   const uint32_t warps = gridDim.x * (kThreads / 32);
   const int lane = threadIdx.x & 31;
   unsigned best = 0x7f800000u;
@@ -614,7 +597,8 @@ __device__ __forceinline__ void q_seed_body(const IndexView& ix, const QueryView
          g0 += warps * kSeedGroup) {
       const uint32_t g = g0 + lane;
       const bool have = lane < kSeedGroup && g < nrow;
-      const float lb = have ? fine_lb2(ix, fup_s, flo_s, ix.perm[a + g]) : INFINITY;
+      const float flb = warp_fine_lb2_32(ix, fup_s, flo_s, have ? ix.perm[a + g] : 0u, __ballot_sync(kFull, have));
+      const float lb = have ? flb : INFINITY;
       float m = lb;
       int mi = lane;
 #pragma unroll
@@ -883,8 +867,11 @@ __device__ __forceinline__ void q_front_body(const IndexView& ix, const QueryVie
       const uint32_t g = g0 + lane;
       const uint32_t pos = g < total ? position(g) : 0u;
       const bool screen = g < total && !(pos >= sa && pos < sb);
-      n_fine += __popc(__ballot_sync(kFull, screen));
-      const bool want = screen && fine_lb2(ix, fup_s, flo_s, ix.perm[pos]) <= lbb;
+      const unsigned sm = __ballot_sync(kFull, screen);
+      n_fine += __popc(sm);
+      // every lane takes part in the warp's bound (it shuffles across all 32 lanes)
+      const float flb = warp_fine_lb2_32(ix, fup_s, flo_s, screen ? ix.perm[pos] : 0u, sm);
+      const bool want = screen && flb <= lbb;
       for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
     }
   } else {
@@ -1034,8 +1021,11 @@ __device__ __forceinline__ void q_front_picked_body(const IndexView& ix, const Q
       const uint32_t g = g0 + lane;
       const uint32_t pos = g < total ? position(g) : 0u;
       const bool screen = g < total && !(pos >= sa && pos < sb);
-      n_fine += __popc(__ballot_sync(kFull, screen));
-      const bool want = screen && fine_lb2(ix, fup_s, flo_s, ix.perm[pos]) <= lbb;
+      const unsigned sm = __ballot_sync(kFull, screen);
+      n_fine += __popc(sm);
+      // every lane takes part in the warp's bound (it shuffles across all 32 lanes)
+      const float flb = warp_fine_lb2_32(ix, fup_s, flo_s, screen ? ix.perm[pos] : 0u, sm);
+      const bool want = screen && flb <= lbb;
       for (unsigned m = __ballot_sync(kFull, want); m; m &= m - 1) refine(__shfl_sync(kFull, pos, __ffs(m) - 1));
     }
   } else {
@@ -1260,7 +1250,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     const uint32_t id = have ? __ldg(ix.perm + e.x) : 0u;
     n_fine += have;
     const float lb2 =
-        fmaxf(__uint_as_float(e.y), warp_fine_lb2_32(ix, fup_s, flo_s, id, count < 32u ? (int)count : 32));
+        fmaxf(__uint_as_float(e.y), warp_fine_lb2_32(ix, fup_s, flo_s, id, count < 32u ? (1u << count) - 1u : kFull));
     __syncwarp();
     for (uint32_t i = 32 + lane; i < count; i += 32) fq[i - 32] = fq[i];  // the rest down (a lane's own slots)
     push(have && lb2 <= bound2, e.x, lb2);

@@ -236,12 +236,36 @@ __device__ __forceinline__ void smem_fill(float* dst, const float* __restrict__ 
 // segments of the squared gap between the series' mean and the query's interval
 // [lo_j, up_j]. The stored mean h is fp16, within e = |h| 2^-11 + 2^-25 of the fp32
 // mean (half an fp16 ulp), so each gap is taken e short; every step rounds down.
-// Computed for up to 32 series at once (lane i: series id, for the lanes in `valid`;
-// the others return 0) by all 32 lanes of the warp together, eight lanes per series: in round r of a half, lane 8 g + c
-// reads 16-byte chunk c (segments 8 c .. 8 c + 7) of series 16 half + 4 r + g, the
-// half's four loads issued before any arithmetic, and the eight partial sums are
-// combined by shuffles. Every step rounds down, so the sum stays at or below the
-// exact one in this order too.
+__device__ __forceinline__ float fine_lb2(const IndexView& ix, const float* fup, const float* flo, uint32_t id) {
+  const int chunks = ix.wf >> 3;
+  const uint4* src = ix.fine + (size_t)id * chunks;
+  float acc = 0.0f;
+  for (int c = 0; c < chunks; ++c) {
+    const uint4 v = __ldg(src + c);
+    const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int h2 = 0; h2 < 4; ++h2) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&parts[h2]));
+      const float hv[2] = {f.x, f.y};
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2) {
+        const int j = 8 * c + 2 * h2 + e2;
+        const float h = hv[e2];
+        const float e = __fmaf_ru(fabsf(h), 4.8828125e-4f, 2.98023223876953125e-8f);
+        const float g = fmaxf(0.0f, fmaxf(__fsub_rd(__fsub_rd(h, fup[j]), e), __fsub_rd(__fsub_rd(flo[j], h), e)));
+        acc = __fmaf_rd(g, g, acc);
+      }
+    }
+  }
+  return __fmul_rd(acc, (float)ix.sf);
+}
+
+// The same bound for up to 32 series at once (lane i: series id, for the lanes in
+// `valid`; the others return 0) by all 32 lanes of the warp together, eight lanes per
+// series: in round r of a half, lane 8 g + c reads 16-byte chunk c (segments 8 c ..
+// 8 c + 7) of series 16 half + 4 r + g, the half's four loads issued before any
+// arithmetic, and the eight partial sums are combined by shuffles. Every step rounds
+// down, so the sum stays at or below the exact one in this order too.
 __device__ __forceinline__ float warp_fine_lb2_32(const IndexView& ix, const float* fup, const float* flo,
                                                   uint32_t id, unsigned valid) {
   const int lane = threadIdx.x & 31, c = lane & 7, g = lane >> 3;
@@ -1157,7 +1181,6 @@ q_filter_blocks(IndexView ix, QueryView qv) {
 // kCoarse entries per segment, at most two lanes per bank); the words that pass are
 // queued per warp and bounded from their full symbols (T) a whole warp at a time.
 constexpr int kQueue = 64;
-constexpr int kFineQueue = 32 + 32 * kUnroll;  // < 32 left over + one drain per task in flight
 
 // Coarse bound from the symbols' top kCoarseBits bits. The table entry's byte offset
 // inside segment j's row comes straight from the word: symbol byte b of a 32-bit part
@@ -1197,7 +1220,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   __shared__ uint2 buf_s[kFiltWarps][64];
   __shared__ uint4 qw_s[kFiltWarps][kQueue];
   __shared__ uint32_t qp_s[kFiltWarps][kQueue];
-  __shared__ uint2 fq_s[kFiltWarps][kFineQueue];
   __shared__ float fup_s[kMaxFine], flo_s[kMaxFine];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   smem_fill(T5s, qv.T5, ix.w * kCoarse);
@@ -1210,7 +1232,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   uint2* buf = buf_s[warp];
   uint4* qw = qw_s[warp];
   uint32_t* qp = qp_s[warp];
-  uint2* fq = fq_s[warp];
   QState* st = qv.st;
   const uint32_t ntask = min(st->blk_count, qv.blks_cap);
   const uint32_t sa = st->seed_a, sb = st->seed_b;
@@ -1220,17 +1241,30 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gw = blockIdx.x * kFiltWarps + warp;
   const uint32_t stride = gridDim.x * kFiltWarps;
-  uint32_t nbuf = 0, nq = 0, nfq = 0, n_lb = 0, n_fine = 0;
+  uint32_t nbuf = 0, nq = 0, n_lb = 0, n_fine = 0;
   float bound2 = 0.0f;
 
-  // survivors {position, bound} to the warp's buffer, flushed 32 at a time with one
-  // atomic, entry by entry
-  auto push = [&](bool pass, uint32_t p, float lb2) {
+  // full bounds of the first 32 queued words (one per lane); survivors to the buffer
+  auto drain32 = [&](uint32_t count) {
+    const bool have = lane < (int)count;
+    const uint32_t p = have ? qp[lane] : 0u;
+    float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
+    bool pass = have && lb2 <= bound2;
+    if (pass && ix.wf) {  // the fine PAA's bound, before the series is read
+      ++n_fine;
+      lb2 = fmaxf(lb2, fine_lb2(ix, fup_s, flo_s, __ldg(ix.perm + p)));
+      pass = lb2 <= bound2;
+    }
+    __syncwarp();
+    if (count > 32 && lane < (int)count - 32) {  // move the rest of the queue down
+      qw[lane] = qw[32 + lane];
+      qp[lane] = qp[32 + lane];
+    }
     const unsigned m = __ballot_sync(kFull, pass);
     if (pass) buf[nbuf + __popc(m & lt)] = make_uint2(p, __float_as_uint(lb2));
     nbuf += __popc(m);
     __syncwarp();
-    if (nbuf >= 32) {
+    if (nbuf >= 32) {  // flush 32 survivors with one atomic, entry by entry
       uint32_t base = 0;
       if (lane == 0) base = atomicAdd(&st->surv_count, 32u);
       base = __shfl_sync(kFull, base, 0);
@@ -1240,47 +1274,6 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
       if (lane < (int)nbuf - 32) buf[lane] = buf[32 + lane];
       nbuf -= 32;
       __syncwarp();
-    }
-  };
-  // fine PAA bounds (before any series is read) of the first 32 words queued after
-  // passing the full bound: their ids and fine PAA are read for all of them at once
-  auto fine32 = [&](uint32_t count) {
-    const bool have = lane < (int)count;
-    const uint2 e = have ? fq[lane] : make_uint2(0u, 0u);
-    const uint32_t id = have ? __ldg(ix.perm + e.x) : 0u;
-    n_fine += have;
-    const float lb2 =
-        fmaxf(__uint_as_float(e.y), warp_fine_lb2_32(ix, fup_s, flo_s, id, count < 32u ? (1u << count) - 1u : kFull));
-    __syncwarp();
-    for (uint32_t i = 32 + lane; i < count; i += 32) fq[i - 32] = fq[i];  // the rest down (a lane's own slots)
-    push(have && lb2 <= bound2, e.x, lb2);
-  };
-  auto fine_drain = [&]() {  // while 32 wait for the fine bound
-    while (nfq >= 32) {
-      fine32(nfq);
-      nfq -= 32;
-    }
-  };
-  // full bounds of the first 32 queued words (one per lane); with a fine PAA the words
-  // that pass go to the fine queue (bounded between rounds of tasks, when the round's
-  // words no longer hold registers), else straight to the survivors
-  auto drain32 = [&](uint32_t count) {
-    const bool have = lane < (int)count;
-    const uint32_t p = have ? qp[lane] : 0u;
-    const float lb2 = have ? word_lb2(qw[lane], Ts, ix.w, ix.card, seglen) : INFINITY;
-    const bool pass = have && lb2 <= bound2;
-    __syncwarp();
-    if (count > 32 && lane < (int)count - 32) {  // move the rest of the queue down
-      qw[lane] = qw[32 + lane];
-      qp[lane] = qp[32 + lane];
-    }
-    if (ix.wf) {
-      const unsigned m = __ballot_sync(kFull, pass);
-      if (pass) fq[nfq + __popc(m & lt)] = make_uint2(p, __float_as_uint(lb2));
-      nfq += __popc(m);
-      __syncwarp();
-    } else {
-      push(pass, p, lb2);
     }
   };
 
@@ -1318,18 +1311,11 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
         nq -= 32;
       }
     }
-    fine_drain();
   }
   while (nq > 0) {
     const uint32_t c = nq;
     drain32(c);
     nq = c > 32 ? c - 32 : 0;
-    fine_drain();
-  }
-  while (nfq > 0) {
-    const uint32_t c = nfq;
-    fine32(c);
-    nfq = c > 32 ? c - 32 : 0;
   }
   // the last partial buffers of the CTA's warps: one atomic for the whole CTA
   __syncwarp();

@@ -200,10 +200,24 @@ __device__ __forceinline__ float tree_half(float v, int width) {
 }
 
 // NC <= 4 (len <= 512) and G <= 16 (segments of at most 64 points).
+// Pairs of rows in flight per warp in summarise_pair (its shared-memory ring): three
+// up to 256 points, two at 512 (16 KB per warp then).
+template <int NC>
+constexpr int kPairStages = NC >= 4 ? 2 : 3;
+template <int NC>
+constexpr size_t pair_ring_bytes() {
+  return (size_t)kSumWarps * kPairStages<NC> * 2 * NC * 32 * sizeof(float4);
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kSumWarps * 32)
 summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bits, int G,
                const float* __restrict__ thr_up_g, const uint8_t* __restrict__ cell_lo_g, SumOut o) {
+  // per warp a ring of kPairStages<NC> pairs of rows in shared memory, filled by
+  // 16-byte asynchronous copies kPairStages - 1 pairs ahead; every lane copies and
+  // later reads only its own float4s, so the ring needs no synchronisation between lanes
+  constexpr int S = kPairStages<NC>;
+  extern __shared__ __align__(16) float4 ring_s[];  // [kSumWarps][S][2 halves][NC * 32]
   __shared__ float thr_s[257];
   __shared__ uint8_t cell_s[kSymCells];
   __shared__ __align__(16) uint8_t sw_s[kSumWarps][2][16];
@@ -224,17 +238,40 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
   uint8_t* sw = sw_s[warp][half];
   __half* fs = fs_s[warp][half];
   float* paa = paa_s[warp][half];
-  for (int64_t i0 = 2 * ((int64_t)blockIdx.x * kSumWarps + warp); i0 < n; i0 += 2 * (int64_t)gridDim.x * kSumWarps) {
+  float4* ring = ring_s + (size_t)warp * S * 2 * NC * 32 + half * NC * 32;  // stage st at + st * 2 NC 32
+  const int64_t first = 2 * ((int64_t)blockIdx.x * kSumWarps + warp), stride = 2 * (int64_t)gridDim.x * kSumWarps;
+  // this lane's float4s of the pair starting at p0 (the half past the end re-reads p0)
+  // into stage st; one commit group per pair, empty past the end
+  auto issue = [&](int64_t p0, int st) {
+    if (p0 < n) {
+      const int64_t i = p0 + half < n ? p0 + half : p0;
+      const float4* row = reinterpret_cast<const float4*>(src + i * len);
+      float4* dst = ring + st * 2 * NC * 32;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        cp_async16(dst + c * 32 + hl, row + c * 32 + hl);
+        cp_async16(dst + c * 32 + hl + 16, row + c * 32 + hl + 16);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int st = 0; st < S - 1; ++st) issue(first + st * stride, st);
+  int stage = 0;
+  for (int64_t i0 = first; i0 < n; i0 += stride) {
+    issue(i0 + (S - 1) * stride, stage == 0 ? S - 1 : stage - 1);  // the slot this lane read last
+    cp_async_wait<S - 1>();  // pair i0 has landed (this lane's copies)
     const int64_t i = i0 + half;
     const bool valid = i < n;
-    const float4* row = reinterpret_cast<const float4*>(src + (valid ? i : i0) * len);
     // part A: canonical lane hl, part B: canonical lane hl + 16 (float4 index 32 c + lane)
     float4 va[NC], vb[NC];
+    const float4* cur = ring + stage * 2 * NC * 32;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      va[c] = __ldcs(row + c * 32 + hl);
-      vb[c] = __ldcs(row + c * 32 + hl + 16);
+      va[c] = cur[c * 32 + hl];
+      vb[c] = cur[c * 32 + hl + 16];
     }
+    stage = stage == S - 1 ? 0 : stage + 1;
     float sa = 0.0f, sb = 0.0f;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -316,6 +353,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
     }
     __syncwarp();
   }
+  cp_async_wait<0>();  // the ring's last (empty) groups, before the block ends
 }
 
 // Generic path: any length up to MSI_MAX_LEN and any segment length. The warp
@@ -943,10 +981,17 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
     MSI_TRY(cudaStreamSynchronize(s));  // the host table is freed on return
     const int64_t pairs = (n + 1) / 2;
     const int64_t blocks = std::min<int64_t>((pairs + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);
+    // the row rings pass the 48 KB default from 256 points on: raise the limit per width
+    MSI_TRY(cudaFuncSetAttribute(summarise_pair<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_ring_bytes<1>()));
+    MSI_TRY(cudaFuncSetAttribute(summarise_pair<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_ring_bytes<2>()));
+    MSI_TRY(cudaFuncSetAttribute(summarise_pair<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_ring_bytes<4>()));
     switch (len / 128) {
-      case 1: summarise_pair<1><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
-      case 2: summarise_pair<2><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
-      default: summarise_pair<4><<<(unsigned)blocks, kSumWarps * 32, 0, s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+      case 1: summarise_pair<1><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<1>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+      case 2: summarise_pair<2><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<2>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
+      default: summarise_pair<4><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<4>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
     }
   } else if (fast) {
     const int64_t blocks = std::min<int64_t>((n + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);

@@ -334,6 +334,16 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* b, uint32_t parity, uint
 }
 // One bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16),
 // completing on barrier b's transaction count.
+// 16-byte asynchronous copy into shared memory (global -> L2 -> shared, no L1), its
+// commit group, and the wait until at most N of this thread's newest groups are pending.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),

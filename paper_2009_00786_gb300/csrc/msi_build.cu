@@ -209,10 +209,17 @@ constexpr size_t pair_ring_bytes() {
   return (size_t)kSumWarps * kPairStages<NC> * 2 * NC * 32 * sizeof(float4);
 }
 
-template <int NC>
+__host__ __device__ constexpr int ilog2c(int v) { return v > 1 ? 1 + ilog2c(v >> 1) : 0; }
+
+// kG, kSF, kW, kBits: the segment's float4 groups, the fine PAA's points per segment,
+// the segments and the symbol bits fixed at compile time (0, or -1 for kSF: read from
+// the arguments), so that the trees unroll and the shape's branches fold away; the
+// arithmetic and its order are the same either way.
+template <int NC, int kG = 0, int kSF = -1, int kW = 0, int kBits = 0>
 __global__ void __launch_bounds__(kSumWarps * 32)
-summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bits, int G,
+summarise_pair(const float* __restrict__ src, int64_t n, int w_rt, int card, int bits_rt, int G_rt,
                const float* __restrict__ thr_up_g, const uint8_t* __restrict__ cell_lo_g, SumOut o) {
+  const int G = kG ? kG : G_rt, w = kW ? kW : w_rt, bits = kBits ? kBits : bits_rt;
   // per warp a ring of kPairStages<NC> pairs of rows in shared memory, filled by
   // 16-byte asynchronous copies kPairStages - 1 pairs ahead; every lane copies and
   // later reads only its own float4s, so the ring needs no synchronisation between lanes
@@ -231,10 +238,13 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
   const int len = NC * 128;
   const int s = 4 * G;
   const int segs_per_chunk = 128 / s;
-  const int sf = o.sf;
-  // len, s and sf are powers of two here: their exact reciprocals
+  const int sf = kSF >= 0 ? kSF : o.sf;
+  // len, s and sf are powers of two here: their exact reciprocals, and shifts for the
+  // per-chunk index divisions by G and sf
   const float inv_len = 1.0f / (float)len, inv_s = 1.0f / (float)s;
   const float inv_sf = sf ? 1.0f / (float)sf : 0.0f;
+  const int lg_g = kG ? ilog2c(kG) : __ffs(G) - 1;
+  const int lg_sf = kSF >= 0 ? ilog2c(kSF > 0 ? kSF : 1) : (sf ? __ffs(sf) - 1 : 0);
   uint8_t* sw = sw_s[warp][half];
   __half* fs = fs_s[warp][half];
   float* paa = paa_s[warp][half];
@@ -321,7 +331,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
           } else {
             float gf = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
             gf = tree_half(gf, sf / 4);  // sf / 4 <= 16 consecutive canonical lanes, one part
-            if ((L & (sf / 4 - 1)) == 0) fs[t0 / sf] = __float2half_rn(div_pow2(gf, inv_sf));
+            if ((L & (sf / 4 - 1)) == 0) fs[t0 >> lg_sf] = __float2half_rn(div_pow2(gf, inv_sf));
           }
         }
         // PAA: groups of 4 points, G consecutive canonical lanes per segment (G <= 16,
@@ -329,7 +339,7 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w, int card, int bi
         float g = __fadd_rn(__fadd_rn(__fadd_rn(z.x, z.y), z.z), z.w);
         g = tree_half(g, G);
         if ((L & (G - 1)) == 0) {
-          const int j = c * segs_per_chunk + L / G;
+          const int j = c * segs_per_chunk + (L >> lg_g);
           if (j < 16) paa[j] = div_pow2(g, inv_s);
         }
       }
@@ -988,7 +998,15 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
                                  (int)pair_ring_bytes<2>()));
     MSI_TRY(cudaFuncSetAttribute(summarise_pair<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)pair_ring_bytes<4>()));
-    switch (len / 128) {
+    MSI_TRY(cudaFuncSetAttribute(summarise_pair<2, 4, 4, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_ring_bytes<2>()));
+    // 256 points, 16 segments of 16, 64 fine segments of 4, 8-bit symbols: its own
+    // compiled shape; every other shape reads these from the arguments
+    const bool shape_256_16 = len == 256 && G == 4 && o.sf == 4 && w == 16 && ix->bits == 8;
+    if (shape_256_16)
+      summarise_pair<2, 4, 4, 16, 8><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<2>(), s>>>(
+          src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o);
+    else switch (len / 128) {
       case 1: summarise_pair<1><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<1>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
       case 2: summarise_pair<2><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<2>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;
       default: summarise_pair<4><<<(unsigned)blocks, kSumWarps * 32, pair_ring_bytes<4>(), s>>>(src_dev, n, w, ix->card, ix->bits, G, ix->thr_up, cell_d, o); break;

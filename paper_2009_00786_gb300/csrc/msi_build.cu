@@ -200,10 +200,10 @@ __device__ __forceinline__ float tree_half(float v, int width) {
 }
 
 // NC <= 4 (len <= 512) and G <= 16 (segments of at most 64 points).
-// Pairs of rows in flight per warp in summarise_pair (its shared-memory ring): three
-// up to 256 points, two at 512 (16 KB per warp then).
+// Pairs of rows per warp in summarise_pair's shared-memory ring: the pair being
+// summarised and the next one in flight (a third stage measured no faster).
 template <int NC>
-constexpr int kPairStages = NC >= 4 ? 2 : 3;
+constexpr int kPairStages = 2;
 template <int NC>
 constexpr size_t pair_ring_bytes() {
   return (size_t)kSumWarps * kPairStages<NC> * 2 * NC * 32 * sizeof(float4);

@@ -442,7 +442,8 @@ rs_upsweep(const unsigned long long* __restrict__ keys, int64_t n, int shift, ui
 // of equal digit in shared memory, and the tile is then written out in that order, so
 // keys of one digit leave as one contiguous run instead of one scattered store each.
 // The tile's count of digit d is the difference of consecutive scanned offsets
-// (digit-major).
+// (digit-major). A thread loads its 16 keys and values of the tile before the first
+// round, so the rounds wait on no global load.
 constexpr size_t kRsSmem = (size_t)kRsTile * (sizeof(unsigned long long) + sizeof(uint32_t));
 __global__ void __launch_bounds__(kRsThreads)
 rs_scatter_local(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
@@ -488,14 +489,27 @@ rs_scatter_local(const unsigned long long* __restrict__ kin, const uint32_t* __r
     run[threadIdx.x] = st;
     __syncthreads();
   }
+  unsigned long long kr[kRsRounds];
+  uint32_t vr[kRsRounds];
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) {
+    const int li = r * kRsThreads + threadIdx.x;
+    kr[r] = li < count ? kin[base + li] : 0ull;
+    vr[r] = li < count ? vin[base + li] : 0u;
+  }
+  // keep the loads here, all in flight together (the compiler would otherwise move
+  // each one down to its round)
+#pragma unroll
+  for (int r = 0; r < kRsRounds; ++r) asm volatile("" : "+l"(kr[r]), "+r"(vr[r]));
+#pragma unroll
   for (int r = 0; r < kRsRounds; ++r) {
 #pragma unroll
     for (int q = 0; q < kW; ++q) wc[q][threadIdx.x] = 0;
     __syncthreads();
     const int li = r * kRsThreads + threadIdx.x;
     const bool valid = li < count;
-    const unsigned long long key = valid ? kin[base + li] : 0ull;
-    const uint32_t val = valid ? vin[base + li] : 0u;
+    const unsigned long long key = kr[r];
+    const uint32_t val = vr[r];
     const int d = valid ? (int)((key >> shift) & 255) : 256;
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & lt);

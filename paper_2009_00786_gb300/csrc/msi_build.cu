@@ -29,11 +29,18 @@ namespace {
 // ------------------------------------------------------------------ summarise
 constexpr int kSumWarps = 8;
 
+// A series' SAX word and moments side by side: one 32-byte sector, so that the
+// gathers into leaf order fetch one sector per series instead of two.
+struct __align__(32) SumRec {
+  uint4 word;
+  float2 stats;  // (mu, 1/sigma)
+  float2 pad;
+};
+
 struct SumOut {
-  uint4* words;                 // [n] collection order
+  SumRec* rec;                  // [n] collection order: word and moments
   unsigned long long* keys;     // [n]
   uint32_t* ids;                // [n] iota
-  float2* stats;                // [n] collection order (mu, 1/sigma)
   float* z_out;                 // [n][len] or nullptr (borrowed data)
   unsigned long long* first_bad;  // min id of a non-finite series
   uint4* fine;                  // [n][wf / 8] collection order: fine PAA (fp16), or nullptr
@@ -54,7 +61,7 @@ __device__ __forceinline__ void emit_word(uint8_t* sw, int sym_lane, int w, int 
   const unsigned long long key = interleave_key(sym_lane, w, bits);
   if (lane == 0) {
     const uint4 word = *reinterpret_cast<const uint4*>(sw);
-    o.words[i] = word;
+    o.rec[i].word = word;
     o.keys[i] = key;
     o.ids[i] = (uint32_t)i;
   }
@@ -149,7 +156,7 @@ summarise_fast(const float* __restrict__ src, int64_t n, int w, int card, int bi
     const int sym = lane < w ? sax_symbol(thr_s, card, paa_s[warp][lane]) : 0;
     if (lane < 16) sw[lane] = (uint8_t)sym;
     __syncwarp();
-    if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
+    if (lane == 0) o.rec[i].stats = make_float2(m.mu, m.rsig);
     emit_word(sw, sym, w, bits, i, o);
     if (o.fine) emit_fine(fs, i, o);
     __syncwarp();
@@ -351,8 +358,8 @@ summarise_pair(const float* __restrict__ src, int64_t n, int w_rt, int card, int
     __syncwarp();
     const unsigned long long key = interleave_key_half(sym, w, bits, hl, half);
     if (valid && hl == 0) {
-      o.stats[i] = make_float2(m.mu, m.rsig);
-      o.words[i] = *reinterpret_cast<const uint4*>(sw);
+      o.rec[i].stats = make_float2(m.mu, m.rsig);
+      o.rec[i].word = *reinterpret_cast<const uint4*>(sw);
       o.keys[i] = key;
       o.ids[i] = (uint32_t)i;
     }
@@ -399,7 +406,7 @@ summarise_generic(const float* __restrict__ src, int64_t n, int len, int w, int 
     if (lane < w) sym = sax_symbol(thr_s, card, paa_segment_generic(zs, lane, s));
     if (lane < 16) sw[lane] = lane < w ? (uint8_t)sym : 0;
     __syncwarp();
-    if (lane == 0) o.stats[i] = make_float2(m.mu, m.rsig);
+    if (lane == 0) o.rec[i].stats = make_float2(m.mu, m.rsig);
     emit_word(sw, sym, w, bits, i, o);
     if (o.fine) {
       for (int j = lane; j < o.wf; j += 32) {
@@ -708,10 +715,10 @@ __global__ void bal_roots(const Node* __restrict__ nodes, const uint32_t* __rest
   root_child[keys[nd.begin] >> (64 - root_bits)] = (int32_t)i;
 }
 
-__global__ void gather_words(const uint32_t* __restrict__ ids, int64_t n, const uint4* __restrict__ words_in,
+__global__ void gather_words(const uint32_t* __restrict__ ids, int64_t n, const SumRec* __restrict__ rec,
                              uint4* __restrict__ words_out) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) words_out[p] = words_in[ids[p]];
+  if (p < n) words_out[p] = rec[ids[p]].word;
 }
 
 __global__ void __launch_bounds__(kScanThreads)
@@ -887,14 +894,13 @@ __global__ void block_envelopes(const uint4* __restrict__ words, int64_t n, uint
   }
 }
 
-__global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, const uint4* __restrict__ words_in,
-                                  const float2* __restrict__ stats_in, uint4* __restrict__ words_out,
-                                  float2* __restrict__ stats_out) {
+__global__ void gather_leaf_order(const uint32_t* __restrict__ perm, int64_t n, const SumRec* __restrict__ rec,
+                                  uint4* __restrict__ words_out, float2* __restrict__ stats_out) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const uint32_t id = perm[p];
-  words_out[p] = words_in[id];
-  stats_out[p] = stats_in[id];
+  words_out[p] = rec[id].word;
+  stats_out[p] = rec[id].stats;
 }
 
 template <typename T>
@@ -958,15 +964,14 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
      // a level (and the balanced split's sort buffers); 64 MB of room for the rest
     const int64_t tiles_b = (n + kRsTile - 1) / kRsTile;
     const bool bal = (ix->flags & MSI_BUILD_BALANCED_SPLIT) != 0;
-    const size_t want = (size_t)n * (16 + 8 + 4 + 8 + 8 + 4 + 1 + 4 + (bal ? 36 : 0)) + (size_t)tiles_b * 1024 +
+    const size_t want = (size_t)n * (32 + 4 + 8 + 8 + 4 + 1 + 4 + (bal ? 36 : 0)) + (size_t)tiles_b * 1024 +
                         (size_t)16 * std::min<int64_t>(n, (1ll << std::min(w * ix->bits, 20)) + 2 * (n / ix->cap) + 2) +
                         ((size_t)64 << 20);
     MSI_TRY(tmp.reserve(want));
   }
-  MSI_TRY(tmp.get(&o.words, n));
+  MSI_TRY(tmp.get(&o.rec, n));
   MSI_TRY(tmp.get(&o.keys, n));
   MSI_TRY(tmp.get(&o.ids, n));
-  MSI_TRY(tmp.get(&o.stats, n));
   MSI_TRY(tmp.get(&keys_alt, n));
   MSI_TRY(tmp.get(&ids_alt, n));
   MSI_TRY(tmp.get(&o.first_bad, 1));
@@ -1132,7 +1137,7 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
     MSI_TRY(tmp.get(&tree_count, 1));
     MSI_TRY(cudaMemcpyAsync(tree_count, counts, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     bal_roots<<<grid_for(R, 256), 256, 0, s>>>(na, counts, ka, w, root_bits, ba, ix->root_child);
-    gather_words<<<grid_for(n, 256), 256, 0, s>>>(va, n, o.words, wsort);
+    gather_words<<<grid_for(n, 256), 256, 0, s>>>(va, n, o.rec, wsort);
     MSI_TRY(cudaGetLastError());
     uint32_t live = R;
     for (int level = 0; live > 0; ++level) {
@@ -1192,7 +1197,7 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   const uint32_t nn = (uint32_t)n;
   MSI_TRY(cudaMemcpyAsync(ix->leaf_begin + ix->L, &nn, sizeof nn, cudaMemcpyHostToDevice, s));
   MSI_TRY(cudaMemcpyAsync(ix->perm, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
-  gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.words, o.stats, ix->words, ix->stats);
+  gather_leaf_order<<<grid_for(n, 256), 256, 0, s>>>(ix->perm, n, o.rec, ix->words, ix->stats);
   if (o.wf) {
     ix->wf = o.wf;
     ix->sf = o.sf;

@@ -997,17 +997,22 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   if (pair) {
     // the symbol cell table: thresholds t_1..t_{card-1} at or below the left edge of
     // the previous cell (-4 + (c - 1) / 128), counted on the host from the same table
-    std::vector<uint8_t> cells(kSymCells, 0);
+    // (ascending, so a binary search); it lives in the index, so the upload needs no wait
+    static_assert(sizeof(ix->h_sym_cells) == kSymCells, "cell table size");
+    ix->h_sym_cells[0] = 0;
     for (int c = 1; c < kSymCells; ++c) {
       const double edge = -4.0 + (double)(c - 1) / 128.0;
-      int cnt = 0;
-      for (int v = 1; v < ix->card; ++v) cnt += (double)ix->h_thr_up[v] <= edge ? 1 : 0;
-      cells[c] = (uint8_t)cnt;
+      int lo = 1, hi = ix->card;  // first v in [1, card) with t_v > edge, or card
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if ((double)ix->h_thr_up[mid] <= edge) lo = mid + 1;
+        else hi = mid;
+      }
+      ix->h_sym_cells[c] = (uint8_t)(lo - 1);
     }
     uint8_t* cell_d;
     MSI_TRY(tmp.get(&cell_d, kSymCells));
-    MSI_TRY(cudaMemcpyAsync(cell_d, cells.data(), kSymCells, cudaMemcpyHostToDevice, s));
-    MSI_TRY(cudaStreamSynchronize(s));  // the host table is freed on return
+    MSI_TRY(cudaMemcpyAsync(cell_d, ix->h_sym_cells, kSymCells, cudaMemcpyHostToDevice, s));
     const int64_t pairs = (n + 1) / 2;
     const int64_t blocks = std::min<int64_t>((pairs + kSumWarps - 1) / kSumWarps, (int64_t)dev_sms * 64);
     // the row rings pass the 48 KB default from 256 points on: raise the limit per width

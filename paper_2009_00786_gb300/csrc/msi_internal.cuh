@@ -403,6 +403,7 @@ struct msi_index {
   int root_bits = 0;
   float h_thr_up[257];
   float h_thr_lo[257];
+  uint8_t h_sym_cells[1024];  // the build's symbol cell table (host copy, read by an async upload)
   int64_t device_bytes = 0;
   cudaStream_t own_stream = nullptr;
   // query workspace (allocated on first use): slot 0 has room for any query; the

@@ -266,8 +266,8 @@ typedef struct msi_query_stats {
   int64_t queries;
   int64_t leaves_total;          /* leaves examined by the leaf filter              */
   int64_t leaves_survived;       /* leaves whose bound did not exceed the threshold */
-  int64_t blocks_examined;       /* blocks of 32 leaf positions whose envelope bound */
-                                 /* passed (k > 32: leaves processed)               */
+  int64_t blocks_examined;       /* half-blocks of 16 leaf positions whose envelope  */
+                                 /* bound passed                                    */
   int64_t series_lower_bounded;  /* per-series lower bounds computed                */
   int64_t series_refined;        /* real distances computed (seed leaf included)    */
   int64_t seed_series;           /* real distances of the approximate-search seed   */

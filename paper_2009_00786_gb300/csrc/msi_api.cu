@@ -105,7 +105,7 @@ void free_index(msi_index* ix) {
   void* ptrs[] = {ix->data_owned, ix->words,     ix->perm,         ix->stats,   ix->leaf_begin, ix->env,
                   ix->benv,       ix->leaf_key,  ix->thr_up,       ix->thr_lo,  ix->qv.counters, ix->ws_qraw,
                   ix->ws_ids,     ix->ws_dists,  ix->ws_ovf,       ix->ws_d64,  ix->root_child,  ix->tree_child,
-                  ix->tree_seg,   ix->fine};
+                  ix->tree_seg,   ix->fine,      ix->henv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   msi::free_workspace(ix->qv);

@@ -869,8 +869,11 @@ __global__ void envelopes(const uint4* __restrict__ words, const uint32_t* __res
   }
 }
 
-// Envelope of every aligned block of 32 leaf-order positions (one warp per block).
-__global__ void block_envelopes(const uint4* __restrict__ words, int64_t n, uint4* __restrict__ benv) {
+// Envelope of every aligned block of 32 leaf-order positions and of each of its two
+// halves of 16 (one warp per block: the first four shuffle levels close the halves,
+// the fifth the block).
+__global__ void block_envelopes(const uint4* __restrict__ words, int64_t n, uint4* __restrict__ benv,
+                                uint4* __restrict__ henv) {
   const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (blk * 32 >= n) return;
@@ -878,7 +881,12 @@ __global__ void block_envelopes(const uint4* __restrict__ words, int64_t n, uint
   uint4 lo = make_uint4(~0u, ~0u, ~0u, ~0u), hi = make_uint4(0, 0, 0, 0);
   if (p < n) lo = hi = words[p];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
+  for (int off = 1; off < 32; off <<= 1) {
+    if (off == 16 && (lane & 15) == 0 && blk * 32 + lane < n) {  // a half with at least one position
+      const int64_t hb = 2 * blk + (lane >> 4);
+      henv[2 * hb] = lo;
+      henv[2 * hb + 1] = hi;
+    }
     lo.x = __vminu4(lo.x, __shfl_xor_sync(kFull, lo.x, off));
     lo.y = __vminu4(lo.y, __shfl_xor_sync(kFull, lo.y, off));
     lo.z = __vminu4(lo.z, __shfl_xor_sync(kFull, lo.z, off));
@@ -946,6 +954,12 @@ struct Freer {
 unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
+
+cudaError_t block_envelopes_of(msi_index* ix, cudaStream_t s) {
+  const int64_t nblk = (ix->n + 31) / 32;
+  block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, ix->n, ix->benv, ix->henv);
+  return cudaGetLastError();
+}
 
 // Builds every device structure of `ix` (shape fields, thresholds and data pointers
 // already set). `src_dev` holds the raw collection on the device; with `in_place`
@@ -1194,9 +1208,10 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
   MSI_TRY(dalloc(&ix->leaf_begin, ix->L + 1));
   MSI_TRY(dalloc(&ix->env, 2 * ix->L));
   MSI_TRY(dalloc(&ix->leaf_key, ix->L));
-  const int64_t nblk = (n + 31) / 32;
+  const int64_t nblk = (n + 31) / 32, nhb = (n + 15) / 16;
   MSI_TRY(dalloc(&ix->benv, 2 * nblk));
-  ix->device_bytes += (int64_t)n * (16 + 4 + 8) + (ix->L + 1) * 4 + ix->L * (32 + 8) + nblk * 32;
+  MSI_TRY(dalloc(&ix->henv, 2 * nhb));
+  ix->device_bytes += (int64_t)n * (16 + 4 + 8) + (ix->L + 1) * 4 + ix->L * (32 + 8) + nblk * 32 + nhb * 32;
   *stage = "envelopes";
   write_leaf_begin<<<grid_for(n, 256), 256, 0, s>>>(flags, rank, n, ix->leaf_begin);
   const uint32_t nn = (uint32_t)n;
@@ -1209,7 +1224,7 @@ cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cuda
     ix->device_bytes += (int64_t)n * 2 * o.wf;
   }
   envelopes<<<grid_for(ix->L * 32, 256), 256, 0, s>>>(ix->words, ix->leaf_begin, ix->L, ka, ix->env, ix->leaf_key);
-  block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, n, ix->benv);
+  block_envelopes<<<grid_for(nblk * 32, 256), 256, 0, s>>>(ix->words, n, ix->benv, ix->henv);
   MSI_TRY(cudaGetLastError());
   MSI_TRY(cudaStreamSynchronize(s));
   return cudaSuccess;

@@ -39,6 +39,7 @@ struct IndexView {
   const uint32_t* leaf_begin; // [L+1]
   const uint4* env;         // [L][2]: per-segment min symbols, max symbols
   const uint4* benv;        // [ceil(n/32)][2]: the same over aligned blocks of 32 leaf positions
+  const uint4* henv;        // [ceil(n/16)][2]: the same over aligned half-blocks of 16 positions
   const uint64_t* leaf_key; // [L]: interleaved key of each leaf's first member
   const float* thr_up;      // [card+1]: region upper edges: thr_up[v] = smallest float >= beta_v,
                             //   thr_up[0] = -inf, thr_up[card] = +inf (also the SAX thresholds)
@@ -90,7 +91,7 @@ struct QState {
   unsigned int leaf_count;      // leaves that passed the leaf filter
   unsigned int item_count;      // refinement work items (<= kItem positions of one leaf)
   unsigned int surv_count;      // series whose bound passed the series filter
-  unsigned int blk_count;       // leaf blocks whose envelope bound passed
+  unsigned int blk_count;       // half-blocks (16 positions) whose envelope bound passed
   unsigned int overflow;        // a candidate or survivor list ran out of room
   float kbase;                  // k > 1: the k-th best after the seed and front leaves; the
                                 // range [0, kbase) of the candidate histogram (0: none yet)
@@ -136,7 +137,7 @@ struct QueryView {
   uint2* surv;                  // [n]: {leaf-order position, bound^2 bits} of filter survivors
   uint2* surv2;                 // [surv_cap]: the same in ascending bound buckets (batch workspaces)
   const uint2* rsurv;           // the list the row kernel reads: surv2 when ordered, else null (surv)
-  uint2* blks;                  // [8 (n / kItem + 2L)]: {block index, lo | hi << 8} of surviving blocks
+  uint2* blks;                  // [16 (n / kItem + 2L)]: {half-block index, lo | hi << 8} of surviving halves
   unsigned long long* blockmin; // [L / 256 + 2]: per leaf-filter block, min (bound^2 bits << 32 | leaf)
   unsigned long long* cand;     // [n]: (fp32 d^2 bits << 32) | id
   double* rc_d;                 // [n]
@@ -391,6 +392,7 @@ struct msi_index {
   uint32_t* leaf_begin = nullptr;
   uint4* env = nullptr;
   uint4* benv = nullptr;
+  uint4* henv = nullptr;  // half-block envelopes: computed from the words (build and load)
   uint64_t* leaf_key = nullptr;
   float* thr_up = nullptr;
   float* thr_lo = nullptr;
@@ -478,6 +480,7 @@ struct msi_index {
     v.leaf_begin = leaf_begin;
     v.env = env;
     v.benv = benv;
+    v.henv = henv;
     v.leaf_key = leaf_key;
     v.thr_up = thr_up;
     v.thr_lo = thr_lo;
@@ -505,13 +508,16 @@ constexpr int kQueryChunk = 1024;
 // Build pipeline (msi_build.cu). All device pointers; stream-ordered.
 cudaError_t build_index(msi_index* ix, const float* src_dev, bool in_place, cudaStream_t s,
                         int64_t* first_bad, const char** stage);
+// Block and half-block envelopes of the leaf-order words (ix->words, ix->benv,
+// ix->henv allocated); enqueued on s.
+cudaError_t block_envelopes_of(msi_index* ix, cudaStream_t s);
 
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
 cudaError_t slots_setup(msi_index* ix);
 // items_cap: work items (and 8x that many block tasks) a query may list; 0: room for
 // any query. A query that needs more is flagged as overflowed and run again.
-// blks_cap: block tasks (0: 8 per work item).
+// blks_cap: half-block tasks (0: 16 per work item).
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
                             int64_t* bytes, uint32_t items_cap = 0, uint32_t blks_cap = 0);
 void slot_capacities(const msi_index* ix, int64_t requested, uint32_t* cand_cap, uint32_t* surv_cap);

@@ -268,6 +268,7 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
       (e = cudaMalloc(&ix->leaf_begin, sizeof(uint32_t) * (size_t)(h.L + 1))) != cudaSuccess ||
       (e = cudaMalloc(&ix->env, sizeof(uint4) * 2 * (size_t)h.L)) != cudaSuccess ||
       (e = cudaMalloc(&ix->benv, sizeof(uint4) * 2 * (size_t)h.nblk)) != cudaSuccess ||
+      (e = cudaMalloc(&ix->henv, sizeof(uint4) * 2 * (size_t)((h.n + 15) / 16))) != cudaSuccess ||
       (e = cudaMalloc(&ix->leaf_key, sizeof(uint64_t) * (size_t)h.L)) != cudaSuccess ||
       (tree && (e = cudaMalloc(&ix->root_child, sizeof(int32_t) << h.root_bits)) != cudaSuccess) ||
       (tree && (e = cudaMalloc(&ix->tree_child, 2 * sizeof(int32_t) * (size_t)h.tree_nodes)) != cudaSuccess) ||
@@ -282,7 +283,8 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
   ix->wf = wf;
   ix->sf = wf ? h.len / wf : 0;
   ix->device_bytes = (int64_t)2 * wf * h.n + (int64_t)(sizeof(uint4) + sizeof(uint32_t) + sizeof(float2)) * h.n +
-                     (int64_t)(4 + 32 + 8) * h.L + 32 * h.nblk + (borrow ? 0 : 4 * h.n * h.len);
+                     (int64_t)(4 + 32 + 8) * h.L + 32 * h.nblk + 32 * ((h.n + 15) / 16) +
+                     (borrow ? 0 : 4 * h.n * h.len);
   secs = sections(ix, h.nblk, !borrow);
   for (size_t si = 0; si < secs.size(); ++si) {
     const bool data = !borrow && si + 1 == secs.size();
@@ -301,6 +303,12 @@ msi_status msi_index_load(const char* path, const float* series, const msi_build
   }
   if (sum != h.index_checksum) {
     st = fail(MSI_EINVAL, "index file checksum mismatch");
+    goto fail_out;
+  }
+  // the half-block envelopes are not stored: computed from the loaded words
+  if ((e = msi::block_envelopes_of(ix, ix->own_stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ix->own_stream)) != cudaSuccess) {
+    st = cuda_fail(e, "computing the block envelopes");
     goto fail_out;
   }
   *out = ix;

@@ -1082,12 +1082,13 @@ __device__ __forceinline__ void q_front_picked_body(const IndexView& ix, const Q
 //
 // q_filter_blocks: a thread per aligned block of 32 positions of a work item (items
 //   are the positions of one surviving leaf inside an aligned tile of kItem
-//   positions): re-tests the leaf's bound against the current BSF and bounds the
-//   block by its symbol envelope; surviving blocks become tasks.
-// q_filter_series: a warp per task bounds every position by its SAX word (a coarse
-//   bound first, then the full one, then the fine PAA's when the index keeps one);
-//   survivors {position, bound} go to a per-warp buffer flushed 32 at a time to the
-//   survivor list. kUnroll tasks are in flight per warp.
+//   positions): re-tests the leaf's bound against the current BSF and bounds each
+//   of the block's two halves of 16 by its symbol envelope; surviving halves become
+//   tasks.
+// q_filter_series: a warp per two tasks (16 lanes each) bounds every position by its
+//   SAX word (a coarse bound first, then the full one, then the fine PAA's when the
+//   index keeps one); survivors {position, bound} go to a per-warp buffer flushed 32
+//   at a time to the survivor list. kUnroll task pairs are in flight per warp.
 // q_refine_rows: real distances of the survivors whose bound still passes the
 //   current BSF, kRows rows per warp at a time. k = 1: the BSF is an atomicMin taken
 //   only by a distance below the current BSF. k > 1: the shared candidate histogram
@@ -1096,6 +1097,7 @@ __device__ __forceinline__ void q_front_picked_body(const IndexView& ix, const Q
 constexpr int kFiltWarps = 8;
 constexpr int kUnroll = 4;
 constexpr int kBlocksPerItem = kItem / 32;
+constexpr int kHalvesPerItem = kItem / 16;  // half-block tasks a work item can yield
 constexpr int kRows = 4;
 constexpr int kRowWarps = 8;
 constexpr int kBlkThreads = 256;
@@ -1131,7 +1133,7 @@ __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const 
   extern __shared__ __align__(16) float Ts[];  // [w][card]
   __shared__ int qsym_s[16];
   __shared__ uint32_t s_cnt, s_base;
-  __shared__ uint2 s_out[kBlkThreads];
+  __shared__ uint2 s_out[2 * kBlkThreads];
   __shared__ uint32_t fl_s[kMaxFront];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
@@ -1150,19 +1152,33 @@ __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const 
       bool front = false;  // a leaf refined early
       for (uint32_t f = 0; f < nfront; ++f) front |= fl_s[f] == item.w;
       if (!front && __uint_as_float(item.z) <= bound2 && blk * 32 < item.y && blk * 32 + 32 > item.x) {
-        if (env_lb2(__ldg(ix.benv + 2 * blk), __ldg(ix.benv + 2 * blk + 1), Ts, qsym_s, ix.w, ix.card, seglen) <=
-            bound2) {
-          // task: block index, and the block's positions inside the item: [lo, hi) offsets
-          const uint32_t lo_off = max(item.x, blk * 32) - blk * 32, hi_off = min(item.y, blk * 32 + 32) - blk * 32;
-          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(blk, lo_off | (hi_off << 8));
+        // the block's positions inside the item, [lo, hi) offsets, and each of its two
+        // halves of 16 that holds some of them, bounded by the half's own envelope; a
+        // task is a half-block and its [lo, hi) offsets inside the half
+        const uint32_t b32 = blk * 32;
+        const uint32_t lo_off = max(item.x, b32) - b32, hi_off = min(item.y, b32 + 32) - b32;
+        const uint4* he = ix.henv + 4 * (size_t)blk;  // half 2 blk: he[0..1], half 2 blk + 1: he[2..3]
+        const bool in0 = lo_off < 16, in1 = hi_off > 16;
+        uint4 l0 = make_uint4(0, 0, 0, 0), h0 = l0, l1 = l0, h1 = l0;
+        if (in0) {
+          l0 = __ldg(he);
+          h0 = __ldg(he + 1);
         }
+        if (in1) {
+          l1 = __ldg(he + 2);
+          h1 = __ldg(he + 3);
+        }
+        if (in0 && env_lb2(l0, h0, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2)
+          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(2 * blk, lo_off | (min(hi_off, 16u) << 8));
+        if (in1 && env_lb2(l1, h1, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2)
+          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(2 * blk + 1, (max(lo_off, 16u) - 16) | ((hi_off - 16) << 8));
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&qv.st->blk_count, s_cnt) : 0u;
     __syncthreads();
-    if (threadIdx.x < s_cnt) {
-      if (s_base + threadIdx.x < qv.blks_cap) qv.blks[s_base + threadIdx.x] = s_out[threadIdx.x];
+    for (uint32_t j = threadIdx.x; j < s_cnt; j += blockDim.x) {
+      if (s_base + j < qv.blks_cap) qv.blks[s_base + j] = s_out[j];
       else qv.st->overflow = 1u;
     }
     __syncthreads();
@@ -1233,7 +1249,10 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   uint4* qw = qw_s[warp];
   uint32_t* qp = qp_s[warp];
   QState* st = qv.st;
-  const uint32_t ntask = min(st->blk_count, qv.blks_cap);
+  // tasks are half-blocks of 16 positions; a warp takes two at a time (lanes 0-15 the
+  // first, 16-31 the second)
+  const uint32_t nhalf = min(st->blk_count, qv.blks_cap), ntask = (nhalf + 1) / 2;
+  const int hl = lane & 15;
   const uint32_t sa = st->seed_a, sb = st->seed_b;
   const float seglen = (float)ix.seglen;
   const int cshift = ix.bits > kCoarseBits ? ix.bits - kCoarseBits : 0;
@@ -1283,20 +1302,20 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
     uint2 task[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t t = t0 + u * stride;
-      task[u] = t < ntask ? qv.blks[t] : make_uint2(0, 0);  // an empty range when past the end
+      const uint32_t r = 2 * (t0 + u * stride) + (lane >> 4);
+      task[u] = r < nhalf ? qv.blks[r] : make_uint2(0, 0);  // an empty range when past the end
     }
     uint4 wd[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t p = task[u].x * 32 + lane;
-      const bool in = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8);
+      const uint32_t p = task[u].x * 16 + hl;
+      const bool in = hl >= (int)(task[u].y & 255u) && hl < (int)(task[u].y >> 8);
       wd[u] = in ? __ldg(ix.words + p) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t p = task[u].x * 32 + lane;
-      const bool valid = lane >= (int)(task[u].y & 255u) && lane < (int)(task[u].y >> 8) && (p < sa || p >= sb);
+      const uint32_t p = task[u].x * 16 + hl;
+      const bool valid = hl >= (int)(task[u].y & 255u) && hl < (int)(task[u].y >> 8) && (p < sa || p >= sb);
       n_lb += valid;
       const bool pass_c = valid && word_lb2_coarse(wd[u], T5s, ix.w, cshift, seglen) <= bound2;
       const unsigned m = __ballot_sync(kFull, pass_c);
@@ -1344,7 +1363,7 @@ __device__ __forceinline__ void q_filter_series_body(const IndexView& ix, const 
   }
   if (lane == 0 && gw < kMaxRefineWarps) {
     qv.partials[gw] = n_lb;
-    qv.partials[2 * kMaxRefineWarps + gw] = gw == 0 ? ntask : 0u;
+    qv.partials[2 * kMaxRefineWarps + gw] = gw == 0 ? nhalf : 0u;
     qv.partials[3 * kMaxRefineWarps + gw] = n_fine;
   }
 }
@@ -2506,7 +2525,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
                             int64_t* bytes, uint32_t items_cap, uint32_t blks_cap) {
   cudaError_t e;
   const size_t items = items_cap ? std::min<size_t>(items_cap, (size_t)full_items(ix)) : (size_t)full_items(ix);
-  const size_t blks = blks_cap ? std::min<size_t>(blks_cap, (size_t)kBlocksPerItem * items) : kBlocksPerItem * items;
+  const size_t blks = blks_cap ? std::min<size_t>(blks_cap, (size_t)kHalvesPerItem * items) : kHalvesPerItem * items;
   if ((e = dalloc(&qv.qz, (size_t)ix->len + 4)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T, (size_t)ix->w * ix->card)) != cudaSuccess) return e;
   if ((e = dalloc(&qv.T5, (size_t)ix->w * kCoarse)) != cudaSuccess) return e;
@@ -2539,7 +2558,7 @@ cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_ca
 int64_t workspace_bytes(const msi_index* ix, uint32_t cand_cap, uint32_t surv_cap, uint32_t items_cap,
                         uint32_t blks_cap) {
   const int64_t items = items_cap ? std::min<int64_t>(items_cap, full_items(ix)) : full_items(ix);
-  const int64_t blks = blks_cap ? std::min<int64_t>(blks_cap, kBlocksPerItem * items) : kBlocksPerItem * items;
+  const int64_t blks = blks_cap ? std::min<int64_t>(blks_cap, kHalvesPerItem * items) : kHalvesPerItem * items;
   return (int64_t)(3 * ix->len + 4 + 256) * 4 + (int64_t)ix->w * (ix->card + kCoarse) * 4 + (int64_t)ix->L * 8 +
          items * 16 + blks * 8 + 12ll * kMaxRefineWarps + (int64_t)cand_cap * 20 + (int64_t)surv_cap * 8;
 }
@@ -2813,12 +2832,12 @@ static void batch_capacities(const msi_index* ix, uint32_t* cand_cap, uint32_t* 
   if (ix->slot_cap) {
     *surv_cap = sc;
     *items_cap = (uint32_t)std::max(256, ix->slot_cap / 4);
-    *blks_cap = 0;  // 8 per item
+    *blks_cap = 0;  // 16 per item
     return;
   }
   *surv_cap = (uint32_t)std::min<int64_t>(ix->n, std::min<int64_t>(1 << 24, std::max<int64_t>(1 << 20, ix->n / 8)));
   *items_cap = 0;  // room for any query
-  *blks_cap = (uint32_t)std::min<int64_t>(kBlocksPerItem * full_items(ix), std::max<int64_t>(1 << 21, ix->n / 16));
+  *blks_cap = (uint32_t)std::min<int64_t>(kHalvesPerItem * full_items(ix), std::max<int64_t>(1 << 22, ix->n / 8));
 }
 
 cudaError_t batch_setup(msi_index* ix) {

@@ -1103,9 +1103,10 @@ constexpr int kRowWarps = 8;
 constexpr int kBlkThreads = 256;
 
 // One thread per (work item, aligned block of 32 positions): re-tests the item's
-// leaf bound against the current BSF, bounds the block by its symbol envelope
-// (T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range),
-// and lists the surviving blocks; the list is compacted per CTA (one atomic per CTA).
+// leaf bound against the current BSF, bounds each half of the block by its symbol
+// envelope (T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value
+// range), and lists the surviving halves; the list is compacted per warp (one atomic
+// per warp).
 // Squared iSAX bound of a symbol envelope (per-segment min / max symbols lo, hi):
 // T[j][clamp(query symbol, lo_j, hi_j)] is the gap to the envelope's value range.
 template <bool kW16>
@@ -1129,11 +1130,8 @@ __device__ __forceinline__ float env_lb2(uint4 lo, uint4 hi, const float* Ts, co
 }
 
 __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const QueryView& qv) {
-  
   extern __shared__ __align__(16) float Ts[];  // [w][card]
   __shared__ int qsym_s[16];
-  __shared__ uint32_t s_cnt, s_base;
-  __shared__ uint2 s_out[2 * kBlkThreads];
   __shared__ uint32_t fl_s[kMaxFront];
   smem_fill(Ts, qv.T, ix.w * ix.card);
   if (threadIdx.x < ix.w) qsym_s[threadIdx.x] = qv.st->qsym[threadIdx.x];
@@ -1142,10 +1140,13 @@ __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const 
   const uint32_t ntask = min(qv.st->item_count, qv.items_cap) * kBlocksPerItem;
   const float bound2 = lb_bound2(*(volatile unsigned*)&qv.st->thr_bits, qv.eps, qv.tau);
   const float seglen = (float)ix.seglen;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  __syncthreads();
   for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < ntask; t0 += gridDim.x * blockDim.x) {
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
     const uint32_t t = t0 + threadIdx.x;
+    bool k0 = false, k1 = false;
+    uint2 o0 = make_uint2(0, 0), o1 = o0;
     if (t < ntask) {
       const uint4 item = qv.items[t / kBlocksPerItem];
       const uint32_t blk = (item.x / kItem) * kBlocksPerItem + (t % kBlocksPerItem);
@@ -1168,20 +1169,30 @@ __device__ __forceinline__ void q_filter_blocks_body(const IndexView& ix, const 
           l1 = __ldg(he + 2);
           h1 = __ldg(he + 3);
         }
-        if (in0 && env_lb2(l0, h0, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2)
-          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(2 * blk, lo_off | (min(hi_off, 16u) << 8));
-        if (in1 && env_lb2(l1, h1, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2)
-          s_out[atomicAdd(&s_cnt, 1u)] = make_uint2(2 * blk + 1, (max(lo_off, 16u) - 16) | ((hi_off - 16) << 8));
+        k0 = in0 && env_lb2(l0, h0, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2;
+        k1 = in1 && env_lb2(l1, h1, Ts, qsym_s, ix.w, ix.card, seglen) <= bound2;
+        o0 = make_uint2(2 * blk, lo_off | (min(hi_off, 16u) << 8));
+        o1 = make_uint2(2 * blk + 1, (max(lo_off, 16u) - 16) | ((hi_off - 16) << 8));
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&qv.st->blk_count, s_cnt) : 0u;
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < s_cnt; j += blockDim.x) {
-      if (s_base + j < qv.blks_cap) qv.blks[s_base + j] = s_out[j];
-      else qv.st->overflow = 1u;
+    // the warp's surviving halves: one atomic for the warp, no block barrier
+    const unsigned m0 = __ballot_sync(kFull, k0), m1 = __ballot_sync(kFull, k1);
+    if (m0 | m1) {
+      const int leader = __ffs(m0 | m1) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&qv.st->blk_count, (uint32_t)(__popc(m0) + __popc(m1)));
+      base = __shfl_sync(kFull, base, leader);
+      if (k0) {
+        const uint32_t slot = base + __popc(m0 & lt);
+        if (slot < qv.blks_cap) qv.blks[slot] = o0;
+        else qv.st->overflow = 1u;
+      }
+      if (k1) {
+        const uint32_t slot = base + __popc(m0) + __popc(m1 & lt);
+        if (slot < qv.blks_cap) qv.blks[slot] = o1;
+        else qv.st->overflow = 1u;
+      }
     }
-    __syncthreads();
   }
 }
 

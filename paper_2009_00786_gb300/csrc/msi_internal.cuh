@@ -39,6 +39,7 @@ struct IndexView {
   const uint32_t* leaf_begin; // [L+1]
   const uint4* env;         // [L][2]: per-segment min symbols, max symbols
   const uint4* benv;        // [ceil(n/32)][2]: the same over aligned blocks of 32 leaf positions
+                            //   (kept in the index file; the block filter reads henv)
   const uint4* henv;        // [ceil(n/16)][2]: the same over aligned half-blocks of 16 positions
   const uint64_t* leaf_key; // [L]: interleaved key of each leaf's first member
   const float* thr_up;      // [card+1]: region upper edges: thr_up[v] = smallest float >= beta_v,
@@ -515,8 +516,8 @@ cudaError_t block_envelopes_of(msi_index* ix, cudaStream_t s);
 // Query pipeline (msi_query.cu).
 cudaError_t query_setup(msi_index* ix);
 cudaError_t slots_setup(msi_index* ix);
-// items_cap: work items (and 8x that many block tasks) a query may list; 0: room for
-// any query. A query that needs more is flagged as overflowed and run again.
+// items_cap: work items (and 16x that many half-block tasks) a query may list; 0: room
+// for any query. A query that needs more is flagged as overflowed and run again.
 // blks_cap: half-block tasks (0: 16 per work item).
 cudaError_t alloc_workspace(const msi_index* ix, QueryView& qv, uint32_t cand_cap, uint32_t surv_cap,
                             int64_t* bytes, uint32_t items_cap = 0, uint32_t blks_cap = 0);

@@ -176,6 +176,31 @@ def test_mindist_lower_bounds_true_distance_brute_force(n, w):
         assert oracle.mindist(qp, np.minimum(own, lo), np.maximum(own, hi), n, 256) == 0.0
 
 
+def test_mindist_of_nested_envelopes_is_monotone():
+    # The block filter bounds a block of 32 positions by the envelope of its halves
+    # of 16 (and could go down to quarters of 8): a symbol range that contains another
+    # bounds no higher, so every word's bound is at least its quarter's, which is at
+    # least its half's, which is at least its block's; and the finer envelopes do prune
+    # more (some half bound strictly exceeds its block's).
+    n, w = 64, 16
+    X = datagen.walks(23, 0, 512, n)
+    Z, _, W, _ = oracle.summarise(X, w, 256)
+    q = oracle.znorm(datagen.walks(24, 0, 1, n)[0])[0]
+    qp = oracle.paa64(q, w)
+    d = np.sqrt(((Z.astype(np.float64) - q.astype(np.float64)) ** 2).sum(axis=1))
+
+    def bounds(width):
+        g = W.reshape(-1, width, w)
+        return np.array([oracle.mindist(qp, b.min(axis=0), b.max(axis=0), n, 256) for b in g])
+
+    b32, b16, b8, b1 = bounds(32), bounds(16), bounds(8), bounds(1)
+    assert np.all(b32 <= b16.reshape(-1, 2).min(axis=1) + 1e-12)
+    assert np.all(b16 <= b8.reshape(-1, 2).min(axis=1) + 1e-12)
+    assert np.all(b8 <= b1.reshape(-1, 8).min(axis=1) + 1e-12)
+    assert np.all(b1 <= d + 1e-5)
+    assert np.any(b16.reshape(-1, 2).max(axis=1) > b32 + 1e-9)
+
+
 def test_mindist_equals_paa_distance_in_the_limit_of_fine_regions():
     # With the query's own symbols, each gap is at most the width of a region,
     # so LB(q, word(q)) == 0; a word whose every segment lies far away gives the
